@@ -1,0 +1,409 @@
+"""Pins of the CPU oracle against what the paper and mathematics fix.
+
+Each oracle function is checked against something other than itself:
+published known-answer vectors, a hand-derived worked example, closed forms,
+invariants (orthogonality, the alpha identity of Eq. 3, the integer identity
+behind the bit-plane estimator), unbiasedness of Eq. 4 over random rotations,
+error bounds against float64, and brute force on tiny inputs.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import philox, rabitq as R
+from tests.conftest import read_golden
+
+F32, F64 = np.float32, np.float64
+
+
+# ---------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    _, lines = read_golden("philox4x32_10_kat.txt")
+    for row in lines:
+        v = [int(t, 16) for t in row]
+        out = philox.philox4x32_10([v[0:4]], v[4:6])[0]
+        assert [int(o) for o in out] == v[6:10]
+
+
+def test_gaussian_moments_and_unit_map():
+    g = philox.gaussian(7, philox.STREAM_ROTATION, 400_000)
+    n = g.size
+    assert abs(g.mean()) < 5 / math.sqrt(n)
+    assert abs(g.var() - 1.0) < 5 * math.sqrt(2.0 / n)
+    # kurtosis of a normal is 3
+    assert abs((g ** 4).mean() / g.var() ** 2 - 3.0) < 0.05
+    a = np.array([0, 2**64 - 1, 2**63], dtype=np.uint64)
+    u = philox.unit_open(a)
+    assert u[0] == 0.5 * 2.0**-52 and u[1] == 1.0 - 0.5 * 2.0**-52 and u[2] == 0.5 + 0.5 * 2.0**-52
+
+
+# ---------------------------------------------------------------- P
+@pytest.mark.parametrize("dp", [128, 1024])
+def test_rotation_orthogonal(dp):
+    P = R.random_orthogonal(3, dp)
+    err = np.abs(P.T @ P - np.eye(dp)).max()
+    assert err <= 1e-12
+    v = np.random.default_rng(0).standard_normal(dp)
+    assert abs(np.linalg.norm(P.T @ v) - np.linalg.norm(v)) <= 1e-12 * np.linalg.norm(v)
+
+
+def test_rotation_is_signed_qr_of_gaussian():
+    # G = P R' must hold with R' = P^T G upper triangular, positive diagonal.
+    dp = 128
+    G = R.gaussian_matrix(11, dp)
+    P = R.random_orthogonal(11, dp)
+    Rp = P.T @ G
+    assert np.abs(np.tril(Rp, -1)).max() < 1e-11
+    assert (np.diag(Rp) > 0).all()
+    # Haar sanity: entries have variance 1/D_p
+    assert abs(P.var() * dp - 1.0) < 0.05
+
+
+# ---------------------------------------------------------------- keys
+def test_orderable_is_monotone_and_invertible():
+    rng = np.random.default_rng(1)
+    v = np.concatenate([rng.standard_normal(5000).astype(F32) * 1e3,
+                        np.array([0.0, -0.0, np.inf, -np.inf, 1e-45, -1e-45], F32)])
+    o = R.orderable(v)
+    for i in range(0, v.size - 1):
+        a, b = v[i], v[i + 1]
+        if a < b:
+            assert o[i] < o[i + 1]
+        elif a > b:
+            assert o[i] > o[i + 1]
+    back = R.from_orderable(o)
+    same = (back == v)
+    assert same.all()
+    keys = R.make_keys(v, np.arange(v.size))
+    srt = np.sort(keys)
+    ref = sorted(range(v.size), key=lambda i: (float(v[i]), i))
+    # -0 and +0 are equal floats (keys order -0 first); == treats them equal
+    assert np.array_equal(R.key_dist(srt), v[ref])
+    assert np.all(np.diff(R.key_dist(srt).astype(F64)) >= 0)
+
+
+# ---------------------------------------------------------------- sums
+def test_lane_sum_error_bound_and_small_cases():
+    rng = np.random.default_rng(2)
+    for n in (1, 7, 31, 32, 33, 96, 128, 960, 1024):
+        v = rng.standard_normal((20, n)).astype(F32)
+        s = R.lane_sum(v * v)
+        ex = (v.astype(F64) ** 2).sum(axis=1)
+        # |err| <= (n/32 + 5) * eps * sum|terms| (sequential then tree depth 5)
+        bound = (n / 32 + 6) * 2.0**-24 * ex
+        assert np.all(np.abs(s - ex) <= bound + 1e-30)
+    # exact on integers: the result is an exact sum when all partial sums fit
+    v = rng.integers(-100, 100, (10, 128)).astype(F32)
+    assert np.array_equal(R.lane_sum(v), v.astype(F64).sum(axis=1))
+
+
+def test_seq_sqdist_error_bound():
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal((17, 128)).astype(F32)
+    b = rng.standard_normal((9, 128)).astype(F32)
+    d = R.seq_sqdist(a, b)
+    ex = ((a.astype(F64)[:, None, :] - b.astype(F64)[None]) ** 2).sum(-1)
+    assert np.all(np.abs(d - ex) <= (128 + 4) * 2.0**-24 * ex)
+
+
+# ---------------------------------------------------------------- k-means
+def test_kmeans_init_is_smallest_keys():
+    n, nlist, seed = 300, 17, 5
+    rows = np.arange(n)
+    got = R.kmeans_init(seed, n, rows, nlist)
+    keys = philox.row_keys(seed, philox.STREAM_KMEANS_INIT, n)
+    ref = sorted(range(n), key=lambda i: (int(keys[i]), i))[:nlist]
+    assert list(got) == ref
+    assert len(set(got.tolist())) == nlist
+
+
+def test_train_subset():
+    rows = R.train_rows(9, 1000, 100)
+    assert rows.size == 100 and np.all(np.diff(rows) > 0)
+    assert np.array_equal(R.train_rows(9, 1000, 0), np.arange(1000))
+
+
+def test_update_is_mean_and_reseeds_empty():
+    # 1-D example worked by hand: centroids 0, 0 (duplicate), 10.
+    x = np.array([[-1.0], [1.0], [2.0], [9.0], [11.0], [30.0]], F32)
+    c0 = np.array([[0.0], [0.0], [10.0]], F32)
+    a, _ = R.assign(x, c0)
+    assert list(a) == [0, 0, 0, 2, 2, 2]      # tie 0 vs 1 goes to 0
+    c1 = R.update(x, a, 3)
+    # cluster 0 mean = 2/3, cluster 2 mean = 50/3; cluster 1 is empty. The
+    # largest clusters are 0 and 2 (3 members each) -> 0 (lowest id). Its
+    # members lie at distances 5/3, 1/3, 4/3 from 2/3, so -1.0 moves.
+    assert c1[0, 0] == F32(2.0 / 3.0) and c1[2, 0] == F32(50.0 / 3.0)
+    assert c1[1, 0] == -1.0
+
+
+def test_kmeans_objective_nonincreasing_and_recovers_mixture():
+    mix = W.mixture("tiny")
+    x, lab = mix.base(3000, labels=True)
+    c, hist = R.kmeans(x, 64, 8, seed=0, return_history=True)
+    assert all(hist[i + 1] <= hist[i] * (1 + 1e-6) for i in range(len(hist) - 1))
+    assert hist[-1] < 0.5 * hist[0]
+    # Started from the true component means of a well separated mixture, one
+    # assignment recovers the labels exactly and the update gives the mean of
+    # each component's rows.
+    means = mix.means().astype(F32)
+    a, _ = R.assign(x, means)
+    assert np.array_equal(a, lab)
+    c1 = R.update(x, a, 64)
+    for j in range(64):
+        m = x[lab == j].astype(F64).mean(axis=0)
+        assert np.allclose(c1[j], m, rtol=0, atol=1e-6 * (1 + np.abs(m).max()))
+
+
+# ---------------------------------------------------------------- encode
+def test_alpha_identity_and_codes():
+    mix = W.mixture("tiny")
+    x = mix.base(500)
+    c = x[:4].copy()
+    a, _ = R.assign(x, c)
+    P = R.random_orthogonal(1, 128)
+    codes, r, alpha, z = R.encode(x, c, a, P)
+    u = x.astype(F64) - c[a].astype(F64)
+    assert np.allclose(np.linalg.norm(z, axis=1), r, rtol=1e-12)
+    bits = R.unpack_bits(codes, 128).astype(F64)
+    b = 2 * bits - 1
+    ok = r > 0
+    # <P b / sqrt(D), u / r> = ||P^T u||_1 / (sqrt(D) r)   (Eq. 3)
+    lhs = ((b @ P.T) * u).sum(axis=1) / (math.sqrt(128) * np.where(ok, r, 1))
+    assert np.allclose(lhs[ok], alpha[ok], rtol=1e-12, atol=0)
+    assert np.all((alpha > 0) & (alpha <= 1 + 1e-12))
+    # sign convention: bit = [z >= 0]
+    assert np.array_equal(bits.astype(bool), z >= 0)
+
+
+def test_alpha_mean_and_zero_residual():
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((2000, 1024)).astype(F32)
+    P = R.random_orthogonal(2, 1024)
+    c = np.zeros((1, 1024), F32)
+    _, _, alpha, _ = R.encode(x, c, np.zeros(2000, np.int64), P)
+    # mean of ||z||_1 / (sqrt(D) ||z||) for a uniform unit vector -> sqrt(2/pi)
+    assert abs(alpha.mean() - math.sqrt(2 / math.pi)) < 2e-3
+    codes, r, alpha, _ = R.encode(c, c, np.zeros(1, np.int64), P)
+    assert r[0] == 0 and alpha[0] == 1.0 and (codes == 255).all()
+
+
+# ---------------------------------------------------------------- quantize
+def test_quantize_error_bound_and_degenerate():
+    rng = np.random.default_rng(5)
+    res = (rng.standard_normal((200, 128)) * rng.uniform(0.01, 100, (200, 1))).astype(F32)
+    qz = R.quantize(res)
+    qu = qz["qu"]
+    assert qu.min() >= 0 and qu.max() <= 15
+    recon = qu * qz["delta"][:, None].astype(F64) + qz["vl"][:, None]
+    err = np.abs(recon - res)
+    assert np.all(err <= qz["delta"][:, None] * (0.5 + 1e-5))
+    assert np.array_equal(qz["sq"], qu.sum(axis=1))
+    # bit-planes reassemble q_u
+    back = sum((1 << j) * R.unpack_bits(qz["planes"][:, j], 128).astype(np.int64)
+               for j in range(4))
+    assert np.array_equal(back, qu)
+    ex = (res.astype(F64) ** 2).sum(axis=1)
+    assert np.all(np.abs(qz["nq2"] - ex) <= 10 * 2.0**-24 * ex)
+    # vr == vl: all zeros
+    flat = np.full((1, 128), 3.5, F32)
+    q1 = R.quantize(flat)
+    assert (q1["qu"] == 0).all() and q1["delta"][0] == 0 and q1["sq"][0] == 0
+
+
+# ---------------------------------------------------------------- estimator
+def _lut_ip(codes, qu):
+    """FastScan form (Section 3.3.2): per 8-dim chunk, a 256-entry table of
+    sum of q_u over the set bits, indexed by the code byte."""
+    total = np.zeros(codes.shape[0], np.int64)
+    for j in range(codes.shape[1]):
+        table = np.array([sum(qu[8 * j + b] for b in range(8) if (v >> b) & 1)
+                          for v in range(256)])
+        total += table[codes[:, j]]
+    return total
+
+
+def test_integer_estimator_forms_agree_exactly():
+    rng = np.random.default_rng(6)
+    dp = 128
+    codes = rng.integers(0, 256, (300, dp // 8), dtype=np.uint8)
+    res = rng.standard_normal((1, dp)).astype(F32)
+    qz = R.quantize(res)
+    qu = qz["qu"][0]
+    bits = R.unpack_bits(codes, dp).astype(np.int64)
+    ip = R.ip_planes(codes, qz["planes"][0])
+    assert np.array_equal(ip, bits @ qu)                       # brute force
+    assert np.array_equal(ip, _lut_ip(codes, qu))              # gather / LUT
+    sel = np.where(bits.astype(bool), qu[None, :], 0).sum(1)   # select / mask
+    assert np.array_equal(ip, sel)
+    b = 2 * bits - 1                                           # +-1 form
+    assert np.array_equal(2 * ip - qz["sq"][0], b @ qu)
+    assert np.array_equal(2 * R.popcount8(codes) - dp, b.sum(1))
+
+
+def test_estimator_worked_example_by_hand():
+    g, _ = read_golden("estimator_by_hand.txt")
+    x = np.array([g["x"]], F32).astype(F32)
+    q = np.array([g["q"]], F32).astype(F32)
+    dp = 8
+    P = np.eye(dp)
+    c = np.zeros((1, dp), F32)
+    codes, r, alpha, _ = R.encode(x, c, np.zeros(1, np.int64), P)
+    assert int(codes[0, 0]) == int(g["code_byte"][0])
+    assert R.popcount8(codes)[0] == int(g["popcount"][0])
+    assert r[0] ** 2 == pytest.approx(float(g["r2"][0]), rel=1e-15)
+    assert alpha[0] == pytest.approx(int(g["alpha_num"][0]) / math.sqrt(int(g["alpha_den_sq"][0])), rel=1e-15)
+    qz = R.quantize(q - c)
+    assert list(qz["qu"][0]) == [int(v) for v in g["qu"]]
+    assert qz["sq"][0] == int(g["sq"][0])
+    assert R.ip_planes(codes, qz["planes"][0])[0] == int(g["ip"][0])
+    assert qz["nq2"][0] == int(g["nq2"][0])
+    r2, f = R.scan_factors(r.astype(F32), alpha.astype(F32), dp)
+    assert f[0] == pytest.approx(int(g["f_num"][0]) / int(g["f_den"][0]), rel=1e-6)
+    d2 = R.estimate(codes, r2, f, qz, dp, qi=0)[0]
+    want = Fraction(int(g["d2_num"][0]), int(g["d2_den"][0]))
+    assert d2 == pytest.approx(float(want), rel=1e-6)
+    assert ((x - q) ** 2).sum() == int(g["exact"][0])
+
+
+def test_t_form_matches_eq5_with_dequantised_query():
+    # Eq. 4-5 evaluated directly in float64 from the dequantised residual must
+    # match the float32 t-form up to float32 rounding.
+    rng = np.random.default_rng(8)
+    dp = 128
+    P = R.random_orthogonal(4, dp)
+    x = rng.standard_normal((400, dp)).astype(F32)
+    c = (rng.standard_normal((1, dp)) * 0.5).astype(F32)
+    q = rng.standard_normal((1, dp)).astype(F32)
+    codes, r, alpha, z = R.encode(x, c, np.zeros(400, np.int64), P)
+    r2, f = R.scan_factors(r.astype(F32), alpha.astype(F32), dp)
+    res = R.rotate(q, P) - (c.astype(F64) @ P).astype(F32)
+    qz = R.quantize(res)
+    d2 = R.estimate(codes, r2, f, qz, dp, qi=0)
+    zq = qz["qu"][0] * F64(qz["delta"][0]) + F64(qz["vl"][0])   # dequantised
+    nq = math.sqrt(F64(qz["nq2"][0]))
+    b = 2.0 * R.unpack_bits(codes, dp) - 1
+    s_hat = (b @ (zq / nq)) / (math.sqrt(dp) * alpha)                # Eq. 4
+    ref = F64(qz["nq2"][0]) + r ** 2 - 2 * nq * r * s_hat             # Eq. 5
+    assert np.allclose(d2, ref, rtol=2e-5, atol=2e-5 * ref.mean())
+
+
+def test_eq5_with_exact_inner_product_is_exact_distance():
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal((50, 16))
+    q = rng.standard_normal(16)
+    c = rng.standard_normal(16)
+    ux = (x - c) / np.linalg.norm(x - c, axis=1, keepdims=True)
+    uq = (q - c) / np.linalg.norm(q - c)
+    d2 = (np.linalg.norm(q - c) ** 2 + np.linalg.norm(x - c, axis=1) ** 2
+          - 2 * np.linalg.norm(q - c) * np.linalg.norm(x - c, axis=1) * (ux @ uq))
+    assert np.allclose(d2, ((x - q) ** 2).sum(axis=1), rtol=1e-12)
+
+
+def test_estimator_unbiased_over_rotations():
+    # E_P[s_hat] = <u_x, u_q> for Haar P (the RaBitQ estimator property).
+    rng = np.random.default_rng(10)
+    d, n = 16, 20000
+    ux = rng.standard_normal(d); ux /= np.linalg.norm(ux)
+    uq = rng.standard_normal(d); uq = uq - 0.6 * ux; uq /= np.linalg.norm(uq)
+    G = rng.standard_normal((n, d, d))
+    Q, Rr = np.linalg.qr(G)
+    s = np.sign(np.einsum("nii->ni", Rr))
+    P = Q * s[:, None, :]
+    zx = np.einsum("nij,i->nj", P, ux)
+    zq = np.einsum("nij,i->nj", P, uq)
+    alpha = np.abs(zx).sum(1) / math.sqrt(d)
+    b = np.where(zx >= 0, 1.0, -1.0)
+    s_hat = (b * zq).sum(1) / (math.sqrt(d) * alpha)
+    diff = s_hat - ux @ uq
+    assert abs(diff.mean()) < 4 * diff.std() / math.sqrt(n)
+
+
+# ---------------------------------------------------------------- search
+@pytest.fixture(scope="module")
+def tiny():
+    mix = W.mixture("tiny")
+    x = mix.base(4000)
+    q = mix.queries(40)
+    ix = R.build_index(x, 32, seed=0, iters=6)
+    return x, q, ix
+
+
+def test_probe_all_lists_and_fp64_order(tiny):
+    x, q, ix = tiny
+    qr = R.rotate(q, ix["P"])
+    ids, d = R.probe(qr, ix["cR"], 32)
+    assert all(sorted(r) == list(range(32)) for r in ids.tolist())
+    ex = ((q.astype(F64)[:, None] - ix["centroids"].astype(F64)[None]) ** 2).sum(-1)
+    ref = np.argsort(ex, axis=1, kind="stable")
+    gap_ok = np.diff(np.sort(ex, axis=1), axis=1).min(axis=1) > 1e-3 * ex.max()
+    assert np.array_equal(ids[gap_ok], ref[gap_ok])
+
+
+def test_prune_is_lossless_including_ties():
+    rng = np.random.default_rng(12)
+    d = rng.integers(0, 50, 5000).astype(F32)   # many exact ties
+    ids = rng.permutation(5000)
+    for n_sel in (1, 10, 200, 1024, 3000, 6000):
+        a = R.select_candidates(d, ids, n_sel, prune=True)
+        b = R.select_candidates(d, ids, n_sel, prune=False)
+        assert np.array_equal(a, b)
+        full = sorted(zip(d.tolist(), ids.tolist()))[:n_sel]
+        assert [int(i) for i in R.key_id(a)] == [i for _, i in full]
+
+
+def test_rerank_matches_fp64_and_pads():
+    rng = np.random.default_rng(13)
+    raw = rng.integers(0, 256, (100, 128)).astype(F32)
+    q = rng.integers(0, 256, 128).astype(F32)
+    cand = rng.choice(100, 30, replace=False)
+    oi, od = R.rerank(raw, q, cand, 10)
+    ex = ((raw[cand].astype(F64) - q) ** 2).sum(1)
+    ref = cand[np.lexsort((cand, ex))][:10]
+    assert np.array_equal(oi, ref) and np.array_equal(od, np.sort(ex)[:10])
+    oi, od = R.rerank(raw, q, cand[:3], 5)
+    assert list(oi[3:]) == [-1, -1] and np.isinf(od[3:]).all()
+
+
+def test_search_limit_is_exact_knn(tiny):
+    x, q, ix = tiny
+    ti, td = R.exact_knn(x, q, 10)
+    ids, dist = R.search(ix, q, 32, 10, x.shape[0])
+    assert np.array_equal(ids, ti)
+    assert np.allclose(dist, td, rtol=1e-5)
+
+
+def test_exact_knn_brute_force():
+    rng = np.random.default_rng(14)
+    x = rng.integers(0, 4, (200, 8)).astype(F32)   # heavy ties
+    q = rng.integers(0, 4, (5, 8)).astype(F32)
+    ids, dist = R.exact_knn(x, q, 7)
+    for i in range(5):
+        d = ((x.astype(F64) - q[i]) ** 2).sum(1)
+        ref = sorted(range(200), key=lambda j: (d[j], j))[:7]
+        assert list(ids[i]) == ref
+
+
+def test_recall_target_on_tiny_workload():
+    wl = W.WORKLOADS["tiny"]
+    x = wl["mix"].base(wl["n"])
+    q = wl["mix"].queries(wl["nq"])
+    ix = R.build_index(x, wl["nlist"], seed=0, iters=wl["iters"])
+    _, td = R.exact_knn(x, q, 10)
+    ids, _ = R.search(ix, q, wl["nprobe"], wl["k"], wl["n_rerank"])
+    assert R.recall_at(x, q, ids, td, 10) >= 0.95
+
+
+def test_per_query_params_and_no_rerank(tiny):
+    x, q, ix = tiny
+    npb = np.array([1, 4, 32, 2] * 10)
+    kk = np.array([1, 10, 5, 3] * 10)
+    ids, dist = R.search(ix, q, npb, kk, 50)
+    for i in range(8):
+        one, _ = R.search(ix, q[i:i + 1], int(npb[i]), int(kk[i]), 50)
+        assert np.array_equal(ids[i, :kk[i]], one[0])
+    ids0, d0 = R.search(ix, q[:4], 4, 5, 0)
+    assert np.all(np.diff(d0, axis=1) >= 0)
