@@ -73,9 +73,13 @@ def u64_words(w: np.ndarray):
 
 
 def row_keys(seed: int, stream: int, n: int) -> np.ndarray:
-    """One uint64 rank key per row 0..n-1 (first 64-bit word of its block)."""
-    a, _ = u64_words(stream_block(seed, stream, np.arange(n, dtype=np.uint64)))
-    return a
+    """Rank key of rows 0..n-1: (first output word << 32) | row, as uint64.
+
+    Keys are unique, and their integer order is (random word, row id) order.
+    """
+    rows = np.arange(n, dtype=np.uint64)
+    w0 = stream_block(seed, stream, rows)[:, 0].astype(np.uint64)
+    return (w0 << SH32) | rows
 
 
 def unit_open(a: np.ndarray) -> np.ndarray:

@@ -169,17 +169,14 @@ def train_rows(seed: int, n: int, n_train: int) -> np.ndarray:
     if n_train <= 0 or n_train >= n:
         return np.arange(n, dtype=np.int64)
     keys = philox.row_keys(seed, philox.STREAM_TRAIN_SAMPLE, n)
-    order = np.lexsort((np.arange(n), keys))
-    return np.sort(order[:n_train]).astype(np.int64)
+    return np.sort(np.argsort(keys)[:n_train]).astype(np.int64)
 
 
 def kmeans_init(seed: int, n: int, rows: np.ndarray, nlist: int) -> np.ndarray:
-    """Initial centroid rows: the nlist training rows with the smallest
-    (rank key, row id), in that order (a uniform sample without replacement).
-    """
+    """Initial centroid rows: the nlist training rows with the smallest rank
+    keys, in ascending key order (a uniform sample without replacement)."""
     keys = philox.row_keys(seed, philox.STREAM_KMEANS_INIT, n)[rows]
-    order = np.lexsort((rows, keys))
-    return rows[order[:nlist]]
+    return rows[np.argsort(keys)[:nlist]]
 
 
 def assign(x: np.ndarray, c: np.ndarray, chunk: int = 4096):

@@ -1,0 +1,159 @@
+// Internal declarations shared by the librq translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/rq.h"
+
+namespace rq {
+
+constexpr int kMaxDim = 2048;
+constexpr int kMaxSelect = 4096;      // largest n_rerank / k / nprobe
+constexpr int kBoundCandidates = 1024;  // candidates that set the first bound
+constexpr int kMaxNlist = 1 << 20;
+
+// Error bookkeeping: the first error message of the calling thread.
+void set_error(const std::string& msg);
+rq_status fail(rq_status s, const std::string& msg);
+rq_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define RQ_CUDA(call)                                                   \
+  do {                                                                  \
+    cudaError_t _e = (call);                                            \
+    if (_e != cudaSuccess) return ::rq::cuda_fail(_e, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define RQ_TRY(call)                         \
+  do {                                       \
+    rq_status _s = (call);                   \
+    if (_s != RQ_OK) return _s;              \
+  } while (0)
+
+inline int dim_pad(int d) { return ((d + 127) / 128) * 128; }
+
+// Search shape: one launch sequence (and one workspace) per distinct shape.
+struct SearchShape {
+  int64_t nq;
+  int npmax;      // largest nprobe of the batch
+  int nsel_max;   // largest selection size (n_rerank, or k when it is 0)
+  int k_stride;   // output row stride
+  int mode;       // resolved scan mode
+  int prune;
+  bool operator<(const SearchShape& o) const {
+    return std::tie(nq, npmax, nsel_max, k_stride, mode, prune) <
+           std::tie(o.nq, o.npmax, o.nsel_max, o.k_stride, o.mode, o.prune);
+  }
+};
+
+// Device workspace of one search shape, carved out of one allocation.
+struct Workspace {
+  void* base = nullptr;
+  size_t bytes = 0;
+  float* q = nullptr;           // nq x dim (input copy)
+  float* qrot = nullptr;        // nq x D_p
+  uint64_t* pkeys = nullptr;    // nq x nlist probe keys
+  int32_t* probe_ids = nullptr; // nq x npmax
+  float* probe_d = nullptr;     // nq x npmax
+  float4* qparams = nullptr;    // nq x npmax: vl, delta, nq2, Sq(bits of int)
+  uint32_t* planes = nullptr;   // nq x npmax x 4 x W words
+  uint32_t* bound = nullptr;    // nq
+  int32_t* counts = nullptr;    // nq
+  uint64_t* cand = nullptr;     // nq x cap
+  uint64_t* sel = nullptr;      // nq x nsel_max
+  int32_t* nprobe = nullptr;    // nq
+  int32_t* kq = nullptr;        // nq
+  int32_t* nsel = nullptr;      // nq
+  int32_t* rerank_on = nullptr; // nq: 1 if n_rerank > 0
+  int64_t* out_ids = nullptr;   // nq x k_stride
+  float* out_d = nullptr;       // nq x k_stride
+  // grouped scan work list
+  int32_t* list_count = nullptr;  // nlist: pairs probing each list
+  int32_t* list_off = nullptr;    // nlist + 1
+  int32_t* list_pairs = nullptr;  // nq*npmax: (q*npmax+p) grouped by list
+  int32_t* list_fill = nullptr;   // nlist
+  int32_t* work_count = nullptr;  // 1 + item counters
+  int4* work = nullptr;           // work items
+  int64_t cap = 0;                // candidate slots per query
+  int64_t max_items = 0;
+};
+
+struct Plan {
+  SearchShape shape;
+  cudaStream_t stream = nullptr;
+  Workspace ws;
+  cudaGraphExec_t graph = nullptr;
+  int32_t* h_params = nullptr;          // pinned staging of per-query parameters
+  cudaEvent_t params_ready = nullptr;   // the last copy out of h_params has run
+  uint64_t last_use = 0;
+};
+
+}  // namespace rq
+
+struct rq_index {
+  int device = 0;
+  int64_t n = 0;
+  int dim = 0, dp = 0, nlist = 0, C = 0;  // C = code bytes = dp / 8
+  rq_dtype raw_dtype = RQ_F32;
+  // device arrays
+  double* P = nullptr;        // dp x dp
+  float* P32 = nullptr;       // dp x dp
+  float* centroids = nullptr; // nlist x dim
+  float* cR = nullptr;        // nlist x dp
+  int64_t* offsets = nullptr; // nlist + 1
+  uint8_t* codes = nullptr;   // n x C
+  float* r = nullptr;         // n
+  float* alpha = nullptr;     // n
+  float2* fac = nullptr;      // n: {r^2, f}
+  uint32_t* ids = nullptr;    // n
+  int32_t* assign = nullptr;  // n (row order)
+  void* raw = nullptr;        // n x dim (float or uint8)
+  int32_t* d_err = nullptr;   // device error word
+  // host copies
+  std::vector<int64_t> h_offsets;
+  std::vector<int64_t> top_len_prefix;  // sum of the j largest list lengths
+  // tuned choice for RQ_SCAN_AUTO
+  std::atomic<int> auto_mode{RQ_SCAN_GROUPED};
+  // plans (workspaces, graphs) per (stream, shape)
+  std::mutex mu;
+  std::map<std::pair<cudaStream_t, rq::SearchShape>, std::unique_ptr<rq::Plan>> plans;
+  uint64_t plan_clock = 0;
+  cudaStream_t graph_stream = nullptr;  // used when a graph is asked on stream 0
+};
+
+namespace rq {
+
+// Build (rq_build.cu)
+rq_status build_index(const float* d_base_f32, const void* d_raw, rq_dtype dt,
+                      int64_t n, int dim, int nlist, uint64_t seed, int iters,
+                      int64_t train_size, const float* given_centroids,
+                      const double* given_P, rq_index* ix);
+rq_status kmeans_device(const float* d_x, int64_t n, int dim, int nlist,
+                        uint64_t seed, int iters, int64_t train_size,
+                        float* d_centroids);
+rq_status philox_gaussian_device(uint64_t seed, uint32_t stream, int64_t count,
+                                 double* d_out);
+void finish_index_host_side(rq_index* ix);
+
+// Search (rq_search.cu)
+rq_status search_run(rq_index* ix, const float* queries, int64_t nq,
+                     const int32_t* nprobe, const int32_t* k,
+                     const int32_t* n_rerank, int k_stride, int64_t* out_ids,
+                     float* out_dist, const rq_search_opts* opts,
+                     cudaStream_t stream);
+rq_status autotune(rq_index* ix, const float* queries, int64_t nq, int nprobe,
+                   int n_rerank, const char* cache_path);
+void free_plans(rq_index* ix);
+
+// Memory residence
+bool is_device_ptr(const void* p);
+
+}  // namespace rq

@@ -1,0 +1,1004 @@
+// IVF-RaBitQ search on the GPU (Section 2.1.2 query processing; Sections
+// 2.2.2 and 3.3): rotate each query once, rank the centroids, quantise each
+// probed residual to 4-bit planes, scan the probed lists with the estimator of
+// Eqs. 4-5 under a per-query bound (Section 3.3.3), select the best
+// candidates and re-rank them exactly (Section 3.3.4).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rq_common.cuh"
+#include "rq_internal.h"
+#include "rq_pairdist.cuh"
+#include "rq_scan.cuh"
+
+namespace rq {
+namespace {
+
+inline unsigned blocks_for(int64_t n, int per) {
+  return (unsigned)std::max<int64_t>(1, (n + per - 1) / per);
+}
+
+// ---------------------------------------------------------------------------
+// Rotation: q' = q P[:D, :] (float32, one multiply-add per term).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+rotate_kernel(const float* __restrict__ q, int64_t nq, int dim,
+              const float* __restrict__ P32, int dp, float* __restrict__ qrot) {
+  __shared__ float As[16][65];
+  __shared__ float Bs[16][64];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t r0 = (int64_t)blockIdx.x * 64;
+  const int col0 = blockIdx.y * 64;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < dim; k0 += 16) {
+    for (int t = threadIdx.x; t < 64 * 16; t += 256) {
+      const int r = t >> 4, kk = t & 15;
+      const int64_t row = r0 + r;
+      const int k = k0 + kk;
+      As[kk][r] = (row < nq && k < dim) ? q[row * dim + k] : 0.0f;
+      const int kr = t >> 6, cc = t & 63;
+      const int kb = k0 + kr;
+      Bs[kr][cc] = (kb < dim) ? P32[(int64_t)kb * dp + col0 + cc] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][4 * ty + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t row = r0 + 4 * ty + i;
+    if (row >= nq) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) qrot[row * dp + col0 + tx + 16 * j] = acc[i][j];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-row selection of the n smallest uint64 keys, ascending, padded with
+// all-ones keys to out_width. OUT 0: write keys; OUT 1: write (id, distance)
+// of probe keys as int32 / float.
+// ---------------------------------------------------------------------------
+template <int OUT>
+__global__ void __launch_bounds__(1024)
+select_rows_kernel(const uint64_t* __restrict__ keys, int64_t row_stride,
+                   const int32_t* __restrict__ counts, int64_t fixed_count, int64_t cap,
+                   const int32_t* __restrict__ nsel, int nsel_fixed,
+                   uint64_t* __restrict__ out, int out_width,
+                   int32_t* __restrict__ out_ids, float* __restrict__ out_d,
+                   int32_t* err) {
+  extern __shared__ uint64_t s_keys[];
+  __shared__ int hist[256];
+  __shared__ uint64_t bcast[2];
+  __shared__ int s_n;
+  const int64_t row = blockIdx.x;
+  const uint64_t* kr = keys + row * row_stride;
+  int64_t count = counts ? (int64_t)counts[row] : fixed_count;
+  if (count > cap) {
+    if (threadIdx.x == 0) flag_error(err, kErrCandidateOverflow);
+    count = cap;
+  }
+  const int n_sel = nsel ? nsel[row] : nsel_fixed;
+  int filled;
+  if (count <= kMaxSelect) {
+    const int m = next_pow2((int)std::max<int64_t>(count, 1));
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s_keys[i] = (i < count) ? kr[i] : kU64Max;
+    __syncthreads();
+    block_bitonic_sort(s_keys, m);
+    filled = (int)std::min<int64_t>(count, n_sel);
+  } else {
+    const uint64_t T = block_radix_select_u64(kr, count, n_sel, hist, bcast);
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < count; i += blockDim.x) {
+      const uint64_t k = kr[i];
+      if (k < T) {
+        const int pos = atomicAdd(&s_n, 1);
+        if (pos < n_sel) s_keys[pos] = k;
+      }
+    }
+    __syncthreads();
+    const int lt = std::min(s_n, n_sel);
+    const int m = next_pow2(n_sel);
+    for (int i = lt + threadIdx.x; i < m; i += blockDim.x) s_keys[i] = (i < n_sel) ? T : kU64Max;
+    __syncthreads();
+    block_bitonic_sort(s_keys, m);
+    filled = n_sel;
+  }
+  for (int j = threadIdx.x; j < out_width; j += blockDim.x) {
+    const uint64_t k = (j < filled) ? s_keys[j] : kU64Max;
+    if (OUT == 0) {
+      out[row * out_width + j] = k;
+    } else {
+      out_ids[row * out_width + j] = (k == kU64Max) ? -1 : (int32_t)(uint32_t)k;
+      out_d[row * out_width + j] =
+          (k == kU64Max) ? __int_as_float(0x7f800000) : from_orderable((uint32_t)(k >> 32));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Quantisation of each probed residual r = q' - P^T c (one warp per pair):
+// vl = min r, vr = max r, delta = (vr - vl)/15, inv = 15/(vr - vl),
+// q_u = min(15, floor((r - vl) inv + 1/2)) (0 when vr == vl), Sq = sum q_u,
+// nq2 = ||r||^2 in the 32-lane order; bit-plane j packs bit j of every q_u
+// (dimension d -> word d/32, bit d%32).
+// ---------------------------------------------------------------------------
+template <int NW4>
+__global__ void __launch_bounds__(256)
+quantize_kernel(const float* __restrict__ qrot, const int32_t* __restrict__ probe_ids,
+                const int32_t* __restrict__ nprobe, int npmax, int64_t nq,
+                const float* __restrict__ cR, int dp, float4* __restrict__ qparams,
+                uint32_t* __restrict__ planes, int32_t* err) {
+  constexpr int PER = 4 * NW4;  // values per lane (dp / 32)
+  const int64_t pair = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (pair >= nq * npmax) return;
+  const int64_t q = pair / npmax;
+  const int p = (int)(pair % npmax);
+  if (p >= nprobe[q]) return;
+  const int c = probe_ids[pair];
+  if (c < 0) {
+    if (lane == 0) flag_error(err, kErrBadProbe);
+    return;
+  }
+  float r[PER];
+  float vl = __int_as_float(0x7f800000), vr = -vl, acc = 0.0f;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int d = lane + 32 * i;
+    r[i] = __fsub_rn(qrot[q * dp + d], cR[(int64_t)c * dp + d]);
+    vl = fminf(vl, r[i]);
+    vr = fmaxf(vr, r[i]);
+    acc = __fadd_rn(acc, __fmul_rn(r[i], r[i]));
+  }
+  vl = warp_min(vl);
+  vr = warp_max(vr);
+  const float nq2 = lane_tree_sum(acc);
+  const float width = __fsub_rn(vr, vl);
+  const bool same = (width == 0.0f);
+  const float delta = same ? 0.0f : __fdiv_rn(width, 15.0f);
+  const float inv = same ? 0.0f : __fdiv_rn(15.0f, width);
+  int sq = 0;
+  constexpr int W = PER;  // words per plane
+  uint32_t* pl = planes + pair * 4 * W;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    int qu = 0;
+    if (!same) {
+      qu = (int)floorf(__fadd_rn(__fmul_rn(__fsub_rn(r[i], vl), inv), 0.5f));
+      qu = min(qu, 15);
+    }
+    sq += qu;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t w = __ballot_sync(0xffffffffu, (qu >> j) & 1);
+      if (lane == 0) pl[j * W + i] = w;
+    }
+  }
+  sq = warp_sum_int(sq);
+  if (lane == 0) qparams[pair] = make_float4(vl, delta, nq2, __int_as_float(sq));
+}
+
+// ---------------------------------------------------------------------------
+// First bound (Section 3.3.3): lists in probe order give the first
+// max(1024, n_sel) candidates; the bound is the n_sel-th smallest of their
+// orderable estimates (all ones when the query has fewer than n_sel).
+// ---------------------------------------------------------------------------
+template <int NW4>
+__global__ void __launch_bounds__(256)
+bound_kernel(const int32_t* __restrict__ probe_ids, const int32_t* __restrict__ nprobe,
+             int npmax, const int32_t* __restrict__ nsel,
+             const float4* __restrict__ qparams, const uint32_t* __restrict__ planes,
+             const int64_t* __restrict__ offsets, const uint8_t* __restrict__ codes,
+             const float2* __restrict__ fac, int dp, uint32_t* __restrict__ bound,
+             const int32_t* __restrict__ no_prune) {
+  constexpr int W = 4 * NW4;
+  __shared__ uint32_t s_keys[kMaxSelect];
+  __shared__ __align__(16) uint32_t s_pl[4 * W];
+  __shared__ int hist[256];
+  __shared__ uint32_t bc[2];
+  const int64_t q = blockIdx.x;
+  const int n_sel = nsel[q];
+  if (*no_prune || n_sel <= 0) {
+    if (threadIdx.x == 0) bound[q] = kU32Max;
+    return;
+  }
+  const int cap1 = max(kBoundCandidates, n_sel);
+  int taken = 0;
+  for (int p = 0; p < nprobe[q] && taken < cap1; ++p) {
+    const int64_t pair = q * npmax + p;
+    const int c = probe_ids[pair];
+    const int64_t lo = offsets[c];
+    const int m = (int)min(offsets[c + 1] - lo, (int64_t)(cap1 - taken));
+    for (int i = threadIdx.x; i < 4 * W; i += blockDim.x) s_pl[i] = planes[pair * 4 * W + i];
+    __syncthreads();
+    const float4 qp = qparams[pair];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const uint4* cp = reinterpret_cast<const uint4*>(codes + (lo + i) * (dp / 8));
+      s_keys[taken + i] = orderable(estimate_code<NW4>(cp, fac[lo + i], s_pl, qp, dp));
+    }
+    taken += m;
+    __syncthreads();
+  }
+  uint32_t tau = kU32Max;
+  if (taken >= n_sel) tau = block_radix_select_u32(s_keys, taken, n_sel, hist, bc);
+  if (threadIdx.x == 0) bound[q] = tau;
+}
+
+// ---------------------------------------------------------------------------
+// Plain scan: one block per (query, probed list) -- the query-level schedule
+// of Section 3.3.1. Candidates at or below the query's bound are appended to
+// its candidate buffer.
+// ---------------------------------------------------------------------------
+template <int NW4>
+__global__ void __launch_bounds__(128)
+scan_plain_kernel(const int32_t* __restrict__ probe_ids, const int32_t* __restrict__ nprobe,
+                  int npmax, const float4* __restrict__ qparams,
+                  const uint32_t* __restrict__ planes, const int64_t* __restrict__ offsets,
+                  const uint8_t* __restrict__ codes, const float2* __restrict__ fac,
+                  const uint32_t* __restrict__ ids, int dp, const uint32_t* __restrict__ bound,
+                  int32_t* __restrict__ counts, uint64_t* __restrict__ cand, int64_t cap,
+                  int32_t* err) {
+  constexpr int W = 4 * NW4;
+  __shared__ __align__(16) uint32_t s_pl[4 * W];
+  const int64_t pair = blockIdx.x;
+  const int64_t q = pair / npmax;
+  const int p = (int)(pair % npmax);
+  if (p >= nprobe[q]) return;
+  for (int i = threadIdx.x; i < 4 * W; i += blockDim.x) s_pl[i] = planes[pair * 4 * W + i];
+  __syncthreads();
+  const float4 qp = qparams[pair];
+  const int c = probe_ids[pair];
+  const int64_t lo = offsets[c], hi = offsets[c + 1];
+  const uint32_t tau = bound[q];
+  const int lane = threadIdx.x & 31;
+  for (int64_t s0 = lo; s0 < hi; s0 += blockDim.x) {
+    const int64_t s = s0 + threadIdx.x;
+    bool pass = false;
+    float d = 0.0f;
+    if (s < hi) {
+      const uint4* cp = reinterpret_cast<const uint4*>(codes + s * (dp / 8));
+      d = estimate_code<NW4>(cp, fac[s], s_pl, qp, dp);
+      pass = orderable(d) <= tau;
+    }
+    append_candidates(pass, d, s, ids, counts + q, cand + q * cap, cap, lane, err);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Grouped scan: the work list. Pairs (query, probe) are grouped by list; a
+// work item is (list, first vector, first pair, pairs) with at most
+// kGroupVectors vectors and group_pairs_for(D_p) pairs. Items cross query boundaries,
+// so one persistent launch stays balanced over skewed list lengths.
+// ---------------------------------------------------------------------------
+__global__ void list_count_kernel(const int32_t* __restrict__ probe_ids,
+                                  const int32_t* __restrict__ nprobe, int npmax, int64_t nq,
+                                  int32_t* __restrict__ list_count) {
+  const int64_t pair = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pair >= nq * npmax) return;
+  if ((int)(pair % npmax) >= nprobe[pair / npmax]) return;
+  atomicAdd(&list_count[probe_ids[pair]], 1);
+}
+
+// One block: exclusive scan of list_count into list_off (nlist + 1) and of
+// the per-list item counts into item_off (nlist + 1); total items to
+// work_count[1].
+__global__ void list_scan_kernel(const int32_t* __restrict__ list_count,
+                                 const int64_t* __restrict__ offsets, int nlist, int gv, int gp,
+                                 int32_t* __restrict__ list_off, int32_t* __restrict__ item_off,
+                                 int32_t* __restrict__ work_count) {
+  __shared__ int64_t part_a[1024], part_b[1024];
+  const int t = threadIdx.x, T = blockDim.x;
+  const int chunk = (nlist + T - 1) / T;
+  const int lo = min(nlist, t * chunk), hi = min(nlist, lo + chunk);
+  int64_t sa = 0, sb = 0;
+  for (int l = lo; l < hi; ++l) {
+    const int cnt = list_count[l];
+    const int64_t len = offsets[l + 1] - offsets[l];
+    sa += cnt;
+    if (cnt > 0 && len > 0) sb += ((len + gv - 1) / gv) * ((cnt + gp - 1) / gp);
+  }
+  part_a[t] = sa;
+  part_b[t] = sb;
+  __syncthreads();
+  if (t == 0) {
+    int64_t ra = 0, rb = 0;
+    for (int i = 0; i < T; ++i) {
+      const int64_t va = part_a[i], vb = part_b[i];
+      part_a[i] = ra;
+      part_b[i] = rb;
+      ra += va;
+      rb += vb;
+    }
+    list_off[nlist] = (int32_t)ra;
+    item_off[nlist] = (int32_t)rb;
+    work_count[0] = 0;
+    work_count[1] = (int32_t)rb;
+  }
+  __syncthreads();
+  int64_t ra = part_a[t], rb = part_b[t];
+  for (int l = lo; l < hi; ++l) {
+    const int cnt = list_count[l];
+    const int64_t len = offsets[l + 1] - offsets[l];
+    list_off[l] = (int32_t)ra;
+    item_off[l] = (int32_t)rb;
+    ra += cnt;
+    if (cnt > 0 && len > 0) rb += ((len + gv - 1) / gv) * ((cnt + gp - 1) / gp);
+  }
+}
+
+__global__ void list_fill_kernel(const int32_t* __restrict__ probe_ids,
+                                 const int32_t* __restrict__ nprobe, int npmax, int64_t nq,
+                                 const int32_t* __restrict__ list_off,
+                                 int32_t* __restrict__ list_fill,
+                                 int32_t* __restrict__ list_pairs) {
+  const int64_t pair = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pair >= nq * npmax) return;
+  if ((int)(pair % npmax) >= nprobe[pair / npmax]) return;
+  const int l = probe_ids[pair];
+  const int pos = list_off[l] + atomicAdd(&list_fill[l], 1);
+  list_pairs[pos] = (int32_t)pair;
+}
+
+__global__ void items_kernel(const int32_t* __restrict__ list_count,
+                             const int32_t* __restrict__ list_off,
+                             const int32_t* __restrict__ item_off,
+                             const int64_t* __restrict__ offsets, int nlist, int gv, int gp,
+                             int4* __restrict__ work, int64_t max_items, int32_t* err) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= nlist) return;
+  const int cnt = list_count[l];
+  const int64_t len = offsets[l + 1] - offsets[l];
+  if (cnt == 0 || len == 0) return;
+  int64_t pos = item_off[l];
+  for (int64_t v = 0; v < len; v += gv)
+    for (int g = 0; g < cnt; g += gp) {
+      if (pos >= max_items) {
+        flag_error(err, kErrCandidateOverflow);
+        return;
+      }
+      work[pos++] = make_int4(l, (int)v, list_off[l] + g, min(gp, cnt - g));
+    }
+}
+
+// Grouped scan: each thread holds one vector's code in registers and runs
+// the estimator for every pair of the item (planes broadcast from shared
+// memory); blocks take items from a global counter until none are left.
+template <int NW4>
+__global__ void __launch_bounds__(kGroupVectors)
+scan_grouped_kernel(const int4* __restrict__ work, int32_t* __restrict__ work_count,
+                    const int32_t* __restrict__ list_pairs, int npmax,
+                    const float4* __restrict__ qparams, const uint32_t* __restrict__ planes,
+                    const int64_t* __restrict__ offsets, const uint8_t* __restrict__ codes,
+                    const float2* __restrict__ fac, const uint32_t* __restrict__ ids, int dp,
+                    const uint32_t* __restrict__ bound, int32_t* __restrict__ counts,
+                    uint64_t* __restrict__ cand, int64_t cap, int64_t max_items,
+                    int32_t* err) {
+  constexpr int W = 4 * NW4;
+  constexpr int GP = GroupPairs<NW4>::value;
+  __shared__ __align__(16) uint32_t s_pl[GP][4 * W];
+  __shared__ float4 s_qp[GP];
+  __shared__ uint32_t s_tau[GP];
+  __shared__ int32_t s_q[GP];
+  __shared__ int s_item;
+  const int lane = threadIdx.x & 31;
+  const int total = (int)min((int64_t)work_count[1], max_items);
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(&work_count[0], 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= total) break;
+    const int4 w = work[it];
+    const int l = w.x, np = w.w;
+    for (int i = threadIdx.x; i < np * 4 * W; i += blockDim.x) {
+      const int g = i / (4 * W), k = i % (4 * W);
+      s_pl[g][k] = planes[(int64_t)list_pairs[w.z + g] * 4 * W + k];
+    }
+    for (int g = threadIdx.x; g < np; g += blockDim.x) {
+      const int pair = list_pairs[w.z + g];
+      const int q = pair / npmax;
+      s_qp[g] = qparams[pair];
+      s_q[g] = q;
+      s_tau[g] = bound[q];
+    }
+    __syncthreads();
+    const int64_t lo = offsets[l] + w.y;
+    const int64_t hi = min(offsets[l + 1], lo + kGroupVectors);
+    const int64_t s = lo + threadIdx.x;
+    const bool valid = s < hi;
+    uint4 code[NW4];
+    float2 f = make_float2(0.0f, 0.0f);
+    int pc = 0;
+    if (valid) {
+      const uint4* cp = reinterpret_cast<const uint4*>(codes + s * (dp / 8));
+#pragma unroll
+      for (int i = 0; i < NW4; ++i) {
+        code[i] = __ldg(cp + i);
+        pc += __popc(code[i].x) + __popc(code[i].y) + __popc(code[i].z) + __popc(code[i].w);
+      }
+      f = fac[s];
+    } else {
+#pragma unroll
+      for (int i = 0; i < NW4; ++i) code[i] = make_uint4(0, 0, 0, 0);
+    }
+    for (int g = 0; g < np; ++g) {
+      float d = 0.0f;
+      bool pass = false;
+      if (valid) {
+        d = estimate_regs<NW4>(code, pc, f, s_pl[g], s_qp[g], dp);
+        pass = orderable(d) <= s_tau[g];
+      }
+      const int q = s_q[g];
+      append_candidates(pass, d, s, ids, counts + q, cand + (int64_t)q * cap, cap, lane, err);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Exact re-rank (Section 3.3.4): float32 distances to the raw vectors in the
+// 32-lane order, then the k smallest (distance, id); or, without re-rank,
+// the selected estimates themselves.
+// ---------------------------------------------------------------------------
+template <typename RawT>
+__global__ void __launch_bounds__(256)
+rerank_kernel(const uint64_t* __restrict__ sel, int nsel_max, const int32_t* __restrict__ nsel,
+              const int32_t* __restrict__ kq, const int32_t* __restrict__ rerank_on,
+              const RawT* __restrict__ raw, const float* __restrict__ q, int dim,
+              int k_stride, int64_t* __restrict__ out_ids, float* __restrict__ out_d) {
+  extern __shared__ uint64_t s_keys[];
+  const int64_t row = blockIdx.x;
+  const int n_sel = nsel[row];
+  const int k = kq[row];
+  const uint64_t* sr = sel + row * nsel_max;
+  const float inf = __int_as_float(0x7f800000);
+  if (!rerank_on[row]) {
+    for (int j = threadIdx.x; j < k_stride; j += blockDim.x) {
+      const uint64_t key = (j < k && j < n_sel) ? sr[j] : kU64Max;
+      out_ids[row * k_stride + j] = (key == kU64Max) ? -1 : (int64_t)(uint32_t)key;
+      out_d[row * k_stride + j] = (key == kU64Max) ? inf : from_orderable((uint32_t)(key >> 32));
+    }
+    return;
+  }
+  const int m = next_pow2(max(n_sel, 1));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const float* qr = q + row * dim;
+  for (int i = warp; i < m; i += nw) {
+    const uint64_t key = (i < n_sel) ? sr[i] : kU64Max;
+    if (key == kU64Max) {
+      if (lane == 0) s_keys[i] = kU64Max;
+      continue;
+    }
+    const uint32_t id = (uint32_t)key;
+    const RawT* xr = raw + (int64_t)id * dim;
+    float acc = 0.0f;
+    for (int d = lane; d < dim; d += 32) {
+      const float df = __fsub_rn((float)xr[d], qr[d]);
+      acc = __fadd_rn(acc, __fmul_rn(df, df));
+    }
+    const float dist = lane_tree_sum(acc);
+    if (lane == 0) s_keys[i] = make_key(dist, id);
+  }
+  __syncthreads();
+  block_bitonic_sort(s_keys, m);
+  for (int j = threadIdx.x; j < k_stride; j += blockDim.x) {
+    const uint64_t key = (j < k) ? s_keys[j] : kU64Max;
+    out_ids[row * k_stride + j] = (key == kU64Max) ? -1 : (int64_t)(uint32_t)key;
+    out_d[row * k_stride + j] = (key == kU64Max) ? inf : from_orderable((uint32_t)(key >> 32));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct Layout {
+  size_t off = 0;
+  template <typename T>
+  size_t take(T** field, int64_t count) {
+    const size_t o = off;
+    off += align_up(sizeof(T) * (size_t)std::max<int64_t>(count, 1));
+    *field = reinterpret_cast<T*>(o);  // offset for now; rebased after allocation
+    return o;
+  }
+};
+
+template <typename T>
+void rebase(T*& p, char* base) {
+  p = reinterpret_cast<T*>(base + reinterpret_cast<size_t>(p));
+}
+
+// Items of a list: ceil(L / S) * ceil(cnt / G) <= (L/S + 1)(cnt/G + 1); summed
+// over lists, sum L*cnt <= nq * cap, sum L = n, sum cnt = pairs.
+int64_t max_items_bound(const rq_index* ix, const SearchShape& sh, int64_t cap) {
+  const int64_t pairs = sh.nq * sh.npmax;
+  const int64_t gp = group_pairs_for(ix->dp);
+  return sh.nq * cap / ((int64_t)kGroupVectors * gp) + ix->n / kGroupVectors + pairs / gp +
+         2 * (int64_t)ix->nlist + 16;
+}
+
+rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, Workspace& ws) {
+  const int64_t nq = sh.nq, np = sh.npmax;
+  const int W = ix->dp / 32;
+  ws.cap = std::max<int64_t>(1, ix->top_len_prefix[std::min(np, (int64_t)ix->nlist)]);
+  Layout L;
+  L.take(&ws.q, nq * ix->dim);
+  L.take(&ws.qrot, nq * ix->dp);
+  L.take(&ws.pkeys, nq * ix->nlist);
+  L.take(&ws.probe_ids, nq * np);
+  L.take(&ws.probe_d, nq * np);
+  L.take(&ws.qparams, nq * np);
+  L.take(&ws.planes, nq * np * 4 * W);
+  L.take(&ws.bound, nq);
+  L.take(&ws.counts, nq);
+  L.take(&ws.cand, nq * ws.cap);
+  L.take(&ws.sel, nq * sh.nsel_max);
+  L.take(&ws.nprobe, nq);
+  L.take(&ws.kq, nq);
+  L.take(&ws.nsel, nq);
+  L.take(&ws.rerank_on, nq + 1);  // last entry: the no-prune flag
+  L.take(&ws.out_ids, nq * sh.k_stride);
+  L.take(&ws.out_d, nq * sh.k_stride);
+  if (sh.mode != RQ_SCAN_PLAIN) {
+    ws.max_items = max_items_bound(ix, sh, ws.cap);
+    L.take(&ws.list_count, ix->nlist);
+    L.take(&ws.list_off, ix->nlist + 1);
+    L.take(&ws.list_pairs, nq * np);
+    L.take(&ws.list_fill, ix->nlist + 1);  // last entry unused (item_off scratch below)
+    L.take(&ws.work_count, 2 * (ix->nlist + 1) + 2);
+    L.take(&ws.work, ws.max_items);
+  }
+  ws.bytes = L.off;
+  (void)st;
+  cudaError_t e = cudaMalloc(&ws.base, ws.bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ws.base = nullptr;
+    return fail(RQ_ERR_OOM, "search workspace of " + std::to_string(ws.bytes) + " bytes");
+  }
+  char* b = static_cast<char*>(ws.base);
+  rebase(ws.q, b);
+  rebase(ws.qrot, b);
+  rebase(ws.pkeys, b);
+  rebase(ws.probe_ids, b);
+  rebase(ws.probe_d, b);
+  rebase(ws.qparams, b);
+  rebase(ws.planes, b);
+  rebase(ws.bound, b);
+  rebase(ws.counts, b);
+  rebase(ws.cand, b);
+  rebase(ws.sel, b);
+  rebase(ws.nprobe, b);
+  rebase(ws.kq, b);
+  rebase(ws.nsel, b);
+  rebase(ws.rerank_on, b);
+  rebase(ws.out_ids, b);
+  rebase(ws.out_d, b);
+  if (sh.mode != RQ_SCAN_PLAIN) {
+    rebase(ws.list_count, b);
+    rebase(ws.list_off, b);
+    rebase(ws.list_pairs, b);
+    rebase(ws.list_fill, b);
+    rebase(ws.work_count, b);
+    rebase(ws.work, b);
+  }
+  return RQ_OK;
+}
+
+template <int NW4>
+rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws,
+                              cudaStream_t st) {
+  const int64_t nq = sh.nq;
+  const int np = sh.npmax;
+  const int dp = ix->dp;
+  const int64_t pairs = nq * np;
+  quantize_kernel<NW4><<<blocks_for(pairs * 32, 256), 256, 0, st>>>(
+      ws.qrot, ws.probe_ids, ws.nprobe, np, nq, ix->cR, dp, ws.qparams, ws.planes, ix->d_err);
+  bound_kernel<NW4><<<(unsigned)nq, 256, 0, st>>>(ws.probe_ids, ws.nprobe, np, ws.nsel, ws.qparams,
+                                                 ws.planes, ix->offsets, ix->codes, ix->fac, dp,
+                                                 ws.bound, ws.rerank_on + nq);
+  RQ_CUDA(cudaMemsetAsync(ws.counts, 0, sizeof(int32_t) * nq, st));
+  if (sh.mode == RQ_SCAN_PLAIN) {
+    scan_plain_kernel<NW4><<<(unsigned)pairs, 128, 0, st>>>(
+        ws.probe_ids, ws.nprobe, np, ws.qparams, ws.planes, ix->offsets, ix->codes, ix->fac,
+        ix->ids, dp, ws.bound, ws.counts, ws.cand, ws.cap, ix->d_err);
+  } else {
+    int32_t* item_off = ws.work_count + 2;
+    RQ_CUDA(cudaMemsetAsync(ws.list_count, 0, sizeof(int32_t) * ix->nlist, st));
+    RQ_CUDA(cudaMemsetAsync(ws.list_fill, 0, sizeof(int32_t) * ix->nlist, st));
+    list_count_kernel<<<blocks_for(pairs, 256), 256, 0, st>>>(ws.probe_ids, ws.nprobe, np, nq,
+                                                             ws.list_count);
+    const int gp = group_pairs_for(dp);
+    list_scan_kernel<<<1, 1024, 0, st>>>(ws.list_count, ix->offsets, ix->nlist, kGroupVectors,
+                                         gp, ws.list_off, item_off, ws.work_count);
+    list_fill_kernel<<<blocks_for(pairs, 256), 256, 0, st>>>(ws.probe_ids, ws.nprobe, np, nq,
+                                                            ws.list_off, ws.list_fill,
+                                                            ws.list_pairs);
+    items_kernel<<<blocks_for(ix->nlist, 128), 128, 0, st>>>(
+        ws.list_count, ws.list_off, item_off, ix->offsets, ix->nlist, kGroupVectors, gp,
+        ws.work, ws.max_items, ix->d_err);
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
+    if (sh.mode == RQ_SCAN_MMA) {
+      RQ_TRY(launch_scan_mma(ix, sh, ws, st, sms));
+    } else {
+      scan_grouped_kernel<NW4><<<(unsigned)(sms * 8), kGroupVectors, 0, st>>>(
+          ws.work, ws.work_count, ws.list_pairs, np, ws.qparams, ws.planes, ix->offsets,
+          ix->codes, ix->fac, ix->ids, dp, ws.bound, ws.counts, ws.cand, ws.cap, ws.max_items,
+          ix->d_err);
+    }
+  }
+  return RQ_OK;
+}
+
+rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cudaStream_t st) {
+  const int64_t nq = sh.nq;
+  const int np = sh.npmax;
+  const int dp = ix->dp;
+  // 1. rotation, once per query
+  rotate_kernel<<<dim3(blocks_for(nq, 64), dp / 64), 256, 0, st>>>(ws.q, nq, ix->dim, ix->P32, dp,
+                                                                  ws.qrot);
+  // 2. centroid ranking and probe selection
+  pair_dist_kernel<1><<<dim3(blocks_for(nq, 64), blocks_for(ix->nlist, 64)), 256, 0, st>>>(
+      ws.qrot, nq, ix->cR, ix->nlist, dp, nullptr, nullptr, ws.pkeys);
+  {
+    const int m = next_pow2_host(std::min<int64_t>(ix->nlist, kMaxSelect));
+    const size_t smem = sizeof(uint64_t) * std::max(m, next_pow2_host(np));
+    select_rows_kernel<1><<<(unsigned)nq, 1024, smem, st>>>(
+        ws.pkeys, ix->nlist, nullptr, ix->nlist, ix->nlist, nullptr, np, nullptr, np,
+        ws.probe_ids, ws.probe_d, ix->d_err);
+  }
+  // 3-4. quantisation, bound, scan
+  switch (dp / 128) {
+    case 1: RQ_TRY(enqueue_scan_stages<1>(ix, sh, ws, st)); break;
+    case 2: RQ_TRY(enqueue_scan_stages<2>(ix, sh, ws, st)); break;
+    case 3: RQ_TRY(enqueue_scan_stages<3>(ix, sh, ws, st)); break;
+    case 4: RQ_TRY(enqueue_scan_stages<4>(ix, sh, ws, st)); break;
+    case 5: RQ_TRY(enqueue_scan_stages<5>(ix, sh, ws, st)); break;
+    case 6: RQ_TRY(enqueue_scan_stages<6>(ix, sh, ws, st)); break;
+    case 7: RQ_TRY(enqueue_scan_stages<7>(ix, sh, ws, st)); break;
+    case 8: RQ_TRY(enqueue_scan_stages<8>(ix, sh, ws, st)); break;
+    case 12: RQ_TRY(enqueue_scan_stages<12>(ix, sh, ws, st)); break;
+    case 16: RQ_TRY(enqueue_scan_stages<16>(ix, sh, ws, st)); break;
+    default:
+      return fail(RQ_ERR_NOT_IMPLEMENTED, "padded dimension " + std::to_string(dp) +
+                                              " has no scan kernel (built: 128..1024, 1536, 2048)");
+  }
+  // 5. candidate selection
+  {
+    const size_t smem = sizeof(uint64_t) * kMaxSelect;
+    select_rows_kernel<0><<<(unsigned)nq, 1024, smem, st>>>(
+        ws.cand, ws.cap, ws.counts, 0, ws.cap, ws.nsel, 0, ws.sel, sh.nsel_max, nullptr, nullptr,
+        ix->d_err);
+  }
+  // 6. exact re-rank
+  {
+    const size_t smem = sizeof(uint64_t) * next_pow2_host(sh.nsel_max);
+    if (ix->raw_dtype == RQ_U8)
+      rerank_kernel<uint8_t><<<(unsigned)nq, 256, smem, st>>>(
+          ws.sel, sh.nsel_max, ws.nsel, ws.kq, ws.rerank_on, static_cast<const uint8_t*>(ix->raw),
+          ws.q, ix->dim, sh.k_stride, ws.out_ids, ws.out_d);
+    else
+      rerank_kernel<float><<<(unsigned)nq, 256, smem, st>>>(
+          ws.sel, sh.nsel_max, ws.nsel, ws.kq, ws.rerank_on, static_cast<const float*>(ix->raw),
+          ws.q, ix->dim, sh.k_stride, ws.out_ids, ws.out_d);
+  }
+  RQ_CUDA(cudaGetLastError());
+  return RQ_OK;
+}
+
+void destroy_plan(Plan* p) {
+  if (p->params_ready) {
+    cudaEventSynchronize(p->params_ready);
+    cudaEventDestroy(p->params_ready);
+  }
+  if (p->h_params) cudaFreeHost(p->h_params);
+  if (p->graph) cudaGraphExecDestroy(p->graph);
+  // cudaFree waits for the device, so the workspace is idle when released
+  // (the stream it was used on may no longer exist).
+  if (p->ws.base) cudaFree(p->ws.base);
+  p->graph = nullptr;
+  p->ws.base = nullptr;
+  p->h_params = nullptr;
+  p->params_ready = nullptr;
+}
+
+constexpr size_t kMaxPlans = 8;
+
+rq_status get_plan(rq_index* ix, cudaStream_t st, const SearchShape& sh, Plan** out) {
+  std::lock_guard<std::mutex> lk(ix->mu);
+  auto key = std::make_pair(st, sh);
+  auto it = ix->plans.find(key);
+  if (it != ix->plans.end()) {
+    it->second->last_use = ++ix->plan_clock;
+    *out = it->second.get();
+    return RQ_OK;
+  }
+  if (ix->plans.size() >= kMaxPlans) {
+    auto victim = ix->plans.begin();
+    for (auto j = ix->plans.begin(); j != ix->plans.end(); ++j)
+      if (j->second->last_use < victim->second->last_use) victim = j;
+    destroy_plan(victim->second.get());
+    ix->plans.erase(victim);
+  }
+  auto p = std::make_unique<Plan>();
+  p->shape = sh;
+  p->stream = st;
+  RQ_TRY(alloc_workspace(ix, sh, st, p->ws));
+  if (cudaMallocHost(&p->h_params, sizeof(int32_t) * (4 * sh.nq + 1)) != cudaSuccess) {
+    cudaGetLastError();
+    destroy_plan(p.get());
+    return fail(RQ_ERR_OOM, "pinned parameter buffer");
+  }
+  RQ_CUDA(cudaEventCreateWithFlags(&p->params_ready, cudaEventDisableTiming));
+  p->last_use = ++ix->plan_clock;
+  *out = p.get();
+  ix->plans[key] = std::move(p);
+  return RQ_OK;
+}
+
+}  // namespace
+
+int next_pow2_host(int64_t v) {
+  int m = 1;
+  while (m < v) m <<= 1;
+  return m;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Time each scan mode on the sample batch (warm-up run, then the best of three
+// CUDA-event timings) and keep the fastest for RQ_SCAN_AUTO. The choice is
+// stored per (n, dim, nlist, nq, nprobe, n_rerank) in a text cache file.
+rq_status autotune(rq_index* ix, const float* queries, int64_t nq, int nprobe, int n_rerank,
+                   const char* cache_path) {
+  if (!ix || !queries || nq < 1) return fail(RQ_ERR_INVALID_ARG, "bad autotune arguments");
+  char key[160];
+  snprintf(key, sizeof(key), "n=%lld dim=%d nlist=%d nq=%lld nprobe=%d n_rerank=%d",
+           (long long)ix->n, ix->dim, ix->nlist, (long long)nq, nprobe, n_rerank);
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "r")) {
+      char line[256];
+      int found = -1;
+      while (fgets(line, sizeof(line), f)) {
+        const size_t kl = strlen(key);
+        if (strncmp(line, key, kl) == 0 && line[kl] == ' ') {
+          int m = 0;
+          if (sscanf(line + kl, " mode=%d", &m) == 1) found = m;
+        }
+      }
+      fclose(f);
+      if (found >= RQ_SCAN_PLAIN && found <= RQ_SCAN_MMA) {
+        ix->auto_mode.store(found);
+        return RQ_OK;
+      }
+    }
+  }
+  const int k = n_rerank > 0 ? std::min(10, n_rerank) : 10;
+  int64_t* d_ids = nullptr;
+  float* d_d = nullptr;
+  float* d_q = nullptr;
+  RQ_CUDA(cudaMalloc(&d_ids, sizeof(int64_t) * nq * k));
+  RQ_CUDA(cudaMalloc(&d_d, sizeof(float) * nq * k));
+  RQ_CUDA(cudaMalloc(&d_q, sizeof(float) * nq * ix->dim));
+  RQ_CUDA(cudaMemcpy(d_q, queries, sizeof(float) * nq * ix->dim, cudaMemcpyDefault));
+  cudaStream_t st;
+  RQ_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  std::vector<int32_t> a(nq, nprobe), b(nq, k), c(nq, n_rerank);
+  int best_mode = RQ_SCAN_GROUPED;
+  float best_ms = 1e30f;
+  std::string report;
+  rq_status s = RQ_OK;
+  for (int mode = RQ_SCAN_PLAIN; mode <= RQ_SCAN_MMA && s == RQ_OK; ++mode) {
+    if (mode == RQ_SCAN_MMA && !mma_supported(ix)) continue;
+    rq_search_opts o{};
+    o.scan_mode = mode;
+    o.use_graph = 1;
+    float best = 1e30f;
+    for (int rep = 0; rep < 4 && s == RQ_OK; ++rep) {
+      cudaEventRecord(e0, st);
+      s = search_run(ix, d_q, nq, a.data(), b.data(), c.data(), k, d_ids, d_d, &o, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) best = std::min(best, ms);
+    }
+    report += " mode" + std::to_string(mode) + "_ms=" + std::to_string(best);
+    if (best < best_ms) {
+      best_ms = best;
+      best_mode = mode;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lk(ix->mu);
+    for (auto it = ix->plans.begin(); it != ix->plans.end();) {
+      if (it->first.first == st) {
+        destroy_plan(it->second.get());
+        it = ix->plans.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+  cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
+  cudaFree(d_ids);
+  cudaFree(d_d);
+  cudaFree(d_q);
+  if (s != RQ_OK) return s;
+  ix->auto_mode.store(best_mode);
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "a")) {
+      fprintf(f, "%s mode=%d%s\n", key, best_mode, report.c_str());
+      fclose(f);
+    }
+  }
+  return RQ_OK;
+}
+
+void free_plans(rq_index* ix) {
+  std::lock_guard<std::mutex> lk(ix->mu);
+  for (auto& kv : ix->plans) destroy_plan(kv.second.get());
+  ix->plans.clear();
+}
+
+rq_status search_run(rq_index* ix, const float* queries, int64_t nq, const int32_t* nprobe,
+                     const int32_t* k, const int32_t* n_rerank, int k_stride, int64_t* out_ids,
+                     float* out_dist, const rq_search_opts* opts, cudaStream_t st) {
+  if (!ix) return fail(RQ_ERR_INVALID_ARG, "index is NULL");
+  if (nq < 0) return fail(RQ_ERR_INVALID_ARG, "nq < 0");
+  if (nq == 0) return RQ_OK;
+  if (!queries || !out_ids || !out_dist || !nprobe || !k || !n_rerank)
+    return fail(RQ_ERR_INVALID_ARG, "NULL pointer argument");
+  if (nq > (int64_t)1 << 24) return fail(RQ_ERR_INVALID_ARG, "nq above 2^24 in one call");
+  const int pmax_allowed = std::min(ix->nlist, kMaxSelect);
+  std::vector<int32_t> h_np(nq), h_k(nq), h_ns(nq), h_rr(nq + 1);
+  int npmax = 0, nsel_max = 0, kmax = 0;
+  for (int64_t i = 0; i < nq; ++i) {
+    const int a = nprobe[i], b = k[i], c = n_rerank[i];
+    if (a < 1 || a > pmax_allowed)
+      return fail(RQ_ERR_INVALID_ARG, "nprobe " + std::to_string(a) + " outside [1, " +
+                                          std::to_string(pmax_allowed) + "]");
+    if (b < 1 || b > kMaxSelect) return fail(RQ_ERR_INVALID_ARG, "k outside [1, 4096]");
+    if (c != 0 && (c < b || c > kMaxSelect))
+      return fail(RQ_ERR_INVALID_ARG, "n_rerank must be 0 or in [k, 4096]");
+    h_np[i] = a;
+    h_k[i] = b;
+    h_ns[i] = c > 0 ? c : b;
+    h_rr[i] = c > 0 ? 1 : 0;
+    npmax = std::max(npmax, a);
+    nsel_max = std::max(nsel_max, h_ns[i]);
+    kmax = std::max(kmax, b);
+  }
+  if (k_stride < kmax) return fail(RQ_ERR_INVALID_ARG, "k_stride below the largest k");
+  int mode = opts ? opts->scan_mode : RQ_SCAN_AUTO;
+  if (mode == RQ_SCAN_AUTO) mode = ix->auto_mode.load();
+  if (mode < RQ_SCAN_PLAIN || mode > RQ_SCAN_MMA)
+    return fail(RQ_ERR_INVALID_ARG, "unknown scan mode");
+  if (mode == RQ_SCAN_MMA && !mma_supported(ix)) mode = RQ_SCAN_GROUPED;
+  const bool no_prune = opts && opts->no_prune;
+  h_rr[nq] = no_prune ? 1 : 0;
+  const bool use_graph = opts && opts->use_graph;
+  const rq_search_dump* dump = opts ? opts->dump : nullptr;
+
+  const bool q_dev = is_device_ptr(queries);
+  if (!q_dev) {
+    for (int64_t i = 0; i < nq * ix->dim; ++i)
+      if (!std::isfinite(queries[i])) return fail(RQ_ERR_INVALID_ARG, "non-finite query value");
+  }
+  const bool ids_dev = is_device_ptr(out_ids), d_dev = is_device_ptr(out_dist);
+
+  SearchShape sh{nq, npmax, nsel_max, k_stride, mode, no_prune ? 1 : 0};
+  cudaStream_t run_st = st;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  if (use_graph && st == nullptr) {
+    std::lock_guard<std::mutex> lk(ix->mu);
+    if (!ix->graph_stream) RQ_CUDA(cudaStreamCreateWithFlags(&ix->graph_stream, cudaStreamNonBlocking));
+    run_st = ix->graph_stream;
+  }
+  Plan* plan = nullptr;
+  RQ_TRY(get_plan(ix, run_st, sh, &plan));
+  Workspace& ws = plan->ws;
+  if (run_st != st) {
+    RQ_CUDA(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+    RQ_CUDA(cudaEventRecord(ev_in, st));
+    RQ_CUDA(cudaStreamWaitEvent(run_st, ev_in, 0));
+  }
+  // Per-query parameters go through the plan's pinned buffer; the previous
+  // call's copy out of it must have run before it is overwritten.
+  RQ_CUDA(cudaEventSynchronize(plan->params_ready));
+  int32_t* hp = plan->h_params;
+  std::memcpy(hp, h_np.data(), sizeof(int32_t) * nq);
+  std::memcpy(hp + nq, h_k.data(), sizeof(int32_t) * nq);
+  std::memcpy(hp + 2 * nq, h_ns.data(), sizeof(int32_t) * nq);
+  std::memcpy(hp + 3 * nq, h_rr.data(), sizeof(int32_t) * (nq + 1));
+  RQ_CUDA(cudaMemcpyAsync(ws.nprobe, hp, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, run_st));
+  RQ_CUDA(cudaMemcpyAsync(ws.kq, hp + nq, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, run_st));
+  RQ_CUDA(cudaMemcpyAsync(ws.nsel, hp + 2 * nq, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, run_st));
+  RQ_CUDA(cudaMemcpyAsync(ws.rerank_on, hp + 3 * nq, sizeof(int32_t) * (nq + 1),
+                          cudaMemcpyHostToDevice, run_st));
+  RQ_CUDA(cudaEventRecord(plan->params_ready, run_st));
+  RQ_CUDA(cudaMemcpyAsync(ws.q, queries, sizeof(float) * nq * ix->dim, cudaMemcpyDefault, run_st));
+  if (use_graph) {
+    if (!plan->graph) {
+      cudaGraph_t g = nullptr;
+      RQ_CUDA(cudaStreamBeginCapture(run_st, cudaStreamCaptureModeThreadLocal));
+      rq_status s = enqueue_search(ix, sh, ws, run_st);
+      cudaError_t e = cudaStreamEndCapture(run_st, &g);
+      if (s != RQ_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+      e = cudaGraphInstantiate(&plan->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+    }
+    RQ_CUDA(cudaGraphLaunch(plan->graph, run_st));
+  } else {
+    RQ_TRY(enqueue_search(ix, sh, ws, run_st));
+  }
+  RQ_CUDA(cudaMemcpyAsync(out_ids, ws.out_ids, sizeof(int64_t) * nq * k_stride, cudaMemcpyDefault,
+                          run_st));
+  RQ_CUDA(cudaMemcpyAsync(out_dist, ws.out_d, sizeof(float) * nq * k_stride, cudaMemcpyDefault,
+                          run_st));
+  if (dump) {
+    const int W = ix->dp / 32;
+    auto cp = [&](void* dst, const void* src, size_t bytes) -> rq_status {
+      if (dst) RQ_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, run_st));
+      return RQ_OK;
+    };
+    RQ_TRY(cp(dump->qrot, ws.qrot, sizeof(float) * nq * ix->dp));
+    RQ_TRY(cp(dump->probe_ids, ws.probe_ids, sizeof(int32_t) * nq * npmax));
+    RQ_TRY(cp(dump->probe_dist, ws.probe_d, sizeof(float) * nq * npmax));
+    RQ_TRY(cp(dump->qparams, ws.qparams, sizeof(float4) * nq * npmax));
+    RQ_TRY(cp(dump->planes, ws.planes, sizeof(uint32_t) * nq * npmax * 4 * W));
+    RQ_TRY(cp(dump->bound, ws.bound, sizeof(uint32_t) * nq));
+    RQ_TRY(cp(dump->selected, ws.sel, sizeof(uint64_t) * nq * nsel_max));
+    RQ_TRY(cp(dump->n_candidates, ws.counts, sizeof(int32_t) * nq));
+  }
+  if (run_st != st) {
+    RQ_CUDA(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+    RQ_CUDA(cudaEventRecord(ev_out, run_st));
+    RQ_CUDA(cudaStreamWaitEvent(st, ev_out, 0));
+    cudaEventDestroy(ev_in);
+    cudaEventDestroy(ev_out);
+  }
+  // Host outputs (or host queries read by a pending copy) need the stream
+  // to finish before the call returns; device-only calls stay asynchronous.
+  if (!ids_dev || !d_dev || !q_dev) RQ_CUDA(cudaStreamSynchronize(st));
+  return RQ_OK;
+}
+
+}  // namespace rq

@@ -115,8 +115,10 @@ def test_kmeans_init_is_smallest_keys():
     rows = np.arange(n)
     got = R.kmeans_init(seed, n, rows, nlist)
     keys = philox.row_keys(seed, philox.STREAM_KMEANS_INIT, n)
-    ref = sorted(range(n), key=lambda i: (int(keys[i]), i))[:nlist]
+    w0 = philox.stream_block(seed, philox.STREAM_KMEANS_INIT, np.arange(n))[:, 0]
+    ref = sorted(range(n), key=lambda i: (int(w0[i]), i))[:nlist]
     assert list(got) == ref
+    assert np.array_equal(keys >> np.uint64(32), w0.astype(np.uint64))
     assert len(set(got.tolist())) == nlist
 
 
