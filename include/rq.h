@@ -101,6 +101,19 @@ typedef struct rq_search_dump {
   int32_t* n_candidates; /* nq: candidates that survived pruning */
 } rq_search_dump;
 
+/* Stages of one search, for rq_search_opts.stage_ms. */
+typedef enum rq_stage {
+  RQ_STAGE_ROTATE = 0,   /* q' = P^T q */
+  RQ_STAGE_PROBE = 1,    /* centroid distances + nprobe selection */
+  RQ_STAGE_QUANTIZE = 2, /* residuals to 4-bit planes */
+  RQ_STAGE_BOUND = 3,    /* first pruning bound per query */
+  RQ_STAGE_WORKLIST = 4, /* grouping of (query, list) pairs (grouped modes) */
+  RQ_STAGE_SCAN = 5,     /* the code scan */
+  RQ_STAGE_SELECT = 6,   /* candidate selection */
+  RQ_STAGE_RERANK = 7,   /* exact re-rank */
+  RQ_STAGE_COUNT = 8
+} rq_stage;
+
 typedef struct rq_search_opts {
   int32_t scan_mode;     /* rq_scan_mode (default AUTO) */
   int32_t no_prune;      /* 1: keep every candidate (no bound); default 0 */
@@ -108,6 +121,10 @@ typedef struct rq_search_opts {
                             cached per (stream, shape); default 0 */
   int32_t reserved;
   rq_search_dump* dump;  /* NULL, or buffers for the intermediates */
+  float* stage_ms;       /* NULL, or host array of RQ_STAGE_COUNT floats that
+                            receives each stage's device time (CUDA events on
+                            the search stream; the call then waits for the
+                            device and does not use a graph) */
 } rq_search_opts;
 
 typedef struct rq_stats {
@@ -120,6 +137,8 @@ typedef struct rq_stats {
   int64_t max_list;      /* longest list */
   int64_t index_bytes;   /* device bytes of codes, factors, ids, centroids, P */
   int64_t raw_bytes;     /* device bytes of the raw vectors kept for re-rank */
+  int32_t auto_scan_mode; /* the scan mode RQ_SCAN_AUTO resolves to */
+  int32_t reserved;
 } rq_stats;
 
 /* Read-only device pointers into an index (valid until rq_free). Lists are

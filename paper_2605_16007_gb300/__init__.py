@@ -46,14 +46,18 @@ class SearchDump(C.Structure):
 class SearchOpts(C.Structure):
     _fields_ = [("scan_mode", C.c_int32), ("no_prune", C.c_int32),
                 ("use_graph", C.c_int32), ("reserved", C.c_int32),
-                ("dump", C.POINTER(SearchDump))]
+                ("dump", C.POINTER(SearchDump)), ("stage_ms", C.POINTER(C.c_float))]
+
+
+STAGES = ("rotate", "probe", "quantize", "bound", "worklist", "scan", "select", "rerank")
 
 
 class Stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("dim", C.c_int32), ("dim_pad", C.c_int32),
                 ("nlist", C.c_int32), ("code_bytes", C.c_int32),
                 ("min_list", C.c_int64), ("max_list", C.c_int64),
-                ("index_bytes", C.c_int64), ("raw_bytes", C.c_int64)]
+                ("index_bytes", C.c_int64), ("raw_bytes", C.c_int64),
+                ("auto_scan_mode", C.c_int32), ("reserved", C.c_int32)]
 
 
 class IndexView(C.Structure):
@@ -212,8 +216,10 @@ def rq_version() -> int:
     return lib().rq_version()
 
 
-def _opts(scan_mode, no_prune, use_graph, dump):
-    o = SearchOpts(scan_mode, int(no_prune), int(use_graph), 0, None)
+def _opts(scan_mode, no_prune, use_graph, dump, stage_ms=None):
+    o = SearchOpts(scan_mode, int(no_prune), int(use_graph), 0, None, None)
+    if stage_ms is not None:
+        o.stage_ms = stage_ms
     if dump is not None:
         d = SearchDump(*[_ptr(dump.get(f)) if dump.get(f) is not None else None
                          for f, _ in SearchDump._fields_])
@@ -231,15 +237,19 @@ class Index:
     # -- search ----------------------------------------------------------
     def rq_search(self, queries, nprobe: int, k: int, n_rerank: int, out_ids=None,
                   out_dist=None, scan_mode: int = RQ_SCAN_AUTO, no_prune: bool = False,
-                  use_graph: bool = False, dump=None, stream=None):
+                  use_graph: bool = False, dump=None, stream=None, stage_times=None):
+        """stage_times: a dict that receives each stage's device time (ms)."""
         nq = _shape(queries)[0]
         if out_ids is None:
             out_ids = np.empty((nq, k), np.int64)
             out_dist = np.empty((nq, k), np.float32)
-        o = _opts(scan_mode, no_prune, use_graph, dump)
+        ms = (C.c_float * len(STAGES))() if stage_times is not None else None
+        o = _opts(scan_mode, no_prune, use_graph, dump, ms)
         _check(lib().rq_search(self.h, _ptr(queries), nq, nprobe, k, n_rerank,
                                _ptr(out_ids), _ptr(out_dist), C.byref(o),
                                _stream_ptr(stream)))
+        if stage_times is not None:
+            stage_times.update({name: ms[i] for i, name in enumerate(STAGES)})
         return out_ids, out_dist
 
     search = rq_search
@@ -281,6 +291,13 @@ class Index:
         v = IndexView()
         _check(lib().rq_get_view(self.h, C.byref(v)))
         return {f: getattr(v, f) for f, _ in IndexView._fields_}
+
+    def offsets(self) -> np.ndarray:
+        """List offsets (nlist + 1) copied to the host."""
+        v = self.view()
+        out = np.empty(v["nlist"] + 1, np.int64)
+        memcpy_d2h(out, v["offsets"])
+        return out
 
     def to_host(self) -> dict:
         """Host copies (numpy) of the index arrays, read through the view."""

@@ -277,7 +277,6 @@ void CUDART_CB batch_done_cb(void* p) {
   delete m;
 }
 
-int64_t round_up(int64_t v, int64_t m) { return ((v + m - 1) / m) * m; }
 int pow2_at_least(int v) {
   int m = 1;
   while (m < v) m <<= 1;
@@ -318,8 +317,8 @@ rq_status slot_reserve(Slot& sl, int64_t nq_elems, int64_t out_elems) {
 }
 
 // Merge the slot's requests into one mixed batch, padded with placeholder
-// queries to a multiple of 64 (at least one placeholder) so that few distinct
-// shapes occur; one placeholder carries the rounded-up nprobe / selection / k
+// queries to a power of two of at least 64 (at least one placeholder) so that
+// few distinct shapes occur; one placeholder carries the rounded-up nprobe / selection / k
 // so that the shape does not depend on the exact mix.
 rq_status launch_batch(rq_server* s, Slot& sl, int npb, int nsb, int kb) {
   rq_index* ix = s->ix;
@@ -411,7 +410,7 @@ void server_loop(rq_server* s) {
         if (!take.empty() && nq2 > s->opts.max_batch) break;
         const int np2 = std::max(npm, r->nprobe), ns2 = std::max(nsm, r->nrr > 0 ? r->nrr : r->k),
                   k2 = std::max(km, r->k);
-        const int64_t b2 = round_up(nq2 + 1, 64);
+        const int64_t b2 = std::max(64, pow2_at_least((int)nq2 + 1));
         const int npb = std::min(pow2_at_least(np2), std::min(s->ix->nlist, kMaxSelect));
         const int nsb = std::min(pow2_at_least(ns2), kMaxSelect);
         const size_t need = batch_bytes(s->ix, b2, npb, nsb, pow2_at_least(k2));
@@ -427,7 +426,7 @@ void server_loop(rq_server* s) {
       if (!take.empty()) {
         sl.reqs = std::move(take);
         sl.nq = nq;
-        sl.bucket = round_up(nq + 1, 64);
+        sl.bucket = std::max(64, pow2_at_least((int)nq + 1));
         const int npb = std::min(pow2_at_least(npm), std::min(s->ix->nlist, kMaxSelect));
         const int nsb = std::min(pow2_at_least(nsm), kMaxSelect);
         const int kb = std::min(pow2_at_least(km), nsb);
@@ -591,6 +590,8 @@ rq_status rq_get_stats(const rq_index* ix, rq_stats* out) {
   out->index_bytes = n * (ix->C + 4 + 4 + 8 + 4 + 4) + (int64_t)ix->nlist * (ix->dim + ix->dp) * 4 +
                      (int64_t)(ix->nlist + 1) * 8 + (int64_t)ix->dp * ix->dp * 12;
   out->raw_bytes = n * ix->dim * (ix->raw_dtype == RQ_U8 ? 1 : 4);
+  out->auto_scan_mode = ix->auto_mode.load();
+  out->reserved = 0;
   return RQ_OK;
 }
 

@@ -24,6 +24,16 @@ inline unsigned blocks_for(int64_t n, int per) {
   return (unsigned)std::max<int64_t>(1, (n + per - 1) / per);
 }
 
+// Optional CUDA events at stage boundaries: ev[s] marks the start of stage s,
+// ev[RQ_STAGE_COUNT] the end of the search.
+struct StageTimer {
+  cudaEvent_t ev[RQ_STAGE_COUNT + 1] = {};
+  bool on = false;
+  void mark(int stage, cudaStream_t st) {
+    if (on) cudaEventRecord(ev[stage], st);
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Rotation: q' = q P[:D, :] (float32, one multiply-add per term).
 // ---------------------------------------------------------------------------
@@ -605,18 +615,22 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
 
 template <int NW4>
 rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws,
-                              cudaStream_t st) {
+                              cudaStream_t st, StageTimer& tm) {
   const int64_t nq = sh.nq;
   const int np = sh.npmax;
   const int dp = ix->dp;
   const int64_t pairs = nq * np;
+  tm.mark(RQ_STAGE_QUANTIZE, st);
   quantize_kernel<NW4><<<blocks_for(pairs * 32, 256), 256, 0, st>>>(
       ws.qrot, ws.probe_ids, ws.nprobe, np, nq, ix->cR, dp, ws.qparams, ws.planes, ix->d_err);
+  tm.mark(RQ_STAGE_BOUND, st);
   bound_kernel<NW4><<<(unsigned)nq, 256, 0, st>>>(ws.probe_ids, ws.nprobe, np, ws.nsel, ws.qparams,
                                                  ws.planes, ix->offsets, ix->codes, ix->fac, dp,
                                                  ws.bound, ws.rerank_on + nq);
   RQ_CUDA(cudaMemsetAsync(ws.counts, 0, sizeof(int32_t) * nq, st));
+  tm.mark(RQ_STAGE_WORKLIST, st);
   if (sh.mode == RQ_SCAN_PLAIN) {
+    tm.mark(RQ_STAGE_SCAN, st);
     scan_plain_kernel<NW4><<<(unsigned)pairs, 128, 0, st>>>(
         ws.probe_ids, ws.nprobe, np, ws.qparams, ws.planes, ix->offsets, ix->codes, ix->fac,
         ix->ids, dp, ws.bound, ws.counts, ws.cand, ws.cap, ix->d_err);
@@ -637,6 +651,7 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
         ws.work, ws.max_items, ix->d_err);
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
+    tm.mark(RQ_STAGE_SCAN, st);
     if (sh.mode == RQ_SCAN_MMA) {
       RQ_TRY(launch_scan_mma(ix, sh, ws, st, sms));
     } else {
@@ -649,14 +664,17 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
   return RQ_OK;
 }
 
-rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cudaStream_t st) {
+rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cudaStream_t st,
+                         StageTimer& tm) {
   const int64_t nq = sh.nq;
   const int np = sh.npmax;
   const int dp = ix->dp;
   // 1. rotation, once per query
+  tm.mark(RQ_STAGE_ROTATE, st);
   rotate_kernel<<<dim3(blocks_for(nq, 64), dp / 64), 256, 0, st>>>(ws.q, nq, ix->dim, ix->P32, dp,
                                                                   ws.qrot);
   // 2. centroid ranking and probe selection
+  tm.mark(RQ_STAGE_PROBE, st);
   pair_dist_kernel<1><<<dim3(blocks_for(nq, 64), blocks_for(ix->nlist, 64)), 256, 0, st>>>(
       ws.qrot, nq, ix->cR, ix->nlist, dp, nullptr, nullptr, ws.pkeys);
   {
@@ -668,21 +686,22 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
   }
   // 3-4. quantisation, bound, scan
   switch (dp / 128) {
-    case 1: RQ_TRY(enqueue_scan_stages<1>(ix, sh, ws, st)); break;
-    case 2: RQ_TRY(enqueue_scan_stages<2>(ix, sh, ws, st)); break;
-    case 3: RQ_TRY(enqueue_scan_stages<3>(ix, sh, ws, st)); break;
-    case 4: RQ_TRY(enqueue_scan_stages<4>(ix, sh, ws, st)); break;
-    case 5: RQ_TRY(enqueue_scan_stages<5>(ix, sh, ws, st)); break;
-    case 6: RQ_TRY(enqueue_scan_stages<6>(ix, sh, ws, st)); break;
-    case 7: RQ_TRY(enqueue_scan_stages<7>(ix, sh, ws, st)); break;
-    case 8: RQ_TRY(enqueue_scan_stages<8>(ix, sh, ws, st)); break;
-    case 12: RQ_TRY(enqueue_scan_stages<12>(ix, sh, ws, st)); break;
-    case 16: RQ_TRY(enqueue_scan_stages<16>(ix, sh, ws, st)); break;
+    case 1: RQ_TRY(enqueue_scan_stages<1>(ix, sh, ws, st, tm)); break;
+    case 2: RQ_TRY(enqueue_scan_stages<2>(ix, sh, ws, st, tm)); break;
+    case 3: RQ_TRY(enqueue_scan_stages<3>(ix, sh, ws, st, tm)); break;
+    case 4: RQ_TRY(enqueue_scan_stages<4>(ix, sh, ws, st, tm)); break;
+    case 5: RQ_TRY(enqueue_scan_stages<5>(ix, sh, ws, st, tm)); break;
+    case 6: RQ_TRY(enqueue_scan_stages<6>(ix, sh, ws, st, tm)); break;
+    case 7: RQ_TRY(enqueue_scan_stages<7>(ix, sh, ws, st, tm)); break;
+    case 8: RQ_TRY(enqueue_scan_stages<8>(ix, sh, ws, st, tm)); break;
+    case 12: RQ_TRY(enqueue_scan_stages<12>(ix, sh, ws, st, tm)); break;
+    case 16: RQ_TRY(enqueue_scan_stages<16>(ix, sh, ws, st, tm)); break;
     default:
       return fail(RQ_ERR_NOT_IMPLEMENTED, "padded dimension " + std::to_string(dp) +
                                               " has no scan kernel (built: 128..1024, 1536, 2048)");
   }
   // 5. candidate selection
+  tm.mark(RQ_STAGE_SELECT, st);
   {
     const size_t smem = sizeof(uint64_t) * kMaxSelect;
     select_rows_kernel<0><<<(unsigned)nq, 1024, smem, st>>>(
@@ -690,6 +709,7 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
         ix->d_err);
   }
   // 6. exact re-rank
+  tm.mark(RQ_STAGE_RERANK, st);
   {
     const size_t smem = sizeof(uint64_t) * next_pow2_host(sh.nsel_max);
     if (ix->raw_dtype == RQ_U8)
@@ -701,6 +721,7 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
           ws.sel, sh.nsel_max, ws.nsel, ws.kq, ws.rerank_on, static_cast<const float*>(ix->raw),
           ws.q, ix->dim, sh.k_stride, ws.out_ids, ws.out_d);
   }
+  tm.mark(RQ_STAGE_COUNT, st);
   RQ_CUDA(cudaGetLastError());
   return RQ_OK;
 }
@@ -721,7 +742,7 @@ void destroy_plan(Plan* p) {
   p->params_ready = nullptr;
 }
 
-constexpr size_t kMaxPlans = 8;
+constexpr size_t kMaxPlans = 64;
 
 rq_status get_plan(rq_index* ix, cudaStream_t st, const SearchShape& sh, Plan** out) {
   std::lock_guard<std::mutex> lk(ix->mu);
@@ -909,8 +930,21 @@ rq_status search_run(rq_index* ix, const float* queries, int64_t nq, const int32
   if (mode == RQ_SCAN_MMA && !mma_supported(ix)) mode = RQ_SCAN_GROUPED;
   const bool no_prune = opts && opts->no_prune;
   h_rr[nq] = no_prune ? 1 : 0;
-  const bool use_graph = opts && opts->use_graph;
+  float* stage_ms = opts ? opts->stage_ms : nullptr;
+  const bool use_graph = opts && opts->use_graph && !stage_ms;
   const rq_search_dump* dump = opts ? opts->dump : nullptr;
+  StageTimer tm;
+  struct EventsGuard {
+    StageTimer& t;
+    ~EventsGuard() {
+      for (auto& e : t.ev)
+        if (e) cudaEventDestroy(e);
+    }
+  } guard{tm};
+  if (stage_ms) {
+    for (auto& e : tm.ev) RQ_CUDA(cudaEventCreate(&e));
+    tm.on = true;
+  }
 
   const bool q_dev = is_device_ptr(queries);
   if (!q_dev) {
@@ -954,7 +988,7 @@ rq_status search_run(rq_index* ix, const float* queries, int64_t nq, const int32
     if (!plan->graph) {
       cudaGraph_t g = nullptr;
       RQ_CUDA(cudaStreamBeginCapture(run_st, cudaStreamCaptureModeThreadLocal));
-      rq_status s = enqueue_search(ix, sh, ws, run_st);
+      rq_status s = enqueue_search(ix, sh, ws, run_st, tm);
       cudaError_t e = cudaStreamEndCapture(run_st, &g);
       if (s != RQ_OK) {
         if (g) cudaGraphDestroy(g);
@@ -967,7 +1001,7 @@ rq_status search_run(rq_index* ix, const float* queries, int64_t nq, const int32
     }
     RQ_CUDA(cudaGraphLaunch(plan->graph, run_st));
   } else {
-    RQ_TRY(enqueue_search(ix, sh, ws, run_st));
+    RQ_TRY(enqueue_search(ix, sh, ws, run_st, tm));
   }
   RQ_CUDA(cudaMemcpyAsync(out_ids, ws.out_ids, sizeof(int64_t) * nq * k_stride, cudaMemcpyDefault,
                           run_st));
@@ -998,6 +1032,14 @@ rq_status search_run(rq_index* ix, const float* queries, int64_t nq, const int32
   // Host outputs (or host queries read by a pending copy) need the stream
   // to finish before the call returns; device-only calls stay asynchronous.
   if (!ids_dev || !d_dev || !q_dev) RQ_CUDA(cudaStreamSynchronize(st));
+  if (stage_ms) {
+    RQ_CUDA(cudaEventSynchronize(tm.ev[RQ_STAGE_COUNT]));
+    for (int i = 0; i < RQ_STAGE_COUNT; ++i) {
+      float ms = 0.0f;
+      RQ_CUDA(cudaEventElapsedTime(&ms, tm.ev[i], tm.ev[i + 1]));
+      stage_ms[i] = ms;
+    }
+  }
   return RQ_OK;
 }
 
