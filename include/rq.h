@@ -259,6 +259,34 @@ RQ_API void rq_free(rq_index* ix);
  * Synchronises the device. */
 RQ_API rq_status rq_device_error(rq_index* ix, int32_t* code);
 
+/* rq_probe_static -- the query rotation and centroid ranking of rq_search
+ * (q' = P^T q, then the nprobe lists of smallest ||q' - P^T c||^2, ties by
+ * list id), for callers that cannot allocate device memory when they search:
+ * code inside a CUDA stream capture it does not own, processes whose
+ * framework owns all device memory through its own allocator, and serving
+ * threads that cannot take the device synchronisation of cudaMalloc/cudaFree.
+ * The paper has no counterpart: it is an interface variant of Phase 1 of the
+ * search, which the paper runs as a batch on the NPU.
+ * It allocates nothing: its scratch (the rotated queries and the distance
+ * keys) is one fixed 16 MiB array in device memory that every GPU loading the
+ * library holds until the process exits. A call needs
+ * nq * (4 * D_p + 8 * nlist) bytes of it (each part rounded up to 256 bytes);
+ * larger calls are rejected with RQ_ERR_INVALID_ARG.
+ *   queries   device, nq x dim float32.
+ *   out_ids   device, nq x nprobe int32: lists in ascending (distance, id).
+ *   out_dist  device, nq x nprobe float32: their squared distances.
+ *   stream    cudaStream_t or NULL; the call only enqueues work.
+ * The results equal the probe stage of rq_search bit for bit. The first call
+ * on a device looks up the array's device address; make that first call
+ * before any stream capture. All calls share the one array and it keeps the
+ * last call's contents (nothing in it needs to start at zero): calls whose
+ * work overlaps on the GPU (on different streams, or from different threads)
+ * race on it and must be serialised by the caller.
+ * Errors: INVALID_ARG (NULL or host pointers, sizes), CUDA. */
+RQ_API rq_status rq_probe_static(const rq_index* ix, const float* queries, int64_t nq,
+                                 int32_t nprobe, int32_t* out_ids, float* out_dist,
+                                 void* stream);
+
 RQ_API const char* rq_status_str(rq_status s);
 RQ_API const char* rq_last_error(void);
 RQ_API int32_t rq_version(void);

@@ -110,6 +110,8 @@ _SIGS = {
     "rq_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_int32,
                           C.POINTER(C.c_double)]),
     "rq_server_destroy": (None, [C.c_void_p]),
+    "rq_probe_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
+                                  C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -280,6 +282,15 @@ class Index:
                                  n_rerank, cache_path.encode() if cache_path else None))
 
     autotune = rq_autotune
+
+    def rq_probe_static(self, queries, nprobe: int, out_ids, out_dist, stream=None):
+        """Rotation + centroid ranking without any allocation (device arrays
+        only); see rq_probe_static in include/rq.h."""
+        _check(lib().rq_probe_static(self.h, _ptr(queries), _shape(queries)[0], nprobe,
+                                     _ptr(out_ids), _ptr(out_dist), _stream_ptr(stream)))
+        return out_ids, out_dist
+
+    probe_static = rq_probe_static
 
     # -- inspection --------------------------------------------------------
     def stats(self) -> dict:

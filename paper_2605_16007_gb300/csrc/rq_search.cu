@@ -1044,3 +1044,88 @@ rq_status search_run(rq_index* ix, const float* queries, int64_t nq, const int32
 }
 
 }  // namespace rq
+
+// ===========================================================================
+// Allocation-free variant of the query rotation and centroid ranking.
+//
+// Some callers cannot allocate device memory at the moment they search: code
+// running inside a CUDA stream capture owned by someone else (an allocation
+// there fails or becomes part of their graph), processes whose framework
+// hands all device memory to its own caching allocator, and latency-critical
+// serving threads that cannot afford the implicit device synchronisation of
+// cudaMalloc / cudaFree. For them, rq_probe_static keeps its scratch (the
+// rotated queries and the distance keys) in one fixed array in device memory
+// that exists for as long as the library is loaded.
+// ===========================================================================
+namespace rq {
+namespace {
+
+constexpr size_t kProbeScratchBytes = size_t(16) << 20;  // 16 MiB per device
+constexpr int kMaxDevices = 64;
+
+// Every GPU that loads the library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_probe_scratch[kProbeScratchBytes];
+
+// Device address of g_probe_scratch, looked up once per device. In host code
+// the symbol itself is only a host-side stand-in and must never be passed to
+// a kernel.
+void* g_probe_scratch_addr[kMaxDevices] = {};
+std::mutex g_probe_scratch_mu;
+
+rq_status probe_scratch_address(int device, void** out) {
+  if (device < 0 || device >= kMaxDevices)
+    return fail(RQ_ERR_INVALID_ARG, "device ordinal above the supported range");
+  std::lock_guard<std::mutex> lk(g_probe_scratch_mu);
+  if (!g_probe_scratch_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_probe_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_probe_scratch)", __FILE__, __LINE__);
+    g_probe_scratch_addr[device] = p;
+  }
+  *out = g_probe_scratch_addr[device];
+  return RQ_OK;
+}
+
+}  // namespace
+}  // namespace rq
+
+extern "C" rq_status rq_probe_static(const rq_index* ix, const float* queries, int64_t nq,
+                                     int32_t nprobe, int32_t* out_ids, float* out_dist,
+                                     void* stream) {
+  using namespace rq;
+  if (!ix || !queries || !out_ids || !out_dist)
+    return fail(RQ_ERR_INVALID_ARG, "NULL pointer argument");
+  if (nq < 1) return fail(RQ_ERR_INVALID_ARG, "nq < 1");
+  if (nprobe < 1 || nprobe > std::min(ix->nlist, kMaxSelect))
+    return fail(RQ_ERR_INVALID_ARG, "nprobe outside [1, min(nlist, 4096)]");
+  const size_t q_bytes = align_up(sizeof(float) * (size_t)nq * ix->dp);
+  const size_t k_bytes = align_up(sizeof(uint64_t) * (size_t)nq * ix->nlist);
+  if (q_bytes + k_bytes > kProbeScratchBytes)
+    return fail(RQ_ERR_INVALID_ARG,
+                "rq_probe_static: nq x (4 D_p + 8 nlist) bytes = " +
+                    std::to_string(q_bytes + k_bytes) + " exceeds its fixed scratch of " +
+                    std::to_string(kProbeScratchBytes) + " bytes; use fewer queries per call");
+  if (!is_device_ptr(queries) || !is_device_ptr(out_ids) || !is_device_ptr(out_dist))
+    return fail(RQ_ERR_INVALID_ARG, "rq_probe_static takes device pointers only");
+  int dev = -1;
+  RQ_CUDA(cudaGetDevice(&dev));
+  if (dev != ix->device)
+    return fail(RQ_ERR_INVALID_ARG, "the current device is not the index's device");
+  void* scratch = nullptr;
+  RQ_TRY(probe_scratch_address(dev, &scratch));
+  float* qrot = static_cast<float*>(scratch);
+  uint64_t* pkeys = reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + q_bytes);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int dp = ix->dp;
+  rotate_kernel<<<dim3(blocks_for(nq, 64), dp / 64), 256, 0, st>>>(queries, nq, ix->dim, ix->P32,
+                                                                  dp, qrot);
+  pair_dist_kernel<1><<<dim3(blocks_for(nq, 64), blocks_for(ix->nlist, 64)), 256, 0, st>>>(
+      qrot, nq, ix->cR, ix->nlist, dp, nullptr, nullptr, pkeys);
+  const int m = next_pow2_host(std::min<int64_t>(ix->nlist, kMaxSelect));
+  const size_t smem = sizeof(uint64_t) * std::max(m, next_pow2_host(nprobe));
+  select_rows_kernel<1><<<(unsigned)nq, 1024, smem, st>>>(pkeys, ix->nlist, nullptr, ix->nlist,
+                                                         ix->nlist, nullptr, nprobe, nullptr,
+                                                         nprobe, out_ids, out_dist, ix->d_err);
+  RQ_CUDA(cudaGetLastError());
+  return RQ_OK;
+}
