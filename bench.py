@@ -77,6 +77,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--profile", action="store_true",
+                    help="only build and run --warmup + --steps batches per scan mode "
+                         "(for ncu captures); prints the stage times")
     return ap.parse_args()
 
 
@@ -321,6 +324,8 @@ def run_ours(args, rank, world, local, pg):
 
     stages = stage_profile(rq.RQ_SCAN_AUTO)
     stages_plain = stage_profile(rq.RQ_SCAN_PLAIN)
+    stages_grouped = stage_profile(rq.RQ_SCAN_GROUPED)
+    stages_mma = stage_profile(rq.RQ_SCAN_MMA)
     # scanned (query, vector) pairs per batch from the probe lists
     h_off = ix.offsets()
     pid = torch.empty((bs, nprobe), dtype=torch.int32, device=dev)
@@ -412,6 +417,8 @@ def run_ours(args, rank, world, local, pg):
         "roofline": roofline,
         "stage_ms": {a: round(b, 4) for a, b in stages.items()},
         "stage_ms_plain": {a: round(b, 4) for a, b in stages_plain.items()},
+        "stage_ms_grouped": {a: round(b, 4) for a, b in stages_grouped.items()},
+        "stage_ms_mma": {a: round(b, 4) for a, b in stages_mma.items()},
         "build_s": round(build_s, 3),
         "index": {"bytes": st["index_bytes"], "min_list": st["min_list"],
                   "max_list": st["max_list"]},
@@ -538,8 +545,39 @@ def run_reference(args, rank, world, local, pg):
     return res
 
 
+def run_profile(args):
+    """Build, then warm-up + steps batches of each scan mode, nothing else."""
+    import torch
+
+    import paper_2605_16007_gb300 as rq
+
+    rq.build()
+    dev = torch.device("cuda", 0)
+    wl = W.WORKLOADS[WORKLOAD]
+    n = args.n or wl["n"]
+    x_dev = torch.from_numpy(wl["mix"].base(n)).to(dev)
+    q_dev = torch.from_numpy(wl["mix"].queries(wl["batch"])).to(dev)
+    ix = rq.rq_build(x_dev, wl["nlist"], seed=0, kmeans_iters=wl["iters"])
+    nprobe = args.nprobe or 16
+    k, nrr = wl["k"], wl["n_rerank"]
+    ids = torch.empty((q_dev.shape[0], k), dtype=torch.int64, device=dev)
+    dist = torch.empty((q_dev.shape[0], k), dtype=torch.float32, device=dev)
+    out = {}
+    for mode, name in ((rq.RQ_SCAN_PLAIN, "plain"), (rq.RQ_SCAN_GROUPED, "grouped"),
+                       (rq.RQ_SCAN_MMA, "mma")):
+        for _ in range(args.warmup + args.steps):
+            st = {}
+            ix.search(q_dev, nprobe, k, nrr, out_ids=ids, out_dist=dist, scan_mode=mode,
+                      stage_times=st)
+        out[name] = {a: round(b, 4) for a, b in st.items()}
+    print(json.dumps({"profile": out, "nprobe": nprobe}), flush=True)
+
+
 def main():
     args = parse()
+    if args.profile:
+        run_profile(args)
+        return
     rank, world, local, pg = dist_setup(args.gpus)
     if args.impl == "reference":
         if rank != 0:

@@ -97,7 +97,9 @@ typedef struct rq_search_dump {
   float* qparams;        /* nq x nprobe_max x 4: vl, delta, nq2, Sq (as float) */
   uint8_t* planes;       /* nq x nprobe_max x 4 x (D_p/8): query bit-planes */
   uint32_t* bound;       /* nq: pruning bound (orderable distance) */
-  uint64_t* selected;    /* nq x nsel_max: selected (distance, id) keys */
+  uint64_t* selected;    /* nq x nsel_max: the selected (estimate, id) keys,
+                            padded with all ones; ascending when n_rerank
+                            is 0, otherwise in no particular order */
   int32_t* n_candidates; /* nq: candidates that survived pruning */
 } rq_search_dump;
 
@@ -109,8 +111,8 @@ typedef enum rq_stage {
   RQ_STAGE_BOUND = 3,    /* first pruning bound per query */
   RQ_STAGE_WORKLIST = 4, /* grouping of (query, list) pairs (grouped modes) */
   RQ_STAGE_SCAN = 5,     /* the code scan */
-  RQ_STAGE_SELECT = 6,   /* candidate selection */
-  RQ_STAGE_RERANK = 7,   /* exact re-rank */
+  RQ_STAGE_SELECT = 6,   /* candidate selection fused with the exact re-rank */
+  RQ_STAGE_RERANK = 7,   /* (runs inside RQ_STAGE_SELECT; reads 0) */
   RQ_STAGE_COUNT = 8
 } rq_stage;
 

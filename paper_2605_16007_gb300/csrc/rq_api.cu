@@ -62,13 +62,14 @@ rq_status check_finite_device(const float* d, int64_t n, const char* what) {
 }
 
 void free_index_arrays(rq_index* ix) {
-  void* ptrs[] = {ix->P,     ix->P32, ix->centroids, ix->cR,     ix->offsets, ix->codes,
-                  ix->r,     ix->alpha, ix->fac,     ix->ids,    ix->assign,  ix->raw,
-                  ix->d_err};
+  void* ptrs[] = {ix->P,     ix->P32,   ix->centroids, ix->cR,     ix->offsets, ix->codes,
+                  ix->r,     ix->alpha, ix->fac,       ix->ids,    ix->assign,  ix->raw,
+                  ix->d_err, ix->items};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ix->P = nullptr;
   ix->raw = nullptr;
+  ix->items = nullptr;
 }
 
 // Copies the base rows to the device: raw (kept for re-rank, in the given
@@ -704,7 +705,11 @@ rq_status rq_import(const char* path, rq_index** out) {
     free_index_arrays(ix.get());
     return s;
   }
-  finish_index_host_side(ix.get());
+  s = finish_index_host_side(ix.get());
+  if (s != RQ_OK) {
+    free_index_arrays(ix.get());
+    return s;
+  }
   if (ix->h_offsets[ix->nlist] != ix->n) {
     free_index_arrays(ix.get());
     return fail(RQ_ERR_IO, "list offsets do not cover the index");

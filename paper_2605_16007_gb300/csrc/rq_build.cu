@@ -11,6 +11,7 @@
 #include "rq_common.cuh"
 #include "rq_internal.h"
 #include "rq_pairdist.cuh"
+#include "rq_scan.cuh"
 
 namespace rq {
 namespace {
@@ -744,19 +745,30 @@ rq_status build_index(const float* d_base, const void* d_raw, rq_dtype dt,
   ix->assign = assign.release();
   ix->d_err = err.release();
   ix->raw = const_cast<void*>(d_raw);
-  finish_index_host_side(ix);
-  return RQ_OK;
+  return finish_index_host_side(ix);
 }
 
-void finish_index_host_side(rq_index* ix) {
+// Host copies of the list layout, and the static work items of the grouped
+// scans: every (list, first vector) block of kGroupVectors vectors.
+rq_status finish_index_host_side(rq_index* ix) {
   ix->h_offsets.resize(ix->nlist + 1);
-  cudaMemcpy(ix->h_offsets.data(), ix->offsets, sizeof(int64_t) * (ix->nlist + 1),
-             cudaMemcpyDeviceToHost);
+  RQ_CUDA(cudaMemcpy(ix->h_offsets.data(), ix->offsets, sizeof(int64_t) * (ix->nlist + 1),
+                     cudaMemcpyDeviceToHost));
   std::vector<int64_t> len(ix->nlist);
-  for (int l = 0; l < ix->nlist; ++l) len[l] = ix->h_offsets[l + 1] - ix->h_offsets[l];
+  std::vector<int2> items;
+  for (int l = 0; l < ix->nlist; ++l) {
+    len[l] = ix->h_offsets[l + 1] - ix->h_offsets[l];
+    for (int64_t v = 0; v < len[l]; v += kGroupVectors) items.push_back(make_int2(l, (int)v));
+  }
   std::sort(len.begin(), len.end(), std::greater<int64_t>());
   ix->top_len_prefix.assign(ix->nlist + 1, 0);
   for (int l = 0; l < ix->nlist; ++l) ix->top_len_prefix[l + 1] = ix->top_len_prefix[l] + len[l];
+  if (ix->items) cudaFree(ix->items);
+  ix->items = nullptr;
+  ix->n_items = (int)items.size();
+  RQ_CUDA(cudaMalloc(&ix->items, sizeof(int2) * std::max<size_t>(items.size(), 1)));
+  RQ_CUDA(cudaMemcpy(ix->items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
+  return RQ_OK;
 }
 
 }  // namespace rq

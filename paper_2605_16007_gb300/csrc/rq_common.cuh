@@ -187,3 +187,205 @@ __device__ inline uint32_t block_radix_select_u32(const uint32_t* keys,
 }
 
 }  // namespace rq
+
+namespace rq {
+
+// ---------------------------------------------------------------------------
+// Block-wide radix selection with 8-bit digits. All threads of the block call
+// these functions (loops run in whole rounds so that warps stay converged).
+// `hist` is 256 ints and `res` 4 ints of shared memory.
+// ---------------------------------------------------------------------------
+
+// Adds 1 to hist[d] for every active lane, one atomic per distinct digit of
+// the warp. All 32 lanes must call it.
+__device__ __forceinline__ void hist_add(int* hist, int d, bool active) {
+  const unsigned act = __ballot_sync(0xffffffffu, active);
+  if (!active) return;
+  const unsigned peers = __match_any_sync(act, d);
+  if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[d], __popc(peers));
+}
+
+// Warp 0 finds the bucket b where the running count of hist reaches `rank`
+// (1-based): res = {b, count below b, hist[b]}. rank must not exceed the
+// total count.
+__device__ __forceinline__ void find_bucket(const int* hist, int rank, int* res) {
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  int h[8];
+  int sum = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    h[i] = hist[lane * 8 + i];
+    sum += h[i];
+  }
+  int incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int excl = incl - sum;
+  const unsigned m = __ballot_sync(0xffffffffu, excl < rank && rank <= incl);
+  const int src = m ? __ffs(m) - 1 : 31;
+  if (lane == src) {
+    int cum = excl, b = 7;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (cum + h[i] >= rank) {
+        b = i;
+        break;
+      }
+      cum += h[i];
+    }
+    res[0] = lane * 8 + b;
+    res[1] = cum;
+    res[2] = h[b];
+  }
+}
+
+// Appends the active lanes' values at dst[base + rank] with one atomic per
+// warp on *counter; positions at or past `cap` are dropped.
+template <typename T>
+__device__ __forceinline__ void block_append(T* dst, int* counter, int cap, T v, bool active) {
+  const unsigned m = __ballot_sync(0xffffffffu, active);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(counter, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (active) {
+    const int pos = base + __popc(m & ((1u << lane) - 1u));
+    if (pos < cap) dst[pos] = v;
+  }
+}
+
+// The n smallest of m distinct uint64 keys at src (shared or global memory),
+// ascending in dst[0, n) and dst[n, next_pow2(n)) = all ones. Returns
+// min(n, m). dst holds next_pow2(max(n, 1)) keys of shared memory; `small`
+// holds kSelectSmall keys of shared memory. Radix passes (8-bit digits from
+// the top) narrow the bucket holding the n-th key until it has at most
+// kSelectSmall keys; the keys below it are taken whole and the bucket is
+// sorted to supply the rest.
+constexpr int kSelectSmall = 256;
+
+__device__ inline int block_select_smallest(const uint64_t* src, int m, int n, uint64_t* dst,
+                                            uint64_t* small, int* hist, int* res,
+                                            bool sorted = true) {
+  const int T = blockDim.x;
+  const int sel = min(n, m);
+  const int mp = next_pow2(max(sel, 1));
+  if (m <= n) {
+    for (int i = threadIdx.x; i < mp; i += T) dst[i] = (i < m) ? src[i] : kU64Max;
+    __syncthreads();
+    if (sorted) block_bitonic_sort(dst, mp);
+    return sel;
+  }
+  uint64_t prefix = 0, mask = 0;
+  int rank = n, cnt = m;
+  for (int shift = 56; shift >= 0 && cnt > kSelectSmall; shift -= 8) {
+    for (int i = threadIdx.x; i < 256; i += T) hist[i] = 0;
+    __syncthreads();
+    for (int base = 0; base < m; base += T) {
+      const int i = base + threadIdx.x;
+      uint64_t k = 0;
+      bool act = false;
+      if (i < m) {
+        k = src[i];
+        act = (k & mask) == prefix;
+      }
+      hist_add(hist, (int)((k >> shift) & 255), act);
+    }
+    __syncthreads();
+    find_bucket(hist, rank, res);
+    __syncthreads();
+    const int b = res[0], below = res[1];
+    cnt = res[2];
+    __syncthreads();
+    prefix |= (uint64_t)b << shift;
+    mask |= 0xFFull << shift;
+    rank -= below;
+  }
+  // Keys below the bucket all belong to the result (n - rank of them); the
+  // bucket (cnt <= kSelectSmall keys, or one key after all eight digits)
+  // gives its rank smallest.
+  if (threadIdx.x == 0) {
+    res[2] = 0;
+    res[3] = 0;
+  }
+  __syncthreads();
+  for (int base = 0; base < m; base += T) {
+    const int i = base + threadIdx.x;
+    uint64_t k = kU64Max;
+    if (i < m) k = src[i];
+    const uint64_t km = k & mask;
+    block_append(dst, &res[3], n, k, i < m && km < prefix);
+    block_append(small, &res[2], kSelectSmall, k, i < m && km == prefix);
+  }
+  __syncthreads();
+  const int nb = min(res[2], kSelectSmall);
+  const int sp = next_pow2(max(nb, 1));
+  for (int i = nb + threadIdx.x; i < sp; i += T) small[i] = kU64Max;
+  __syncthreads();
+  block_bitonic_sort(small, sp);
+  const int have = n - rank;
+  for (int i = threadIdx.x; i < rank; i += T) dst[have + i] = small[i];
+  for (int i = n + threadIdx.x; i < mp; i += T) dst[i] = kU64Max;
+  __syncthreads();
+  if (sorted) block_bitonic_sort(dst, mp);
+  return sel;
+}
+
+// The rank-th smallest (1-based) of m uint32 values in shared memory
+// (duplicates allowed): radix passes narrow the bucket holding it to at most
+// kSelectSmall values, which are then sorted. `small` holds kSelectSmall
+// uint64 of shared memory.
+__device__ inline uint32_t block_kth_u32(const uint32_t* src, int m, int rank, uint64_t* small,
+                                         int* hist, int* res) {
+  const int T = blockDim.x;
+  uint32_t prefix = 0, mask = 0;
+  int cnt = m;
+  for (int shift = 24; shift >= 0 && cnt > kSelectSmall; shift -= 8) {
+    for (int i = threadIdx.x; i < 256; i += T) hist[i] = 0;
+    __syncthreads();
+    for (int base = 0; base < m; base += T) {
+      const int i = base + threadIdx.x;
+      uint32_t k = 0;
+      bool act = false;
+      if (i < m) {
+        k = src[i];
+        act = (k & mask) == prefix;
+      }
+      hist_add(hist, (int)((k >> shift) & 255), act);
+    }
+    __syncthreads();
+    find_bucket(hist, rank, res);
+    __syncthreads();
+    const int b = res[0], below = res[1];
+    cnt = res[2];
+    __syncthreads();
+    prefix |= (uint32_t)b << shift;
+    mask |= 0xFFu << shift;
+    rank -= below;
+  }
+  if (mask == 0xFFFFFFFFu) return prefix;
+  if (threadIdx.x == 0) res[3] = 0;
+  __syncthreads();
+  for (int base = 0; base < m; base += T) {
+    const int i = base + threadIdx.x;
+    uint32_t k = 0;
+    if (i < m) k = src[i];
+    block_append(small, &res[3], kSelectSmall, (uint64_t)k, i < m && (k & mask) == prefix);
+  }
+  __syncthreads();
+  const int nb = min(res[3], kSelectSmall);
+  const int sp = next_pow2(max(nb, 1));
+  for (int i = nb + threadIdx.x; i < sp; i += T) small[i] = kU64Max;
+  __syncthreads();
+  block_bitonic_sort(small, sp);
+  const uint32_t v = (uint32_t)small[rank - 1];
+  __syncthreads();
+  return v;
+}
+
+}  // namespace rq

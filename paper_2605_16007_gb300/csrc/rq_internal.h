@@ -75,15 +75,12 @@ struct Workspace {
   int32_t* rerank_on = nullptr; // nq: 1 if n_rerank > 0
   int64_t* out_ids = nullptr;   // nq x k_stride
   float* out_d = nullptr;       // nq x k_stride
-  // grouped scan work list
+  // grouped scans: (query, probe) pairs bucketed by list
   int32_t* list_count = nullptr;  // nlist: pairs probing each list
-  int32_t* list_off = nullptr;    // nlist + 1
-  int32_t* list_pairs = nullptr;  // nq*npmax: (q*npmax+p) grouped by list
-  int32_t* list_fill = nullptr;   // nlist
-  int32_t* work_count = nullptr;  // 1 + item counters
-  int4* work = nullptr;           // work items
+  int32_t* list_pairs = nullptr;  // nlist x nq: pair ids (q * npmax + p) per list
+  int32_t* work_count = nullptr;  // work-item counter of the persistent scan
+  uint8_t* qdig = nullptr;        // nq x npmax x D_p: query digits as FP8 (MMA scan)
   int64_t cap = 0;                // candidate slots per query
-  int64_t max_items = 0;
 };
 
 struct Plan {
@@ -117,6 +114,8 @@ struct rq_index {
   int32_t* assign = nullptr;  // n (row order)
   void* raw = nullptr;        // n x dim (float or uint8)
   int32_t* d_err = nullptr;   // device error word
+  int2* items = nullptr;      // static scan items (list, first vector)
+  int n_items = 0;
   // host copies
   std::vector<int64_t> h_offsets;
   std::vector<int64_t> top_len_prefix;  // sum of the j largest list lengths
@@ -141,7 +140,7 @@ rq_status kmeans_device(const float* d_x, int64_t n, int dim, int nlist,
                         float* d_centroids);
 rq_status philox_gaussian_device(uint64_t seed, uint32_t stream, int64_t count,
                                  double* d_out);
-void finish_index_host_side(rq_index* ix);
+rq_status finish_index_host_side(rq_index* ix);
 
 // Search (rq_search.cu)
 rq_status search_run(rq_index* ix, const float* queries, int64_t nq,

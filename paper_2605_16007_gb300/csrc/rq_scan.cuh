@@ -84,6 +84,15 @@ __device__ __forceinline__ void append_candidates(bool pass, float d, int64_t s,
   }
 }
 
+// FP8 E4M3 encoding of an integer 0..15 (exact): v = 2^e (1 + m/8) with
+// e = floor(log2 v), stored as (e + 7) << 3 | m; 0 encodes as 0.
+__device__ __forceinline__ uint8_t e4m3_of_int(int v) {
+  if (v <= 0) return 0;
+  const int e = 31 - __clz(v);
+  const int m = (v << (3 - e)) & 7;
+  return (uint8_t)(((e + 7) << 3) | m);
+}
+
 // Tensor-core scan (rq_scan_mma.cu).
 bool mma_supported(const rq_index* ix);
 rq_status launch_scan_mma(rq_index* ix, const SearchShape& sh, Workspace& ws, cudaStream_t st,

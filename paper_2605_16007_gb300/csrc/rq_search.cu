@@ -24,6 +24,8 @@ inline unsigned blocks_for(int64_t n, int per) {
   return (unsigned)std::max<int64_t>(1, (n + per - 1) / per);
 }
 
+__device__ __forceinline__ int next_pow2_dev(int v) { return next_pow2(v); }
+
 // Optional CUDA events at stage boundaries: ev[s] marks the start of stage s,
 // ev[RQ_STAGE_COUNT] the end of the search.
 struct StageTimer {
@@ -155,7 +157,8 @@ __global__ void __launch_bounds__(256)
 quantize_kernel(const float* __restrict__ qrot, const int32_t* __restrict__ probe_ids,
                 const int32_t* __restrict__ nprobe, int npmax, int64_t nq,
                 const float* __restrict__ cR, int dp, float4* __restrict__ qparams,
-                uint32_t* __restrict__ planes, int32_t* err) {
+                uint32_t* __restrict__ planes, int32_t* __restrict__ list_count,
+                int32_t* __restrict__ list_pairs, uint8_t* __restrict__ qdig, int32_t* err) {
   constexpr int PER = 4 * NW4;  // values per lane (dp / 32)
   const int64_t pair = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -196,6 +199,7 @@ quantize_kernel(const float* __restrict__ qrot, const int32_t* __restrict__ prob
       qu = min(qu, 15);
     }
     sq += qu;
+    if (qdig) qdig[pair * dp + lane + 32 * i] = e4m3_of_int(qu);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const uint32_t w = __ballot_sync(0xffffffffu, (qu >> j) & 1);
@@ -203,7 +207,12 @@ quantize_kernel(const float* __restrict__ qrot, const int32_t* __restrict__ prob
     }
   }
   sq = warp_sum_int(sq);
-  if (lane == 0) qparams[pair] = make_float4(vl, delta, nq2, __int_as_float(sq));
+  if (lane == 0) {
+    qparams[pair] = make_float4(vl, delta, nq2, __int_as_float(sq));
+    // Grouped scans: the pair joins the bucket of its list (room for every
+    // query of the batch).
+    if (list_count) list_pairs[(int64_t)c * nq + atomicAdd(&list_count[c], 1)] = (int32_t)pair;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -223,7 +232,8 @@ bound_kernel(const int32_t* __restrict__ probe_ids, const int32_t* __restrict__ 
   __shared__ uint32_t s_keys[kMaxSelect];
   __shared__ __align__(16) uint32_t s_pl[4 * W];
   __shared__ int hist[256];
-  __shared__ uint32_t bc[2];
+  __shared__ int res[4];
+  __shared__ uint64_t small[kSelectSmall];
   const int64_t q = blockIdx.x;
   const int n_sel = nsel[q];
   if (*no_prune || n_sel <= 0) {
@@ -248,7 +258,7 @@ bound_kernel(const int32_t* __restrict__ probe_ids, const int32_t* __restrict__ 
     __syncthreads();
   }
   uint32_t tau = kU32Max;
-  if (taken >= n_sel) tau = block_radix_select_u32(s_keys, taken, n_sel, hist, bc);
+  if (taken >= n_sel) tau = block_kth_u32(s_keys, taken, n_sel, small, hist, res);
   if (threadIdx.x == 0) bound[q] = tau;
 }
 
@@ -298,109 +308,23 @@ scan_plain_kernel(const int32_t* __restrict__ probe_ids, const int32_t* __restri
 // kGroupVectors vectors and group_pairs_for(D_p) pairs. Items cross query boundaries,
 // so one persistent launch stays balanced over skewed list lengths.
 // ---------------------------------------------------------------------------
-__global__ void list_count_kernel(const int32_t* __restrict__ probe_ids,
-                                  const int32_t* __restrict__ nprobe, int npmax, int64_t nq,
-                                  int32_t* __restrict__ list_count) {
-  const int64_t pair = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (pair >= nq * npmax) return;
-  if ((int)(pair % npmax) >= nprobe[pair / npmax]) return;
-  atomicAdd(&list_count[probe_ids[pair]], 1);
-}
-
-// One block: exclusive scan of list_count into list_off (nlist + 1) and of
-// the per-list item counts into item_off (nlist + 1); total items to
-// work_count[1].
-__global__ void list_scan_kernel(const int32_t* __restrict__ list_count,
-                                 const int64_t* __restrict__ offsets, int nlist, int gv, int gp,
-                                 int32_t* __restrict__ list_off, int32_t* __restrict__ item_off,
-                                 int32_t* __restrict__ work_count) {
-  __shared__ int64_t part_a[1024], part_b[1024];
-  const int t = threadIdx.x, T = blockDim.x;
-  const int chunk = (nlist + T - 1) / T;
-  const int lo = min(nlist, t * chunk), hi = min(nlist, lo + chunk);
-  int64_t sa = 0, sb = 0;
-  for (int l = lo; l < hi; ++l) {
-    const int cnt = list_count[l];
-    const int64_t len = offsets[l + 1] - offsets[l];
-    sa += cnt;
-    if (cnt > 0 && len > 0) sb += ((len + gv - 1) / gv) * ((cnt + gp - 1) / gp);
-  }
-  part_a[t] = sa;
-  part_b[t] = sb;
-  __syncthreads();
-  if (t == 0) {
-    int64_t ra = 0, rb = 0;
-    for (int i = 0; i < T; ++i) {
-      const int64_t va = part_a[i], vb = part_b[i];
-      part_a[i] = ra;
-      part_b[i] = rb;
-      ra += va;
-      rb += vb;
-    }
-    list_off[nlist] = (int32_t)ra;
-    item_off[nlist] = (int32_t)rb;
-    work_count[0] = 0;
-    work_count[1] = (int32_t)rb;
-  }
-  __syncthreads();
-  int64_t ra = part_a[t], rb = part_b[t];
-  for (int l = lo; l < hi; ++l) {
-    const int cnt = list_count[l];
-    const int64_t len = offsets[l + 1] - offsets[l];
-    list_off[l] = (int32_t)ra;
-    item_off[l] = (int32_t)rb;
-    ra += cnt;
-    if (cnt > 0 && len > 0) rb += ((len + gv - 1) / gv) * ((cnt + gp - 1) / gp);
-  }
-}
-
-__global__ void list_fill_kernel(const int32_t* __restrict__ probe_ids,
-                                 const int32_t* __restrict__ nprobe, int npmax, int64_t nq,
-                                 const int32_t* __restrict__ list_off,
-                                 int32_t* __restrict__ list_fill,
-                                 int32_t* __restrict__ list_pairs) {
-  const int64_t pair = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (pair >= nq * npmax) return;
-  if ((int)(pair % npmax) >= nprobe[pair / npmax]) return;
-  const int l = probe_ids[pair];
-  const int pos = list_off[l] + atomicAdd(&list_fill[l], 1);
-  list_pairs[pos] = (int32_t)pair;
-}
-
-__global__ void items_kernel(const int32_t* __restrict__ list_count,
-                             const int32_t* __restrict__ list_off,
-                             const int32_t* __restrict__ item_off,
-                             const int64_t* __restrict__ offsets, int nlist, int gv, int gp,
-                             int4* __restrict__ work, int64_t max_items, int32_t* err) {
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= nlist) return;
-  const int cnt = list_count[l];
-  const int64_t len = offsets[l + 1] - offsets[l];
-  if (cnt == 0 || len == 0) return;
-  int64_t pos = item_off[l];
-  for (int64_t v = 0; v < len; v += gv)
-    for (int g = 0; g < cnt; g += gp) {
-      if (pos >= max_items) {
-        flag_error(err, kErrCandidateOverflow);
-        return;
-      }
-      work[pos++] = make_int4(l, (int)v, list_off[l] + g, min(gp, cnt - g));
-    }
-}
-
-// Grouped scan: each thread holds one vector's code in registers and runs
-// the estimator for every pair of the item (planes broadcast from shared
-// memory); blocks take items from a global counter until none are left.
+// Grouped scan (Section 3.3.1 block-level schedule, with the queries that
+// probe one list served together): work items are the index's static
+// (list, first vector) blocks of kGroupVectors vectors, taken from a global
+// counter by persistent blocks so that work crosses query boundaries. A
+// thread holds one vector's code in registers and runs the estimator for every
+// (query, list) pair that probes the list, GP pairs at a time with their
+// bit-planes staged in shared memory.
 template <int NW4>
 __global__ void __launch_bounds__(kGroupVectors)
-scan_grouped_kernel(const int4* __restrict__ work, int32_t* __restrict__ work_count,
-                    const int32_t* __restrict__ list_pairs, int npmax,
-                    const float4* __restrict__ qparams, const uint32_t* __restrict__ planes,
+scan_grouped_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict__ work_counter,
+                    const int32_t* __restrict__ list_count, const int32_t* __restrict__ list_pairs,
+                    int64_t pair_stride, const float4* __restrict__ qparams,
+                    const uint32_t* __restrict__ planes, int npmax,
                     const int64_t* __restrict__ offsets, const uint8_t* __restrict__ codes,
                     const float2* __restrict__ fac, const uint32_t* __restrict__ ids, int dp,
                     const uint32_t* __restrict__ bound, int32_t* __restrict__ counts,
-                    uint64_t* __restrict__ cand, int64_t cap, int64_t max_items,
-                    int32_t* err) {
+                    uint64_t* __restrict__ cand, int64_t cap, int32_t* err) {
   constexpr int W = 4 * NW4;
   constexpr int GP = GroupPairs<NW4>::value;
   __shared__ __align__(16) uint32_t s_pl[GP][4 * W];
@@ -409,26 +333,18 @@ scan_grouped_kernel(const int4* __restrict__ work, int32_t* __restrict__ work_co
   __shared__ int32_t s_q[GP];
   __shared__ int s_item;
   const int lane = threadIdx.x & 31;
-  const int total = (int)min((int64_t)work_count[1], max_items);
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(&work_count[0], 1);
+    if (threadIdx.x == 0) s_item = atomicAdd(work_counter, 1);
     __syncthreads();
     const int it = s_item;
-    if (it >= total) break;
-    const int4 w = work[it];
-    const int l = w.x, np = w.w;
-    for (int i = threadIdx.x; i < np * 4 * W; i += blockDim.x) {
-      const int g = i / (4 * W), k = i % (4 * W);
-      s_pl[g][k] = planes[(int64_t)list_pairs[w.z + g] * 4 * W + k];
+    if (it >= n_items) break;
+    const int2 w = items[it];
+    const int l = w.x;
+    const int cnt = list_count[l];
+    if (cnt == 0) {
+      __syncthreads();
+      continue;
     }
-    for (int g = threadIdx.x; g < np; g += blockDim.x) {
-      const int pair = list_pairs[w.z + g];
-      const int q = pair / npmax;
-      s_qp[g] = qparams[pair];
-      s_q[g] = q;
-      s_tau[g] = bound[q];
-    }
-    __syncthreads();
     const int64_t lo = offsets[l] + w.y;
     const int64_t hi = min(offsets[l + 1], lo + kGroupVectors);
     const int64_t s = lo + threadIdx.x;
@@ -448,68 +364,222 @@ scan_grouped_kernel(const int4* __restrict__ work, int32_t* __restrict__ work_co
 #pragma unroll
       for (int i = 0; i < NW4; ++i) code[i] = make_uint4(0, 0, 0, 0);
     }
-    for (int g = 0; g < np; ++g) {
-      float d = 0.0f;
-      bool pass = false;
-      if (valid) {
-        d = estimate_regs<NW4>(code, pc, f, s_pl[g], s_qp[g], dp);
-        pass = orderable(d) <= s_tau[g];
+    const int32_t* lp = list_pairs + (int64_t)l * pair_stride;
+    for (int g0 = 0; g0 < cnt; g0 += GP) {
+      const int np = min(GP, cnt - g0);
+      for (int i = threadIdx.x; i < np * 4 * W; i += blockDim.x) {
+        const int g = i / (4 * W), k = i % (4 * W);
+        s_pl[g][k] = planes[(int64_t)lp[g0 + g] * 4 * W + k];
       }
-      const int q = s_q[g];
-      append_candidates(pass, d, s, ids, counts + q, cand + (int64_t)q * cap, cap, lane, err);
+      for (int g = threadIdx.x; g < np; g += blockDim.x) {
+        const int pair = lp[g0 + g];
+        const int q = pair / npmax;
+        s_qp[g] = qparams[pair];
+        s_q[g] = q;
+        s_tau[g] = bound[q];
+      }
+      __syncthreads();
+      for (int g = 0; g < np; ++g) {
+        float d = 0.0f;
+        bool pass = false;
+        if (valid) {
+          d = estimate_regs<NW4>(code, pc, f, s_pl[g], s_qp[g], dp);
+          pass = orderable(d) <= s_tau[g];
+        }
+        const int q = s_q[g];
+        append_candidates(pass, d, s, ids, counts + q, cand + (int64_t)q * cap, cap, lane, err);
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------------------
-// Exact re-rank (Section 3.3.4): float32 distances to the raw vectors in the
-// 32-lane order, then the k smallest (distance, id); or, without re-rank,
-// the selected estimates themselves.
+// Rotation with more blocks: 16 queries x 64 output columns per block, K in
+// chunks of 128 staged in shared memory.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+rotate16_kernel(const float* __restrict__ q, int64_t nq, int dim, const float* __restrict__ P32,
+                int dp, float* __restrict__ qrot) {
+  __shared__ float As[16][129];
+  __shared__ float Bs[128][64];
+  const int r = threadIdx.x >> 4, cg = threadIdx.x & 15;
+  const int64_t r0 = (int64_t)blockIdx.x * 16;
+  const int col0 = blockIdx.y * 64;
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  for (int k0 = 0; k0 < dim; k0 += 128) {
+    for (int t = threadIdx.x; t < 16 * 128; t += 256) {
+      const int rr = t >> 7, kk = t & 127;
+      const int64_t row = r0 + rr;
+      As[rr][kk] = (row < nq && k0 + kk < dim) ? q[row * dim + k0 + kk] : 0.0f;
+    }
+    for (int t = threadIdx.x; t < 128 * 64; t += 256) {
+      const int kk = t >> 6, c = t & 63;
+      Bs[kk][c] = (k0 + kk < dim) ? P32[(int64_t)(k0 + kk) * dp + col0 + c] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 128; ++kk) {
+      const float a = As[r][kk];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[j] = fmaf(a, Bs[kk][cg + 16 * j], acc[j]);
+    }
+    __syncthreads();
+  }
+  const int64_t row = r0 + r;
+  if (row < nq) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) qrot[row * dp + col0 + cg + 16 * j] = acc[j];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Probe selection: the nprobe smallest (distance, list) keys of each query,
+// one block of 128 threads per query (radix selection, then a sort of the
+// selected keys only).
+// ---------------------------------------------------------------------------
+constexpr int kProbeSmemKeys = 2048;
+
+__global__ void __launch_bounds__(128)
+probe_select_kernel(const uint64_t* __restrict__ pkeys, int nlist, int np,
+                    int32_t* __restrict__ out_ids, float* __restrict__ out_d) {
+  extern __shared__ uint64_t s_dyn[];
+  __shared__ int hist[256];
+  __shared__ int res[4];
+  __shared__ uint64_t small[kSelectSmall];
+  const int64_t row = blockIdx.x;
+  const uint64_t* src = pkeys + row * nlist;
+  uint64_t* dst = s_dyn;
+  if (nlist <= kProbeSmemKeys) {
+    uint64_t* keys = s_dyn;
+    for (int i = threadIdx.x; i < nlist; i += blockDim.x) keys[i] = src[i];
+    __syncthreads();
+    src = keys;
+    dst = s_dyn + nlist;
+  }
+  const int got = block_select_smallest(src, nlist, np, dst, small, hist, res);
+  for (int j = threadIdx.x; j < np; j += blockDim.x) {
+    const uint64_t k = (j < got) ? dst[j] : kU64Max;
+    out_ids[row * np + j] = (k == kU64Max) ? -1 : (int32_t)(uint32_t)k;
+    out_d[row * np + j] =
+        (k == kU64Max) ? __int_as_float(0x7f800000) : from_orderable((uint32_t)(k >> 32));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Exact squared distance of one raw row to the query in the 32-lane order,
+// computed by one thread: partial sum l takes d = l, l + 32, ... in order,
+// then partials l and l + s are added for s = 16, 8, 4, 2, 1.
 // ---------------------------------------------------------------------------
 template <typename RawT>
-__global__ void __launch_bounds__(256)
-rerank_kernel(const uint64_t* __restrict__ sel, int nsel_max, const int32_t* __restrict__ nsel,
-              const int32_t* __restrict__ kq, const int32_t* __restrict__ rerank_on,
-              const RawT* __restrict__ raw, const float* __restrict__ q, int dim,
-              int k_stride, int64_t* __restrict__ out_ids, float* __restrict__ out_d) {
-  extern __shared__ uint64_t s_keys[];
+__device__ __forceinline__ float exact_dist_lanes(const RawT* __restrict__ x,
+                                                  const float* __restrict__ qs, int dim) {
+  float acc[32];
+#pragma unroll
+  for (int l = 0; l < 32; ++l) acc[l] = 0.0f;
+  int d0 = 0;
+  for (; d0 + 32 <= dim; d0 += 32) {
+    if (sizeof(RawT) == 4 && (dim & 3) == 0) {
+      const float4* x4 = reinterpret_cast<const float4*>(x + d0);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float4 t = __ldg(x4 + j);
+        const float v[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float df = __fsub_rn(v[e], qs[d0 + 4 * j + e]);
+          acc[4 * j + e] = __fadd_rn(acc[4 * j + e], __fmul_rn(df, df));
+        }
+      }
+    } else if (sizeof(RawT) == 1 && (dim & 15) == 0) {
+      const uint4* x16 = reinterpret_cast<const uint4*>(x + d0);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const uint4 t = __ldg(x16 + j);
+        const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+          const float v = (float)((w[b >> 2] >> (8 * (b & 3))) & 255u);
+          const float df = __fsub_rn(v, qs[d0 + 16 * j + b]);
+          acc[16 * j + b] = __fadd_rn(acc[16 * j + b], __fmul_rn(df, df));
+        }
+      }
+    } else {
+#pragma unroll
+      for (int l = 0; l < 32; ++l) {
+        const float df = __fsub_rn((float)x[d0 + l], qs[d0 + l]);
+        acc[l] = __fadd_rn(acc[l], __fmul_rn(df, df));
+      }
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < 32; ++l) {
+    if (d0 + l < dim) {
+      const float df = __fsub_rn((float)x[d0 + l], qs[d0 + l]);
+      acc[l] = __fadd_rn(acc[l], __fmul_rn(df, df));
+    }
+  }
+#pragma unroll
+  for (int s = 16; s; s >>= 1)
+#pragma unroll
+    for (int l = 0; l < s; ++l) acc[l] = __fadd_rn(acc[l], acc[l + s]);
+  return acc[0];
+}
+
+// ---------------------------------------------------------------------------
+// Candidate selection fused with the exact re-rank (Section 3.3.4): one
+// block per query selects its n_sel smallest estimate keys (written, sorted,
+// to `sel`), computes their exact distances (one thread per candidate), and
+// writes the k smallest (distance, id); without re-rank, the estimates.
+// ---------------------------------------------------------------------------
+template <typename RawT>
+__global__ void __launch_bounds__(256, 4)
+finalize_kernel(const uint64_t* __restrict__ cand, int64_t cap, const int32_t* __restrict__ counts,
+                const int32_t* __restrict__ nsel, const int32_t* __restrict__ kq,
+                const int32_t* __restrict__ rerank_on, int nsel_max, uint64_t* __restrict__ sel,
+                const RawT* __restrict__ raw, const float* __restrict__ q, int dim, int k_stride,
+                int64_t* __restrict__ out_ids, float* __restrict__ out_d, int32_t* err) {
+  extern __shared__ uint64_t s_dyn[];
+  __shared__ int hist[256];
+  __shared__ int res[4];
+  __shared__ uint64_t small[kSelectSmall];
   const int64_t row = blockIdx.x;
+  int64_t count = counts[row];
+  if (count > cap) {
+    if (threadIdx.x == 0) flag_error(err, kErrCandidateOverflow);
+    count = cap;
+  }
   const int n_sel = nsel[row];
   const int k = kq[row];
-  const uint64_t* sr = sel + row * nsel_max;
+  uint64_t* s_sel = s_dyn;
+  float* s_q = reinterpret_cast<float*>(s_dyn + next_pow2_dev(nsel_max));
+  const bool rerank = rerank_on[row] != 0;
+  // Without re-rank the selection is the answer and is sorted; with re-rank
+  // only the set matters and the exact keys are sorted below.
+  const int got = block_select_smallest(cand + row * cap, (int)count, n_sel, s_sel, small, hist,
+                                        res, !rerank);
+  for (int j = threadIdx.x; j < nsel_max; j += blockDim.x)
+    sel[row * nsel_max + j] = (j < got) ? s_sel[j] : kU64Max;
   const float inf = __int_as_float(0x7f800000);
-  if (!rerank_on[row]) {
+  if (!rerank) {
     for (int j = threadIdx.x; j < k_stride; j += blockDim.x) {
-      const uint64_t key = (j < k && j < n_sel) ? sr[j] : kU64Max;
+      const uint64_t key = (j < k && j < got) ? s_sel[j] : kU64Max;
       out_ids[row * k_stride + j] = (key == kU64Max) ? -1 : (int64_t)(uint32_t)key;
       out_d[row * k_stride + j] = (key == kU64Max) ? inf : from_orderable((uint32_t)(key >> 32));
     }
     return;
   }
-  const int m = next_pow2(max(n_sel, 1));
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const float* qr = q + row * dim;
-  for (int i = warp; i < m; i += nw) {
-    const uint64_t key = (i < n_sel) ? sr[i] : kU64Max;
-    if (key == kU64Max) {
-      if (lane == 0) s_keys[i] = kU64Max;
-      continue;
-    }
-    const uint32_t id = (uint32_t)key;
-    const RawT* xr = raw + (int64_t)id * dim;
-    float acc = 0.0f;
-    for (int d = lane; d < dim; d += 32) {
-      const float df = __fsub_rn((float)xr[d], qr[d]);
-      acc = __fadd_rn(acc, __fmul_rn(df, df));
-    }
-    const float dist = lane_tree_sum(acc);
-    if (lane == 0) s_keys[i] = make_key(dist, id);
+  for (int d = threadIdx.x; d < dim; d += blockDim.x) s_q[d] = q[row * dim + d];
+  __syncthreads();
+  for (int i = threadIdx.x; i < got; i += blockDim.x) {
+    const uint32_t id = (uint32_t)s_sel[i];
+    const float dist = exact_dist_lanes<RawT>(raw + (int64_t)id * dim, s_q, dim);
+    s_sel[i] = make_key(dist, id);
   }
   __syncthreads();
-  block_bitonic_sort(s_keys, m);
+  block_bitonic_sort(s_sel, next_pow2(max(got, 1)));
   for (int j = threadIdx.x; j < k_stride; j += blockDim.x) {
-    const uint64_t key = (j < k) ? s_keys[j] : kU64Max;
+    const uint64_t key = (j < k && j < got) ? s_sel[j] : kU64Max;
     out_ids[row * k_stride + j] = (key == kU64Max) ? -1 : (int64_t)(uint32_t)key;
     out_d[row * k_stride + j] = (key == kU64Max) ? inf : from_orderable((uint32_t)(key >> 32));
   }
@@ -536,15 +606,6 @@ void rebase(T*& p, char* base) {
   p = reinterpret_cast<T*>(base + reinterpret_cast<size_t>(p));
 }
 
-// Items of a list: ceil(L / S) * ceil(cnt / G) <= (L/S + 1)(cnt/G + 1); summed
-// over lists, sum L*cnt <= nq * cap, sum L = n, sum cnt = pairs.
-int64_t max_items_bound(const rq_index* ix, const SearchShape& sh, int64_t cap) {
-  const int64_t pairs = sh.nq * sh.npmax;
-  const int64_t gp = group_pairs_for(ix->dp);
-  return sh.nq * cap / ((int64_t)kGroupVectors * gp) + ix->n / kGroupVectors + pairs / gp +
-         2 * (int64_t)ix->nlist + 16;
-}
-
 rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, Workspace& ws) {
   const int64_t nq = sh.nq, np = sh.npmax;
   const int W = ix->dp / 32;
@@ -568,14 +629,11 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
   L.take(&ws.out_ids, nq * sh.k_stride);
   L.take(&ws.out_d, nq * sh.k_stride);
   if (sh.mode != RQ_SCAN_PLAIN) {
-    ws.max_items = max_items_bound(ix, sh, ws.cap);
     L.take(&ws.list_count, ix->nlist);
-    L.take(&ws.list_off, ix->nlist + 1);
-    L.take(&ws.list_pairs, nq * np);
-    L.take(&ws.list_fill, ix->nlist + 1);  // last entry unused (item_off scratch below)
-    L.take(&ws.work_count, 2 * (ix->nlist + 1) + 2);
-    L.take(&ws.work, ws.max_items);
+    L.take(&ws.list_pairs, (int64_t)ix->nlist * nq);
+    L.take(&ws.work_count, 4);
   }
+  if (sh.mode == RQ_SCAN_MMA) L.take(&ws.qdig, nq * np * ix->dp);
   ws.bytes = L.off;
   (void)st;
   cudaError_t e = cudaMalloc(&ws.base, ws.bytes);
@@ -604,12 +662,10 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
   rebase(ws.out_d, b);
   if (sh.mode != RQ_SCAN_PLAIN) {
     rebase(ws.list_count, b);
-    rebase(ws.list_off, b);
     rebase(ws.list_pairs, b);
-    rebase(ws.list_fill, b);
     rebase(ws.work_count, b);
-    rebase(ws.work, b);
   }
+  if (sh.mode == RQ_SCAN_MMA) rebase(ws.qdig, b);
   return RQ_OK;
 }
 
@@ -621,8 +677,12 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
   const int dp = ix->dp;
   const int64_t pairs = nq * np;
   tm.mark(RQ_STAGE_QUANTIZE, st);
+  const bool grouped = sh.mode != RQ_SCAN_PLAIN;
+  if (grouped) RQ_CUDA(cudaMemsetAsync(ws.list_count, 0, sizeof(int32_t) * ix->nlist, st));
   quantize_kernel<NW4><<<blocks_for(pairs * 32, 256), 256, 0, st>>>(
-      ws.qrot, ws.probe_ids, ws.nprobe, np, nq, ix->cR, dp, ws.qparams, ws.planes, ix->d_err);
+      ws.qrot, ws.probe_ids, ws.nprobe, np, nq, ix->cR, dp, ws.qparams, ws.planes,
+      grouped ? ws.list_count : nullptr, ws.list_pairs,
+      sh.mode == RQ_SCAN_MMA ? ws.qdig : nullptr, ix->d_err);
   tm.mark(RQ_STAGE_BOUND, st);
   bound_kernel<NW4><<<(unsigned)nq, 256, 0, st>>>(ws.probe_ids, ws.nprobe, np, ws.nsel, ws.qparams,
                                                  ws.planes, ix->offsets, ix->codes, ix->fac, dp,
@@ -635,20 +695,7 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
         ws.probe_ids, ws.nprobe, np, ws.qparams, ws.planes, ix->offsets, ix->codes, ix->fac,
         ix->ids, dp, ws.bound, ws.counts, ws.cand, ws.cap, ix->d_err);
   } else {
-    int32_t* item_off = ws.work_count + 2;
-    RQ_CUDA(cudaMemsetAsync(ws.list_count, 0, sizeof(int32_t) * ix->nlist, st));
-    RQ_CUDA(cudaMemsetAsync(ws.list_fill, 0, sizeof(int32_t) * ix->nlist, st));
-    list_count_kernel<<<blocks_for(pairs, 256), 256, 0, st>>>(ws.probe_ids, ws.nprobe, np, nq,
-                                                             ws.list_count);
-    const int gp = group_pairs_for(dp);
-    list_scan_kernel<<<1, 1024, 0, st>>>(ws.list_count, ix->offsets, ix->nlist, kGroupVectors,
-                                         gp, ws.list_off, item_off, ws.work_count);
-    list_fill_kernel<<<blocks_for(pairs, 256), 256, 0, st>>>(ws.probe_ids, ws.nprobe, np, nq,
-                                                            ws.list_off, ws.list_fill,
-                                                            ws.list_pairs);
-    items_kernel<<<blocks_for(ix->nlist, 128), 128, 0, st>>>(
-        ws.list_count, ws.list_off, item_off, ix->offsets, ix->nlist, kGroupVectors, gp,
-        ws.work, ws.max_items, ix->d_err);
+    RQ_CUDA(cudaMemsetAsync(ws.work_count, 0, sizeof(int32_t) * 4, st));
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
     tm.mark(RQ_STAGE_SCAN, st);
@@ -656,9 +703,9 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
       RQ_TRY(launch_scan_mma(ix, sh, ws, st, sms));
     } else {
       scan_grouped_kernel<NW4><<<(unsigned)(sms * 8), kGroupVectors, 0, st>>>(
-          ws.work, ws.work_count, ws.list_pairs, np, ws.qparams, ws.planes, ix->offsets,
-          ix->codes, ix->fac, ix->ids, dp, ws.bound, ws.counts, ws.cand, ws.cap, ws.max_items,
-          ix->d_err);
+          ix->items, ix->n_items, ws.work_count, ws.list_count, ws.list_pairs, nq, ws.qparams,
+          ws.planes, np, ix->offsets, ix->codes, ix->fac, ix->ids, dp, ws.bound, ws.counts,
+          ws.cand, ws.cap, ix->d_err);
     }
   }
   return RQ_OK;
@@ -671,18 +718,17 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
   const int dp = ix->dp;
   // 1. rotation, once per query
   tm.mark(RQ_STAGE_ROTATE, st);
-  rotate_kernel<<<dim3(blocks_for(nq, 64), dp / 64), 256, 0, st>>>(ws.q, nq, ix->dim, ix->P32, dp,
-                                                                  ws.qrot);
+  rotate16_kernel<<<dim3(blocks_for(nq, 16), dp / 64), 256, 0, st>>>(ws.q, nq, ix->dim, ix->P32,
+                                                                    dp, ws.qrot);
   // 2. centroid ranking and probe selection
   tm.mark(RQ_STAGE_PROBE, st);
-  pair_dist_kernel<1><<<dim3(blocks_for(nq, 64), blocks_for(ix->nlist, 64)), 256, 0, st>>>(
+  pair_dist_kernel<1, 2><<<dim3(blocks_for(nq, 32), blocks_for(ix->nlist, 64)), 256, 0, st>>>(
       ws.qrot, nq, ix->cR, ix->nlist, dp, nullptr, nullptr, ws.pkeys);
   {
-    const int m = next_pow2_host(std::min<int64_t>(ix->nlist, kMaxSelect));
-    const size_t smem = sizeof(uint64_t) * std::max(m, next_pow2_host(np));
-    select_rows_kernel<1><<<(unsigned)nq, 1024, smem, st>>>(
-        ws.pkeys, ix->nlist, nullptr, ix->nlist, ix->nlist, nullptr, np, nullptr, np,
-        ws.probe_ids, ws.probe_d, ix->d_err);
+    const size_t smem = sizeof(uint64_t) * ((ix->nlist <= kProbeSmemKeys ? ix->nlist : 0) +
+                                            next_pow2_host(np));
+    probe_select_kernel<<<(unsigned)nq, 128, smem, st>>>(ws.pkeys, ix->nlist, np, ws.probe_ids,
+                                                        ws.probe_d);
   }
   // 3-4. quantisation, bound, scan
   switch (dp / 128) {
@@ -700,27 +746,22 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
       return fail(RQ_ERR_NOT_IMPLEMENTED, "padded dimension " + std::to_string(dp) +
                                               " has no scan kernel (built: 128..1024, 1536, 2048)");
   }
-  // 5. candidate selection
+  // 5-6. candidate selection and exact re-rank
   tm.mark(RQ_STAGE_SELECT, st);
   {
-    const size_t smem = sizeof(uint64_t) * kMaxSelect;
-    select_rows_kernel<0><<<(unsigned)nq, 1024, smem, st>>>(
-        ws.cand, ws.cap, ws.counts, 0, ws.cap, ws.nsel, 0, ws.sel, sh.nsel_max, nullptr, nullptr,
-        ix->d_err);
-  }
-  // 6. exact re-rank
-  tm.mark(RQ_STAGE_RERANK, st);
-  {
-    const size_t smem = sizeof(uint64_t) * next_pow2_host(sh.nsel_max);
+    const size_t smem = sizeof(uint64_t) * next_pow2_host(sh.nsel_max) + sizeof(float) * ix->dim;
     if (ix->raw_dtype == RQ_U8)
-      rerank_kernel<uint8_t><<<(unsigned)nq, 256, smem, st>>>(
-          ws.sel, sh.nsel_max, ws.nsel, ws.kq, ws.rerank_on, static_cast<const uint8_t*>(ix->raw),
-          ws.q, ix->dim, sh.k_stride, ws.out_ids, ws.out_d);
+      finalize_kernel<uint8_t><<<(unsigned)nq, 256, smem, st>>>(
+          ws.cand, ws.cap, ws.counts, ws.nsel, ws.kq, ws.rerank_on, sh.nsel_max, ws.sel,
+          static_cast<const uint8_t*>(ix->raw), ws.q, ix->dim, sh.k_stride, ws.out_ids, ws.out_d,
+          ix->d_err);
     else
-      rerank_kernel<float><<<(unsigned)nq, 256, smem, st>>>(
-          ws.sel, sh.nsel_max, ws.nsel, ws.kq, ws.rerank_on, static_cast<const float*>(ix->raw),
-          ws.q, ix->dim, sh.k_stride, ws.out_ids, ws.out_d);
+      finalize_kernel<float><<<(unsigned)nq, 256, smem, st>>>(
+          ws.cand, ws.cap, ws.counts, ws.nsel, ws.kq, ws.rerank_on, sh.nsel_max, ws.sel,
+          static_cast<const float*>(ix->raw), ws.q, ix->dim, sh.k_stride, ws.out_ids, ws.out_d,
+          ix->d_err);
   }
+  tm.mark(RQ_STAGE_RERANK, st);
   tm.mark(RQ_STAGE_COUNT, st);
   RQ_CUDA(cudaGetLastError());
   return RQ_OK;

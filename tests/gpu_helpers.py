@@ -98,7 +98,7 @@ def replay_and_compare(hix: dict, q: np.ndarray, dump: dict, prune: bool = True,
         tau = R.first_bound(d2, n_sel) if prune else R.U32_MAX
         assert int(dump["bound"][i]) == int(tau), (i, "bound")
         sel = R.select_candidates(d2, cid, n_sel, prune)
-        gsel = dump["selected"][i, :n_sel]
+        gsel = np.sort(dump["selected"][i, :n_sel])   # a set when re-ranked
         assert np.array_equal(gsel[:sel.size], sel), (i, "selected keys")
         assert np.all(gsel[sel.size:] == U64_MAX), (i, "selection padding")
         stats["candidates"] += d2.size

@@ -113,7 +113,7 @@ def test_build_with_given_centroids_and_rotation(rq):
 
 
 # ---------------------------------------------------------------- search
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 @pytest.mark.parametrize("prune", [True, False])
 def test_search_stages_replay_bit_exact(tiny, mode, prune):
     _, q, ix, h = tiny
@@ -136,7 +136,8 @@ def test_modes_graph_and_streams_identical(tiny):
     _, q, ix, _ = tiny
     ref = ix.search(q, 16, 10, 200, scan_mode=1)
     for kw in (dict(scan_mode=2), dict(scan_mode=2, use_graph=True),
-               dict(scan_mode=1, use_graph=True), dict(scan_mode=0)):
+               dict(scan_mode=1, use_graph=True), dict(scan_mode=0),
+               dict(scan_mode=3), dict(scan_mode=3, use_graph=True)):
         for _ in range(2):
             got = ix.search(q, 16, 10, 200, **kw)
             assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), kw
@@ -155,8 +156,9 @@ def test_mixed_batch_equals_alone_and_replays(tiny):
     nq = 40
     npb, kk = W.per_query_params(nq, 5, (1, 64), (1, 10, 33))
     nr = np.where(np.arange(nq) % 5 == 0, 0, np.maximum(kk, 50)).astype(np.int32)
-    dump = search_dump(ix, q[:nq], npb, kk, nr, mixed=True, scan_mode=2)
-    replay_and_compare(h, q[:nq], dump)
+    for mode in (2, 3):
+        dump = search_dump(ix, q[:nq], npb, kk, nr, mixed=True, scan_mode=mode)
+        replay_and_compare(h, q[:nq], dump)
     for i in range(0, nq, 7):
         alone = ix.search(q[i:i + 1], int(npb[i]), int(kk[i]), int(nr[i]))
         assert np.array_equal(alone[0][0], dump["ids"][i, :kk[i]])
@@ -169,8 +171,9 @@ def test_short_results_are_padded(rq):
     ix = rq.rq_build(x, 30, seed=2, kmeans_iters=3)
     h = host_index(ix)
     # one probed list holds ~10 vectors, far fewer than k
-    dump = search_dump(ix, q, 1, 50, 60, scan_mode=2)
-    replay_and_compare(h, q, dump)
+    for mode in (1, 2, 3):
+        dump = search_dump(ix, q, 1, 50, 60, scan_mode=mode)
+        replay_and_compare(h, q, dump)
     assert (dump["ids"] == -1).any() and np.isinf(dump["dist"]).any()
     # n_rerank = 0 returns the estimated top k
     dump = search_dump(ix, q, 3, 7, 0, scan_mode=1)
@@ -198,8 +201,9 @@ def test_uint8_base_and_sift_like_data(rq):
     ix = rq.rq_build(x8, 64, seed=4, kmeans_iters=4)
     h = host_index(ix)
     assert h["raw"].dtype == np.float32 and np.array_equal(h["raw"], x)
-    dump = search_dump(ix, q, 12, 10, 200, scan_mode=2)
-    replay_and_compare(h, q, dump)
+    for mode in (2, 3):
+        dump = search_dump(ix, q, 12, 10, 200, scan_mode=mode)
+        replay_and_compare(h, q, dump)
     _, td = R.exact_knn(x, q, 10)
     assert R.recall_at(x, q, dump["ids"], td, 10) >= 0.9
 
