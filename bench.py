@@ -570,6 +570,11 @@ def run_profile(args):
             ix.search(q_dev, nprobe, k, nrr, out_ids=ids, out_dist=dist, scan_mode=mode,
                       stage_times=st)
         out[name] = {a: round(b, 4) for a, b in st.items()}
+    nc = torch.empty((q_dev.shape[0],), dtype=torch.int32, device=dev)
+    ix.search(q_dev, nprobe, k, nrr, out_ids=ids, out_dist=dist, dump={"n_candidates": nc})
+    c = nc.cpu().numpy()
+    out["candidates_per_query"] = {"mean": float(c.mean()), "p50": float(np.median(c)),
+                                   "max": int(c.max()), "min": int(c.min())}
     print(json.dumps({"profile": out, "nprobe": nprobe}), flush=True)
 
 

@@ -676,7 +676,8 @@ rq_status rq_import(const char* path, rq_index** out) {
       s = fail(RQ_ERR_IO, "truncated index file");
       break;
     }
-    if (cudaMalloc(a.dev, std::max<size_t>(a.bytes, 1)) != cudaSuccess) {
+    // 16 bytes of tail room: bulk copies read whole 16-byte units.
+    if (cudaMalloc(a.dev, a.bytes + 16) != cudaSuccess) {
       cudaGetLastError();
       *a.dev = nullptr;
       s = fail(RQ_ERR_OOM, "index arrays");

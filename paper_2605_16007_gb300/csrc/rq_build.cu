@@ -690,7 +690,7 @@ rq_status build_index(const float* d_base, const void* d_raw, rq_dtype dt,
   RQ_TRY(codes.alloc((size_t)n * ix->C));
   RQ_TRY(r.alloc(n));
   RQ_TRY(alpha.alloc(n));
-  RQ_TRY(fac.alloc(n));
+  RQ_TRY(fac.alloc(n + 2));  // 16 bytes of tail room for 16-byte bulk copies
   RQ_TRY(ids.alloc(n));
   RQ_TRY(assign.alloc(n));
   RQ_TRY(err.alloc(1));

@@ -191,9 +191,8 @@ __device__ inline uint32_t block_radix_select_u32(const uint32_t* keys,
 namespace rq {
 
 // ---------------------------------------------------------------------------
-// Block-wide radix selection with 8-bit digits. All threads of the block call
-// these functions (loops run in whole rounds so that warps stay converged).
-// `hist` is 256 ints and `res` 4 ints of shared memory.
+// Helpers of the radix selections (8-bit digits): loops run in whole rounds
+// of 32 so that warps stay converged.
 // ---------------------------------------------------------------------------
 
 // Adds 1 to hist[d] for every active lane, one atomic per distinct digit of
@@ -205,12 +204,39 @@ __device__ __forceinline__ void hist_add(int* hist, int d, bool active) {
   if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[d], __popc(peers));
 }
 
-// Warp 0 finds the bucket b where the running count of hist reaches `rank`
-// (1-based): res = {b, count below b, hist[b]}. rank must not exceed the
-// total count.
-__device__ __forceinline__ void find_bucket(const int* hist, int rank, int* res) {
-  if (threadIdx.x >= 32) return;
-  const int lane = threadIdx.x;
+// Sorts 32 uint64 keys held one per lane (ascending by lane) with a bitonic
+// network of warp shuffles. All 32 lanes must call it.
+__device__ __forceinline__ uint64_t warp_sort32(uint64_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const uint64_t o = __shfl_xor_sync(0xffffffffu, v, j);
+      const bool up = (lane & k) == 0;
+      const bool lower = (lane & j) == 0;
+      // keep the smaller of the pair on the lower lane of an ascending run
+      v = (lower == up) ? (v < o ? v : o) : (v < o ? o : v);
+    }
+  }
+  return v;
+}
+
+}  // namespace rq
+
+namespace rq {
+
+// ---------------------------------------------------------------------------
+// Warp-level selection: one warp serves one query, synchronising with
+// __syncwarp only. `hist` is 256 ints and `small` 32 keys of the warp's own
+// shared memory. All 32 lanes call these functions.
+// ---------------------------------------------------------------------------
+
+// The bucket where the running count of hist reaches `rank` (1-based), as
+// (b, count below b, hist[b]) in every lane.
+__device__ __forceinline__ void warp_find_bucket(const int* hist, int rank, int& b, int& below,
+                                                 int& cnt) {
+  const int lane = threadIdx.x & 31;
   int h[8];
   int sum = 0;
 #pragma unroll
@@ -227,67 +253,76 @@ __device__ __forceinline__ void find_bucket(const int* hist, int rank, int* res)
   const int excl = incl - sum;
   const unsigned m = __ballot_sync(0xffffffffu, excl < rank && rank <= incl);
   const int src = m ? __ffs(m) - 1 : 31;
-  if (lane == src) {
-    int cum = excl, b = 7;
+  int bb = 7, cum = excl;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      if (cum + h[i] >= rank) {
-        b = i;
-        break;
-      }
-      cum += h[i];
+  for (int i = 0; i < 8; ++i) {
+    if (cum + h[i] >= rank) {
+      bb = i;
+      break;
     }
-    res[0] = lane * 8 + b;
-    res[1] = cum;
-    res[2] = h[b];
+    cum += h[i];
   }
+  int hb = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    if (i == bb) hb = h[i];
+  b = __shfl_sync(0xffffffffu, lane * 8 + bb, src);
+  below = __shfl_sync(0xffffffffu, cum, src);
+  cnt = __shfl_sync(0xffffffffu, hb, src);
 }
 
-// Appends the active lanes' values at dst[base + rank] with one atomic per
-// warp on *counter; positions at or past `cap` are dropped.
-template <typename T>
-__device__ __forceinline__ void block_append(T* dst, int* counter, int cap, T v, bool active) {
-  const unsigned m = __ballot_sync(0xffffffffu, active);
-  if (!m) return;
+// Sorts dst[0, n) ascending, dst[n, next_pow2(n)) holding all ones: in
+// registers for n <= 32, else a bitonic network over shared memory.
+__device__ inline void warp_sort_keys(uint64_t* dst, int n) {
   const int lane = threadIdx.x & 31;
-  const int leader = __ffs(m) - 1;
-  int base = 0;
-  if (lane == leader) base = atomicAdd(counter, __popc(m));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (active) {
-    const int pos = base + __popc(m & ((1u << lane) - 1u));
-    if (pos < cap) dst[pos] = v;
+  if (n <= 32) {
+    const uint64_t v = warp_sort32(lane < n ? dst[lane] : kU64Max);
+    if (lane < n) dst[lane] = v;
+    __syncwarp();
+    return;
+  }
+  const int m = next_pow2(n);
+  for (int k = 2; k <= m; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < m; i += 32) {
+        const int l = i ^ j;
+        if (l > i) {
+          const uint64_t a = dst[i], c = dst[l];
+          if ((a > c) == ((i & k) == 0)) {
+            dst[i] = c;
+            dst[l] = a;
+          }
+        }
+      }
+      __syncwarp();
+    }
   }
 }
 
-// The n smallest of m distinct uint64 keys at src (shared or global memory),
-// ascending in dst[0, n) and dst[n, next_pow2(n)) = all ones. Returns
-// min(n, m). dst holds next_pow2(max(n, 1)) keys of shared memory; `small`
-// holds kSelectSmall keys of shared memory. Radix passes (8-bit digits from
-// the top) narrow the bucket holding the n-th key until it has at most
-// kSelectSmall keys; the keys below it are taken whole and the bucket is
-// sorted to supply the rest.
-constexpr int kSelectSmall = 256;
-
-__device__ inline int block_select_smallest(const uint64_t* src, int m, int n, uint64_t* dst,
-                                            uint64_t* small, int* hist, int* res,
-                                            bool sorted = true) {
-  const int T = blockDim.x;
+// The n smallest of m distinct uint64 keys at src (shared or global memory)
+// into dst[0, n) (ascending if `sorted`) with dst[n, next_pow2(n)) = all
+// ones; dst holds next_pow2(max(n, 1)) keys. Returns min(n, m). Radix passes
+// narrow the bucket of the n-th key to at most 32 keys, which the warp sorts
+// in registers.
+__device__ inline int warp_select_smallest(const uint64_t* src, int m, int n, uint64_t* dst,
+                                           int* hist, uint64_t* small, bool sorted) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
   const int sel = min(n, m);
   const int mp = next_pow2(max(sel, 1));
   if (m <= n) {
-    for (int i = threadIdx.x; i < mp; i += T) dst[i] = (i < m) ? src[i] : kU64Max;
-    __syncthreads();
-    if (sorted) block_bitonic_sort(dst, mp);
+    for (int i = lane; i < mp; i += 32) dst[i] = (i < m) ? src[i] : kU64Max;
+    __syncwarp();
+    if (sorted) warp_sort_keys(dst, sel);
     return sel;
   }
   uint64_t prefix = 0, mask = 0;
   int rank = n, cnt = m;
-  for (int shift = 56; shift >= 0 && cnt > kSelectSmall; shift -= 8) {
-    for (int i = threadIdx.x; i < 256; i += T) hist[i] = 0;
-    __syncthreads();
-    for (int base = 0; base < m; base += T) {
-      const int i = base + threadIdx.x;
+  for (int shift = 56; shift >= 0 && cnt > 32; shift -= 8) {
+    for (int i = lane; i < 256; i += 32) hist[i] = 0;
+    __syncwarp();
+    for (int base = 0; base < m; base += 32) {
+      const int i = base + lane;
       uint64_t k = 0;
       bool act = false;
       if (i < m) {
@@ -296,60 +331,58 @@ __device__ inline int block_select_smallest(const uint64_t* src, int m, int n, u
       }
       hist_add(hist, (int)((k >> shift) & 255), act);
     }
-    __syncthreads();
-    find_bucket(hist, rank, res);
-    __syncthreads();
-    const int b = res[0], below = res[1];
-    cnt = res[2];
-    __syncthreads();
+    __syncwarp();
+    int b, below;
+    warp_find_bucket(hist, rank, b, below, cnt);
+    __syncwarp();
     prefix |= (uint64_t)b << shift;
     mask |= 0xFFull << shift;
     rank -= below;
   }
-  // Keys below the bucket all belong to the result (n - rank of them); the
-  // bucket (cnt <= kSelectSmall keys, or one key after all eight digits)
-  // gives its rank smallest.
-  if (threadIdx.x == 0) {
-    res[2] = 0;
-    res[3] = 0;
-  }
-  __syncthreads();
-  for (int base = 0; base < m; base += T) {
-    const int i = base + threadIdx.x;
+  int nd = 0, ns = 0;
+  for (int base = 0; base < m; base += 32) {
+    const int i = base + lane;
     uint64_t k = kU64Max;
     if (i < m) k = src[i];
     const uint64_t km = k & mask;
-    block_append(dst, &res[3], n, k, i < m && km < prefix);
-    block_append(small, &res[2], kSelectSmall, k, i < m && km == prefix);
+    const bool lo = i < m && km < prefix;
+    const bool eq = i < m && km == prefix;
+    const uint32_t mlo = __ballot_sync(0xffffffffu, lo);
+    const uint32_t meq = __ballot_sync(0xffffffffu, eq);
+    if (lo) {
+      const int p = nd + __popc(mlo & lt);
+      if (p < n) dst[p] = k;
+    }
+    if (eq) {
+      const int p = ns + __popc(meq & lt);
+      if (p < 32) small[p] = k;
+    }
+    nd += __popc(mlo);
+    ns += __popc(meq);
   }
-  __syncthreads();
-  const int nb = min(res[2], kSelectSmall);
-  const int sp = next_pow2(max(nb, 1));
-  for (int i = nb + threadIdx.x; i < sp; i += T) small[i] = kU64Max;
-  __syncthreads();
-  block_bitonic_sort(small, sp);
+  __syncwarp();
+  const uint64_t v = warp_sort32(lane < min(ns, 32) ? small[lane] : kU64Max);
   const int have = n - rank;
-  for (int i = threadIdx.x; i < rank; i += T) dst[have + i] = small[i];
-  for (int i = n + threadIdx.x; i < mp; i += T) dst[i] = kU64Max;
-  __syncthreads();
-  if (sorted) block_bitonic_sort(dst, mp);
+  if (lane < rank) dst[have + lane] = v;
+  for (int i = n + lane; i < mp; i += 32) dst[i] = kU64Max;
+  __syncwarp();
+  if (sorted) warp_sort_keys(dst, n);
   return sel;
 }
 
 // The rank-th smallest (1-based) of m uint32 values in shared memory
-// (duplicates allowed): radix passes narrow the bucket holding it to at most
-// kSelectSmall values, which are then sorted. `small` holds kSelectSmall
-// uint64 of shared memory.
-__device__ inline uint32_t block_kth_u32(const uint32_t* src, int m, int rank, uint64_t* small,
-                                         int* hist, int* res) {
-  const int T = blockDim.x;
+// (duplicates allowed), by one warp.
+__device__ inline uint32_t warp_kth_u32(const uint32_t* src, int m, int rank, int* hist,
+                                        uint64_t* small) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
   uint32_t prefix = 0, mask = 0;
   int cnt = m;
-  for (int shift = 24; shift >= 0 && cnt > kSelectSmall; shift -= 8) {
-    for (int i = threadIdx.x; i < 256; i += T) hist[i] = 0;
-    __syncthreads();
-    for (int base = 0; base < m; base += T) {
-      const int i = base + threadIdx.x;
+  for (int shift = 24; shift >= 0 && cnt > 32; shift -= 8) {
+    for (int i = lane; i < 256; i += 32) hist[i] = 0;
+    __syncwarp();
+    for (int base = 0; base < m; base += 32) {
+      const int i = base + lane;
       uint32_t k = 0;
       bool act = false;
       if (i < m) {
@@ -358,34 +391,31 @@ __device__ inline uint32_t block_kth_u32(const uint32_t* src, int m, int rank, u
       }
       hist_add(hist, (int)((k >> shift) & 255), act);
     }
-    __syncthreads();
-    find_bucket(hist, rank, res);
-    __syncthreads();
-    const int b = res[0], below = res[1];
-    cnt = res[2];
-    __syncthreads();
+    __syncwarp();
+    int b, below;
+    warp_find_bucket(hist, rank, b, below, cnt);
+    __syncwarp();
     prefix |= (uint32_t)b << shift;
     mask |= 0xFFu << shift;
     rank -= below;
   }
   if (mask == 0xFFFFFFFFu) return prefix;
-  if (threadIdx.x == 0) res[3] = 0;
-  __syncthreads();
-  for (int base = 0; base < m; base += T) {
-    const int i = base + threadIdx.x;
+  int ns = 0;
+  for (int base = 0; base < m; base += 32) {
+    const int i = base + lane;
     uint32_t k = 0;
     if (i < m) k = src[i];
-    block_append(small, &res[3], kSelectSmall, (uint64_t)k, i < m && (k & mask) == prefix);
+    const bool eq = i < m && (k & mask) == prefix;
+    const uint32_t meq = __ballot_sync(0xffffffffu, eq);
+    if (eq) {
+      const int p = ns + __popc(meq & lt);
+      if (p < 32) small[p] = k;
+    }
+    ns += __popc(meq);
   }
-  __syncthreads();
-  const int nb = min(res[3], kSelectSmall);
-  const int sp = next_pow2(max(nb, 1));
-  for (int i = nb + threadIdx.x; i < sp; i += T) small[i] = kU64Max;
-  __syncthreads();
-  block_bitonic_sort(small, sp);
-  const uint32_t v = (uint32_t)small[rank - 1];
-  __syncthreads();
-  return v;
+  __syncwarp();
+  const uint64_t v = warp_sort32(lane < min(ns, 32) ? small[lane] : kU64Max);
+  return (uint32_t)__shfl_sync(0xffffffffu, v, rank - 1);
 }
 
 }  // namespace rq

@@ -79,7 +79,8 @@ struct Workspace {
   int32_t* list_count = nullptr;  // nlist: pairs probing each list
   int32_t* list_pairs = nullptr;  // nlist x nq: pair ids (q * npmax + p) per list
   int32_t* work_count = nullptr;  // work-item counter of the persistent scan
-  uint8_t* qdig = nullptr;        // nq x npmax x D_p: query digits as FP8 (MMA scan)
+  uint8_t* qdig = nullptr;        // nlist x nq x D_p: per-list buckets of FP8 query digits
+  float4* qpb = nullptr;          // nlist x nq: per-list buckets of quantisation parameters
   int64_t cap = 0;                // candidate slots per query
 };
 

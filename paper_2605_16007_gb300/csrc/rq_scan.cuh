@@ -84,6 +84,45 @@ __device__ __forceinline__ void append_candidates(bool pass, float d, int64_t s,
   }
 }
 
+// Append for a chunk of J pairs at once: bit j of `passbits` says whether
+// this lane's vector (slot s) passes for pair j, whose query is qid[j] and
+// estimate d[j]. Lane 0 issues the chunk's counter atomics back to back (they
+// are independent), then every lane writes its survivors. All 32 lanes must
+// call it.
+template <int J>
+__device__ __forceinline__ void append_chunk(uint32_t passbits, const float (&d)[J],
+                                             const int32_t* qid, int64_t s,
+                                             const uint32_t* __restrict__ ids,
+                                             int32_t* counts, uint64_t* cand, int64_t cap,
+                                             int lane, int32_t* err) {
+  uint32_t mk[J];
+  int any = 0;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    mk[j] = __ballot_sync(0xffffffffu, (passbits >> j) & 1u);
+    any |= mk[j] != 0;
+  }
+  if (!any) return;
+  int base[J];
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < J; ++j) base[j] = mk[j] ? atomicAdd(counts + qid[j], __popc(mk[j])) : 0;
+  }
+  const uint32_t id = passbits ? ids[s] : 0u;
+  const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int b = __shfl_sync(0xffffffffu, base[j], 0);
+    if ((passbits >> j) & 1u) {
+      const int64_t pos = (int64_t)b + __popc(mk[j] & lt);
+      if (pos < cap)
+        cand[(int64_t)qid[j] * cap + pos] = make_key(d[j], id);
+      else
+        flag_error(err, kErrCandidateOverflow);
+    }
+  }
+}
+
 // FP8 E4M3 encoding of an integer 0..15 (exact): v = 2^e (1 + m/8) with
 // e = floor(log2 v), stored as (e + 7) << 3 | m; 0 encodes as 0.
 __device__ __forceinline__ uint8_t e4m3_of_int(int v) {

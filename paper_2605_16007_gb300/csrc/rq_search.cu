@@ -24,8 +24,6 @@ inline unsigned blocks_for(int64_t n, int per) {
   return (unsigned)std::max<int64_t>(1, (n + per - 1) / per);
 }
 
-__device__ __forceinline__ int next_pow2_dev(int v) { return next_pow2(v); }
-
 // Optional CUDA events at stage boundaries: ev[s] marks the start of stage s,
 // ev[RQ_STAGE_COUNT] the end of the search.
 struct StageTimer {
@@ -158,7 +156,8 @@ quantize_kernel(const float* __restrict__ qrot, const int32_t* __restrict__ prob
                 const int32_t* __restrict__ nprobe, int npmax, int64_t nq,
                 const float* __restrict__ cR, int dp, float4* __restrict__ qparams,
                 uint32_t* __restrict__ planes, int32_t* __restrict__ list_count,
-                int32_t* __restrict__ list_pairs, uint8_t* __restrict__ qdig, int32_t* err) {
+                int32_t* __restrict__ list_pairs, uint8_t* __restrict__ qdb,
+                float4* __restrict__ qpb, int32_t* err) {
   constexpr int PER = 4 * NW4;  // values per lane (dp / 32)
   const int64_t pair = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -170,6 +169,13 @@ quantize_kernel(const float* __restrict__ qrot, const int32_t* __restrict__ prob
   if (c < 0) {
     if (lane == 0) flag_error(err, kErrBadProbe);
     return;
+  }
+  // Grouped scans: the pair takes the next slot of its list's bucket (room
+  // for every query of the batch).
+  int slot = 0;
+  if (list_count) {
+    if (lane == 0) slot = atomicAdd(&list_count[c], 1);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
   }
   float r[PER];
   float vl = __int_as_float(0x7f800000), vr = -vl, acc = 0.0f;
@@ -199,7 +205,14 @@ quantize_kernel(const float* __restrict__ qrot, const int32_t* __restrict__ prob
       qu = min(qu, 15);
     }
     sq += qu;
-    if (qdig) qdig[pair * dp + lane + 32 * i] = e4m3_of_int(qu);
+    if (qdb) {
+      // The tensor-core scan's B rows: FP8 digits in the 128B-swizzled row
+      // layout (16-byte chunk d/16 of bucket row `slot` at chunk position
+      // (d/16) ^ (slot % 8)), so that one bulk copy lands them in place.
+      const int d = lane + 32 * i;
+      qdb[((int64_t)c * nq + slot) * dp + ((((d >> 4) ^ (slot & 7))) << 4) + (d & 15)] =
+          e4m3_of_int(qu);
+    }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const uint32_t w = __ballot_sync(0xffffffffu, (qu >> j) & 1);
@@ -208,58 +221,13 @@ quantize_kernel(const float* __restrict__ qrot, const int32_t* __restrict__ prob
   }
   sq = warp_sum_int(sq);
   if (lane == 0) {
-    qparams[pair] = make_float4(vl, delta, nq2, __int_as_float(sq));
-    // Grouped scans: the pair joins the bucket of its list (room for every
-    // query of the batch).
-    if (list_count) list_pairs[(int64_t)c * nq + atomicAdd(&list_count[c], 1)] = (int32_t)pair;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// First bound (Section 3.3.3): lists in probe order give the first
-// max(1024, n_sel) candidates; the bound is the n_sel-th smallest of their
-// orderable estimates (all ones when the query has fewer than n_sel).
-// ---------------------------------------------------------------------------
-template <int NW4>
-__global__ void __launch_bounds__(256)
-bound_kernel(const int32_t* __restrict__ probe_ids, const int32_t* __restrict__ nprobe,
-             int npmax, const int32_t* __restrict__ nsel,
-             const float4* __restrict__ qparams, const uint32_t* __restrict__ planes,
-             const int64_t* __restrict__ offsets, const uint8_t* __restrict__ codes,
-             const float2* __restrict__ fac, int dp, uint32_t* __restrict__ bound,
-             const int32_t* __restrict__ no_prune) {
-  constexpr int W = 4 * NW4;
-  __shared__ uint32_t s_keys[kMaxSelect];
-  __shared__ __align__(16) uint32_t s_pl[4 * W];
-  __shared__ int hist[256];
-  __shared__ int res[4];
-  __shared__ uint64_t small[kSelectSmall];
-  const int64_t q = blockIdx.x;
-  const int n_sel = nsel[q];
-  if (*no_prune || n_sel <= 0) {
-    if (threadIdx.x == 0) bound[q] = kU32Max;
-    return;
-  }
-  const int cap1 = max(kBoundCandidates, n_sel);
-  int taken = 0;
-  for (int p = 0; p < nprobe[q] && taken < cap1; ++p) {
-    const int64_t pair = q * npmax + p;
-    const int c = probe_ids[pair];
-    const int64_t lo = offsets[c];
-    const int m = (int)min(offsets[c + 1] - lo, (int64_t)(cap1 - taken));
-    for (int i = threadIdx.x; i < 4 * W; i += blockDim.x) s_pl[i] = planes[pair * 4 * W + i];
-    __syncthreads();
-    const float4 qp = qparams[pair];
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      const uint4* cp = reinterpret_cast<const uint4*>(codes + (lo + i) * (dp / 8));
-      s_keys[taken + i] = orderable(estimate_code<NW4>(cp, fac[lo + i], s_pl, qp, dp));
+    const float4 qp = make_float4(vl, delta, nq2, __int_as_float(sq));
+    qparams[pair] = qp;
+    if (list_count) {
+      list_pairs[(int64_t)c * nq + slot] = (int32_t)pair;
+      if (qpb) qpb[(int64_t)c * nq + slot] = qp;
     }
-    taken += m;
-    __syncthreads();
   }
-  uint32_t tau = kU32Max;
-  if (taken >= n_sel) tau = block_kth_u32(s_keys, taken, n_sel, small, hist, res);
-  if (threadIdx.x == 0) bound[q] = tau;
 }
 
 // ---------------------------------------------------------------------------
@@ -379,15 +347,19 @@ scan_grouped_kernel(const int2* __restrict__ items, int n_items, int32_t* __rest
         s_tau[g] = bound[q];
       }
       __syncthreads();
-      for (int g = 0; g < np; ++g) {
-        float d = 0.0f;
-        bool pass = false;
-        if (valid) {
-          d = estimate_regs<NW4>(code, pc, f, s_pl[g], s_qp[g], dp);
-          pass = orderable(d) <= s_tau[g];
+      for (int g0c = 0; g0c < np; g0c += 16) {
+        float d[16];
+        uint32_t passbits = 0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int g = g0c + j;
+          d[j] = 0.0f;
+          if (valid && g < np) {
+            d[j] = estimate_regs<NW4>(code, pc, f, s_pl[g], s_qp[g], dp);
+            if (orderable(d[j]) <= s_tau[g]) passbits |= 1u << j;
+          }
         }
-        const int q = s_q[g];
-        append_candidates(pass, d, s, ids, counts + q, cand + (int64_t)q * cap, cap, lane, err);
+        append_chunk<16>(passbits, d, s_q + g0c, s, ids, counts, cand, cap, lane, err);
       }
       __syncthreads();
     }
@@ -430,39 +402,6 @@ rotate16_kernel(const float* __restrict__ q, int64_t nq, int dim, const float* _
   if (row < nq) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) qrot[row * dp + col0 + cg + 16 * j] = acc[j];
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Probe selection: the nprobe smallest (distance, list) keys of each query,
-// one block of 128 threads per query (radix selection, then a sort of the
-// selected keys only).
-// ---------------------------------------------------------------------------
-constexpr int kProbeSmemKeys = 2048;
-
-__global__ void __launch_bounds__(128)
-probe_select_kernel(const uint64_t* __restrict__ pkeys, int nlist, int np,
-                    int32_t* __restrict__ out_ids, float* __restrict__ out_d) {
-  extern __shared__ uint64_t s_dyn[];
-  __shared__ int hist[256];
-  __shared__ int res[4];
-  __shared__ uint64_t small[kSelectSmall];
-  const int64_t row = blockIdx.x;
-  const uint64_t* src = pkeys + row * nlist;
-  uint64_t* dst = s_dyn;
-  if (nlist <= kProbeSmemKeys) {
-    uint64_t* keys = s_dyn;
-    for (int i = threadIdx.x; i < nlist; i += blockDim.x) keys[i] = src[i];
-    __syncthreads();
-    src = keys;
-    dst = s_dyn + nlist;
-  }
-  const int got = block_select_smallest(src, nlist, np, dst, small, hist, res);
-  for (int j = threadIdx.x; j < np; j += blockDim.x) {
-    const uint64_t k = (j < got) ? dst[j] : kU64Max;
-    out_ids[row * np + j] = (k == kU64Max) ? -1 : (int32_t)(uint32_t)k;
-    out_d[row * np + j] =
-        (k == kU64Max) ? __int_as_float(0x7f800000) : from_orderable((uint32_t)(k >> 32));
   }
 }
 
@@ -527,62 +466,161 @@ __device__ __forceinline__ float exact_dist_lanes(const RawT* __restrict__ x,
 }
 
 // ---------------------------------------------------------------------------
-// Candidate selection fused with the exact re-rank (Section 3.3.4): one
-// block per query selects its n_sel smallest estimate keys (written, sorted,
-// to `sel`), computes their exact distances (one thread per candidate), and
-// writes the k smallest (distance, id); without re-rank, the estimates.
+// One warp per query: probe selection, first bound, and candidate selection
+// fused with the exact re-rank. Warps only synchronise with themselves, so a
+// block of several warps serves several queries at once.
 // ---------------------------------------------------------------------------
+
+// Per-warp shared memory of the finalize kernel: selection (P keys), top-k
+// (PK keys), histogram (256 ints), bucket (32 keys), query row (dim floats).
+struct FinalizeLayout {
+  int P, PK, S, dim;  // S: candidate keys staged per warp
+  __host__ __device__ int bytes() const {
+    return (P + PK + S) * 8 + 256 * 4 + 32 * 8 + ((dim * 4 + 15) & ~15);
+  }
+};
+
 template <typename RawT>
-__global__ void __launch_bounds__(256, 4)
-finalize_kernel(const uint64_t* __restrict__ cand, int64_t cap, const int32_t* __restrict__ counts,
-                const int32_t* __restrict__ nsel, const int32_t* __restrict__ kq,
-                const int32_t* __restrict__ rerank_on, int nsel_max, uint64_t* __restrict__ sel,
-                const RawT* __restrict__ raw, const float* __restrict__ q, int dim, int k_stride,
-                int64_t* __restrict__ out_ids, float* __restrict__ out_d, int32_t* err) {
-  extern __shared__ uint64_t s_dyn[];
-  __shared__ int hist[256];
-  __shared__ int res[4];
-  __shared__ uint64_t small[kSelectSmall];
-  const int64_t row = blockIdx.x;
+__global__ void __launch_bounds__(256)
+finalize_warp_kernel(const uint64_t* __restrict__ cand, int64_t cap,
+                     const int32_t* __restrict__ counts, const int32_t* __restrict__ nsel,
+                     const int32_t* __restrict__ kq, const int32_t* __restrict__ rerank_on,
+                     int nsel_max, uint64_t* __restrict__ sel, const RawT* __restrict__ raw,
+                     const float* __restrict__ q, int dim, int k_stride, int64_t nq,
+                     FinalizeLayout lay, int64_t* __restrict__ out_ids,
+                     float* __restrict__ out_d, int32_t* err) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (row >= nq) return;
+  uint8_t* base = smem + (size_t)warp * lay.bytes();
+  uint64_t* s_sel = reinterpret_cast<uint64_t*>(base);
+  uint64_t* s_top = s_sel + lay.P;
+  int* hist = reinterpret_cast<int*>(s_top + lay.PK);
+  uint64_t* small = reinterpret_cast<uint64_t*>(hist + 256);
+  uint64_t* s_stage = small + 32;
+  float* s_q = reinterpret_cast<float*>(s_stage + lay.S);
   int64_t count = counts[row];
   if (count > cap) {
-    if (threadIdx.x == 0) flag_error(err, kErrCandidateOverflow);
+    if (lane == 0) flag_error(err, kErrCandidateOverflow);
     count = cap;
   }
   const int n_sel = nsel[row];
   const int k = kq[row];
-  uint64_t* s_sel = s_dyn;
-  float* s_q = reinterpret_cast<float*>(s_dyn + next_pow2_dev(nsel_max));
   const bool rerank = rerank_on[row] != 0;
   // Without re-rank the selection is the answer and is sorted; with re-rank
-  // only the set matters and the exact keys are sorted below.
-  const int got = block_select_smallest(cand + row * cap, (int)count, n_sel, s_sel, small, hist,
-                                        res, !rerank);
-  for (int j = threadIdx.x; j < nsel_max; j += blockDim.x)
-    sel[row * nsel_max + j] = (j < got) ? s_sel[j] : kU64Max;
+  // only the set matters and the exact keys are selected below.
+  // Candidates that fit are read once (independent loads) into the warp's
+  // shared memory; the radix passes then read them there.
+  const uint64_t* src = cand + row * cap;
+  if (count <= lay.S && count > n_sel) {
+    for (int i = lane; i < count; i += 32) s_stage[i] = src[i];
+    __syncwarp();
+    src = s_stage;
+  }
+  const int got = warp_select_smallest(src, (int)count, n_sel, s_sel, hist, small, !rerank);
+  for (int j = lane; j < nsel_max; j += 32) sel[row * nsel_max + j] = (j < got) ? s_sel[j] : kU64Max;
   const float inf = __int_as_float(0x7f800000);
-  if (!rerank) {
-    for (int j = threadIdx.x; j < k_stride; j += blockDim.x) {
-      const uint64_t key = (j < k && j < got) ? s_sel[j] : kU64Max;
-      out_ids[row * k_stride + j] = (key == kU64Max) ? -1 : (int64_t)(uint32_t)key;
-      out_d[row * k_stride + j] = (key == kU64Max) ? inf : from_orderable((uint32_t)(key >> 32));
+  const uint64_t* res = s_sel;
+  int kk = min(k, got);
+  if (rerank) {
+    for (int d = lane; d < dim; d += 32) s_q[d] = q[row * dim + d];
+    __syncwarp();
+    for (int i = lane; i < got; i += 32) {
+      const uint32_t id = (uint32_t)s_sel[i];
+      const float dist = exact_dist_lanes<RawT>(raw + (int64_t)id * dim, s_q, dim);
+      s_sel[i] = make_key(dist, id);
     }
-    return;
+    __syncwarp();
+    kk = warp_select_smallest(s_sel, got, k, s_top, hist, small, true);
+    res = s_top;
   }
-  for (int d = threadIdx.x; d < dim; d += blockDim.x) s_q[d] = q[row * dim + d];
-  __syncthreads();
-  for (int i = threadIdx.x; i < got; i += blockDim.x) {
-    const uint32_t id = (uint32_t)s_sel[i];
-    const float dist = exact_dist_lanes<RawT>(raw + (int64_t)id * dim, s_q, dim);
-    s_sel[i] = make_key(dist, id);
-  }
-  __syncthreads();
-  block_bitonic_sort(s_sel, next_pow2(max(got, 1)));
-  for (int j = threadIdx.x; j < k_stride; j += blockDim.x) {
-    const uint64_t key = (j < k && j < got) ? s_sel[j] : kU64Max;
+  for (int j = lane; j < k_stride; j += 32) {
+    const uint64_t key = (j < kk) ? res[j] : kU64Max;
     out_ids[row * k_stride + j] = (key == kU64Max) ? -1 : (int64_t)(uint32_t)key;
     out_d[row * k_stride + j] = (key == kU64Max) ? inf : from_orderable((uint32_t)(key >> 32));
   }
+}
+
+// Probe selection: the np smallest (distance, list) keys of each query.
+constexpr int kProbeStageKeys = 2048;
+
+__global__ void __launch_bounds__(256)
+probe_select_warp_kernel(const uint64_t* __restrict__ pkeys, int nlist, int np, int64_t nq,
+                         int32_t* __restrict__ out_ids, float* __restrict__ out_d) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (row >= nq) return;
+  const int P = next_pow2(np);
+  const int S = nlist <= kProbeStageKeys ? nlist : 0;
+  uint8_t* base = smem + (size_t)warp * ((P + S) * 8 + 256 * 4 + 32 * 8);
+  uint64_t* dst = reinterpret_cast<uint64_t*>(base);
+  int* hist = reinterpret_cast<int*>(dst + P);
+  uint64_t* small = reinterpret_cast<uint64_t*>(hist + 256);
+  const uint64_t* src = pkeys + row * nlist;
+  if (S) {
+    uint64_t* stage = small + 32;
+    for (int i = lane; i < nlist; i += 32) stage[i] = src[i];
+    __syncwarp();
+    src = stage;
+  }
+  const int got = warp_select_smallest(src, nlist, np, dst, hist, small, true);
+  for (int j = lane; j < np; j += 32) {
+    const uint64_t k = (j < got) ? dst[j] : kU64Max;
+    out_ids[row * np + j] = (k == kU64Max) ? -1 : (int32_t)(uint32_t)k;
+    out_d[row * np + j] =
+        (k == kU64Max) ? __int_as_float(0x7f800000) : from_orderable((uint32_t)(k >> 32));
+  }
+}
+
+// First bound (Section 3.3.3), one warp per query: lists in probe order give
+// the first max(1024, n_sel) candidates; the bound is the n_sel-th smallest
+// orderable estimate among them (all ones when the query has fewer).
+template <int NW4>
+__global__ void __launch_bounds__(256)
+bound_warp_kernel(const int32_t* __restrict__ probe_ids, const int32_t* __restrict__ nprobe,
+                  int npmax, const int32_t* __restrict__ nsel, const float4* __restrict__ qparams,
+                  const uint32_t* __restrict__ planes, const int64_t* __restrict__ offsets,
+                  const uint8_t* __restrict__ codes, const float2* __restrict__ fac, int dp,
+                  int keys_per_warp, int64_t nq, uint32_t* __restrict__ bound,
+                  const int32_t* __restrict__ no_prune) {
+  constexpr int W = 4 * NW4;
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t qi = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (qi >= nq) return;
+  uint8_t* base = smem + (size_t)warp * (keys_per_warp * 4 + 4 * W * 4 + 256 * 4 + 32 * 8);
+  uint32_t* s_keys = reinterpret_cast<uint32_t*>(base);
+  uint32_t* s_pl = s_keys + keys_per_warp;
+  int* hist = reinterpret_cast<int*>(s_pl + 4 * W);
+  uint64_t* small = reinterpret_cast<uint64_t*>(hist + 256);
+  const int n_sel = nsel[qi];
+  if (*no_prune || n_sel <= 0) {
+    if (lane == 0) bound[qi] = kU32Max;
+    return;
+  }
+  const int cap1 = max(kBoundCandidates, n_sel);
+  int taken = 0;
+  for (int p = 0; p < nprobe[qi] && taken < cap1; ++p) {
+    const int64_t pair = qi * npmax + p;
+    const int c = probe_ids[pair];
+    const int64_t lo = offsets[c];
+    const int m = (int)min(offsets[c + 1] - lo, (int64_t)(cap1 - taken));
+    __syncwarp();
+    for (int i = lane; i < 4 * W; i += 32) s_pl[i] = planes[pair * 4 * W + i];
+    __syncwarp();
+    const float4 qp = qparams[pair];
+    for (int i = lane; i < m; i += 32) {
+      const uint4* cp = reinterpret_cast<const uint4*>(codes + (lo + i) * (dp / 8));
+      s_keys[taken + i] = orderable(estimate_code<NW4>(cp, fac[lo + i], s_pl, qp, dp));
+    }
+    taken += m;
+  }
+  __syncwarp();
+  uint32_t tau = kU32Max;
+  if (taken >= n_sel) tau = warp_kth_u32(s_keys, taken, n_sel, hist, small);
+  if (lane == 0) bound[qi] = tau;
 }
 
 // ---------------------------------------------------------------------------
@@ -633,7 +671,10 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
     L.take(&ws.list_pairs, (int64_t)ix->nlist * nq);
     L.take(&ws.work_count, 4);
   }
-  if (sh.mode == RQ_SCAN_MMA) L.take(&ws.qdig, nq * np * ix->dp);
+  if (sh.mode == RQ_SCAN_MMA) {
+    L.take(&ws.qdig, (int64_t)ix->nlist * nq * ix->dp);
+    L.take(&ws.qpb, (int64_t)ix->nlist * nq);
+  }
   ws.bytes = L.off;
   (void)st;
   cudaError_t e = cudaMalloc(&ws.base, ws.bytes);
@@ -665,7 +706,10 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
     rebase(ws.list_pairs, b);
     rebase(ws.work_count, b);
   }
-  if (sh.mode == RQ_SCAN_MMA) rebase(ws.qdig, b);
+  if (sh.mode == RQ_SCAN_MMA) {
+    rebase(ws.qdig, b);
+    rebase(ws.qpb, b);
+  }
   return RQ_OK;
 }
 
@@ -682,11 +726,18 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
   quantize_kernel<NW4><<<blocks_for(pairs * 32, 256), 256, 0, st>>>(
       ws.qrot, ws.probe_ids, ws.nprobe, np, nq, ix->cR, dp, ws.qparams, ws.planes,
       grouped ? ws.list_count : nullptr, ws.list_pairs,
-      sh.mode == RQ_SCAN_MMA ? ws.qdig : nullptr, ix->d_err);
+      sh.mode == RQ_SCAN_MMA ? ws.qdig : nullptr, sh.mode == RQ_SCAN_MMA ? ws.qpb : nullptr,
+      ix->d_err);
   tm.mark(RQ_STAGE_BOUND, st);
-  bound_kernel<NW4><<<(unsigned)nq, 256, 0, st>>>(ws.probe_ids, ws.nprobe, np, ws.nsel, ws.qparams,
-                                                 ws.planes, ix->offsets, ix->codes, ix->fac, dp,
-                                                 ws.bound, ws.rerank_on + nq);
+  {
+    const int kpw = std::max(kBoundCandidates, sh.nsel_max);
+    const int per_warp = kpw * 4 + 4 * (4 * NW4) * 4 + 256 * 4 + 32 * 8;
+    const int wpb = std::max(1, std::min(8, (48 * 1024) / per_warp));
+    const size_t smem = (size_t)wpb * per_warp;
+    bound_warp_kernel<NW4><<<blocks_for(nq, wpb), wpb * 32, smem, st>>>(
+        ws.probe_ids, ws.nprobe, np, ws.nsel, ws.qparams, ws.planes, ix->offsets, ix->codes,
+        ix->fac, dp, kpw, nq, ws.bound, ws.rerank_on + nq);
+  }
   RQ_CUDA(cudaMemsetAsync(ws.counts, 0, sizeof(int32_t) * nq, st));
   tm.mark(RQ_STAGE_WORKLIST, st);
   if (sh.mode == RQ_SCAN_PLAIN) {
@@ -725,10 +776,17 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
   pair_dist_kernel<1, 2><<<dim3(blocks_for(nq, 32), blocks_for(ix->nlist, 64)), 256, 0, st>>>(
       ws.qrot, nq, ix->cR, ix->nlist, dp, nullptr, nullptr, ws.pkeys);
   {
-    const size_t smem = sizeof(uint64_t) * ((ix->nlist <= kProbeSmemKeys ? ix->nlist : 0) +
-                                            next_pow2_host(np));
-    probe_select_kernel<<<(unsigned)nq, 128, smem, st>>>(ws.pkeys, ix->nlist, np, ws.probe_ids,
-                                                        ws.probe_d);
+    const int stage = ix->nlist <= kProbeStageKeys ? ix->nlist : 0;
+    const int per_warp = (next_pow2_host(np) + stage) * 8 + 256 * 4 + 32 * 8;
+    const int wpb = std::max(1, std::min(8, (64 * 1024) / per_warp));
+    static bool attr = false;
+    if (!attr) {
+      RQ_CUDA(cudaFuncSetAttribute(probe_select_warp_kernel,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      attr = true;
+    }
+    probe_select_warp_kernel<<<blocks_for(nq, wpb), wpb * 32, (size_t)wpb * per_warp, st>>>(
+        ws.pkeys, ix->nlist, np, nq, ws.probe_ids, ws.probe_d);
   }
   // 3-4. quantisation, bound, scan
   switch (dp / 128) {
@@ -749,17 +807,29 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
   // 5-6. candidate selection and exact re-rank
   tm.mark(RQ_STAGE_SELECT, st);
   {
-    const size_t smem = sizeof(uint64_t) * next_pow2_host(sh.nsel_max) + sizeof(float) * ix->dim;
+    const FinalizeLayout lay{next_pow2_host(sh.nsel_max), next_pow2_host(sh.k_stride), 1024,
+                             ix->dim};
+    const int per_warp = lay.bytes();
+    const int wpb = std::max(1, std::min(8, (64 * 1024) / per_warp));
+    const size_t smem = (size_t)wpb * per_warp;
+    static bool attr = false;
+    if (!attr) {
+      RQ_CUDA(cudaFuncSetAttribute(finalize_warp_kernel<uint8_t>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      RQ_CUDA(cudaFuncSetAttribute(finalize_warp_kernel<float>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      attr = true;
+    }
     if (ix->raw_dtype == RQ_U8)
-      finalize_kernel<uint8_t><<<(unsigned)nq, 256, smem, st>>>(
+      finalize_warp_kernel<uint8_t><<<blocks_for(nq, wpb), wpb * 32, smem, st>>>(
           ws.cand, ws.cap, ws.counts, ws.nsel, ws.kq, ws.rerank_on, sh.nsel_max, ws.sel,
-          static_cast<const uint8_t*>(ix->raw), ws.q, ix->dim, sh.k_stride, ws.out_ids, ws.out_d,
-          ix->d_err);
+          static_cast<const uint8_t*>(ix->raw), ws.q, ix->dim, sh.k_stride, nq, lay, ws.out_ids,
+          ws.out_d, ix->d_err);
     else
-      finalize_kernel<float><<<(unsigned)nq, 256, smem, st>>>(
+      finalize_warp_kernel<float><<<blocks_for(nq, wpb), wpb * 32, smem, st>>>(
           ws.cand, ws.cap, ws.counts, ws.nsel, ws.kq, ws.rerank_on, sh.nsel_max, ws.sel,
-          static_cast<const float*>(ix->raw), ws.q, ix->dim, sh.k_stride, ws.out_ids, ws.out_d,
-          ix->d_err);
+          static_cast<const float*>(ix->raw), ws.q, ix->dim, sh.k_stride, nq, lay, ws.out_ids,
+          ws.out_d, ix->d_err);
   }
   tm.mark(RQ_STAGE_RERANK, st);
   tm.mark(RQ_STAGE_COUNT, st);
