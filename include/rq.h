@@ -82,7 +82,11 @@ typedef enum rq_scan_mode {
 typedef struct rq_build_opts {
   int32_t kmeans_iters; /* Lloyd iterations (default 10; 0 keeps the
                            initial rows as centroids) */
-  int32_t reserved0;
+  int32_t keep_float_raw; /* 0 (default): a float32 base whose values are
+                           all integers in [0, 255] is kept for the re-rank
+                           as uint8 (lossless: every re-rank distance is
+                           unchanged, the gather reads 4x fewer bytes);
+                           1: always keep float32 */
   int64_t train_size;   /* rows of the k-means training subset; 0 = all rows */
 } rq_build_opts;
 

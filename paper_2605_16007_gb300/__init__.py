@@ -32,7 +32,7 @@ class RQError(RuntimeError):
 
 
 class BuildOpts(C.Structure):
-    _fields_ = [("kmeans_iters", C.c_int32), ("reserved0", C.c_int32),
+    _fields_ = [("kmeans_iters", C.c_int32), ("keep_float_raw", C.c_int32),
                 ("train_size", C.c_int64)]
 
 
@@ -170,9 +170,9 @@ def _is_u8(a):
 
 # ------------------------------------------------------------------ C names
 def rq_build(base, nlist: int, seed: int, kmeans_iters: int = 10,
-             train_size: int = 0) -> "Index":
+             train_size: int = 0, keep_float_raw: bool = False) -> "Index":
     n, dim = _shape(base)
-    opts = BuildOpts(kmeans_iters, 0, train_size)
+    opts = BuildOpts(kmeans_iters, int(keep_float_raw), train_size)
     h = C.c_void_p()
     _check(lib().rq_build(_ptr(base), RQ_U8 if _is_u8(base) else RQ_F32, n, dim, nlist,
                           seed, C.byref(opts), C.byref(h)))

@@ -43,6 +43,20 @@ __global__ void count_nonfinite_kernel(const float* x, int64_t n, int32_t* out) 
   if (i < n && !isfinite(x[i])) atomicAdd(out, 1);
 }
 
+// Counts values that are not integers in [0, 255].
+__global__ void count_non_byte_kernel(const float* x, int64_t n, int32_t* out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float v = x[i];
+    if (!(v >= 0.0f && v <= 255.0f && v == rintf(v))) atomicAdd(out, 1);
+  }
+}
+
+__global__ void f32_to_u8_kernel(const float* a, uint8_t* b, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (uint8_t)a[i];
+}
+
 __global__ void u8_to_f32_kernel(const uint8_t* a, float* b, int64_t n) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
@@ -121,9 +135,37 @@ rq_status check_build_args(const void* base, rq_dtype dt, int64_t n, int32_t dim
   return RQ_OK;
 }
 
+// A float32 raw copy whose values are all integers in [0, 255] is replaced
+// by a uint8 copy: the re-rank converts each byte back to the same float.
+rq_status compress_raw(rq_index* ix) {
+  if (ix->raw_dtype != RQ_F32) return RQ_OK;
+  const int64_t count = ix->n * ix->dim;
+  int32_t* cnt = nullptr;
+  RQ_CUDA(cudaMalloc(&cnt, sizeof(int32_t)));
+  cudaMemset(cnt, 0, sizeof(int32_t));
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, (count + 255) / 256);
+  count_non_byte_kernel<<<blocks, 256>>>(static_cast<const float*>(ix->raw), count, cnt);
+  int32_t h = 1;
+  cudaError_t e = cudaMemcpy(&h, cnt, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  cudaFree(cnt);
+  if (e != cudaSuccess) return cuda_fail(e, "raw check", __FILE__, __LINE__);
+  if (h != 0) return RQ_OK;
+  uint8_t* r8 = nullptr;
+  if (cudaMalloc(&r8, (size_t)count + 16) != cudaSuccess) {
+    cudaGetLastError();
+    return RQ_OK;  // keep the float copy
+  }
+  f32_to_u8_kernel<<<blocks, 256>>>(static_cast<const float*>(ix->raw), r8, count);
+  RQ_CUDA(cudaDeviceSynchronize());
+  cudaFree(ix->raw);
+  ix->raw = r8;
+  ix->raw_dtype = RQ_U8;
+  return RQ_OK;
+}
+
 rq_status build_common(const void* base, rq_dtype dt, int64_t n, int32_t dim, int32_t nlist,
                        uint64_t seed, int iters, int64_t train, const float* cent,
-                       const double* P, rq_index** out) {
+                       const double* P, rq_index** out, bool keep_float_raw = false) {
   RQ_TRY(check_build_args(base, dt, n, dim, nlist, out));
   *out = nullptr;
   std::unique_ptr<rq_index> ix(new rq_index());
@@ -156,6 +198,7 @@ rq_status build_common(const void* base, rq_dtype dt, int64_t n, int32_t dim, in
   if (cent_tmp) cudaFree(cent_tmp);
   if (P_tmp) cudaFree(P_tmp);
   if (temp) cudaFree(d_f32);
+  if (s == RQ_OK && !keep_float_raw) s = compress_raw(ix.get());
   if (s != RQ_OK) {
     if (ix->raw == nullptr) cudaFree(d_raw);
     free_index_arrays(ix.get());
@@ -499,7 +542,8 @@ rq_status rq_build(const void* base, rq_dtype dtype, int64_t n, int32_t dim, int
   if (iters < 0) return fail(RQ_ERR_INVALID_ARG, "kmeans_iters < 0");
   if (train < 0) return fail(RQ_ERR_INVALID_ARG, "train_size < 0");
   if (train > 0 && train < nlist) return fail(RQ_ERR_INVALID_ARG, "train_size below nlist");
-  return build_common(base, dtype, n, dim, nlist, seed, iters, train, nullptr, nullptr, out);
+  return build_common(base, dtype, n, dim, nlist, seed, iters, train, nullptr, nullptr, out,
+                      opts && opts->keep_float_raw);
 }
 
 rq_status rq_build_with(const void* base, rq_dtype dtype, int64_t n, int32_t dim, int32_t nlist,

@@ -12,7 +12,7 @@
 #include <tuple>
 #include <vector>
 
-#include "../../include/rq.h"
+#include "rq.h"
 
 namespace rq {
 

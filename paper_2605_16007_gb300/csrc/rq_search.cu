@@ -417,12 +417,39 @@ __device__ __forceinline__ float exact_dist_lanes(const RawT* __restrict__ x,
 #pragma unroll
   for (int l = 0; l < 32; ++l) acc[l] = 0.0f;
   int d0 = 0;
-  for (; d0 + 32 <= dim; d0 += 32) {
-    if (sizeof(RawT) == 4 && (dim & 3) == 0) {
-      const float4* x4 = reinterpret_cast<const float4*>(x + d0);
+  if (sizeof(RawT) == 4 && (dim & 3) == 0) {
+    // float rows: two 32-dim chunks per step (sixteen 16-byte loads in
+    // flight), the terms added in increasing d (chunk d0, then d0 + 32).
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    for (; d0 + 64 <= dim; d0 += 64) {
+      float4 a[8], b[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) a[j] = __ldg(x4 + (d0 >> 2) + j);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) b[j] = __ldg(x4 + (d0 >> 2) + 8 + j);
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const float4 t = __ldg(x4 + j);
+        const float va[4] = {a[j].x, a[j].y, a[j].z, a[j].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float df = __fsub_rn(va[e], qs[d0 + 4 * j + e]);
+          acc[4 * j + e] = __fadd_rn(acc[4 * j + e], __fmul_rn(df, df));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float vb[4] = {b[j].x, b[j].y, b[j].z, b[j].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float df = __fsub_rn(vb[e], qs[d0 + 32 + 4 * j + e]);
+          acc[4 * j + e] = __fadd_rn(acc[4 * j + e], __fmul_rn(df, df));
+        }
+      }
+    }
+    for (; d0 + 32 <= dim; d0 += 32) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float4 t = __ldg(x4 + (d0 >> 2) + j);
         const float v[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -430,7 +457,9 @@ __device__ __forceinline__ float exact_dist_lanes(const RawT* __restrict__ x,
           acc[4 * j + e] = __fadd_rn(acc[4 * j + e], __fmul_rn(df, df));
         }
       }
-    } else if (sizeof(RawT) == 1 && (dim & 15) == 0) {
+    }
+  } else if (sizeof(RawT) == 1 && (dim & 15) == 0) {
+    for (; d0 + 32 <= dim; d0 += 32) {
       const uint4* x16 = reinterpret_cast<const uint4*>(x + d0);
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
@@ -443,7 +472,9 @@ __device__ __forceinline__ float exact_dist_lanes(const RawT* __restrict__ x,
           acc[16 * j + b] = __fadd_rn(acc[16 * j + b], __fmul_rn(df, df));
         }
       }
-    } else {
+    }
+  } else {
+    for (; d0 + 32 <= dim; d0 += 32) {
 #pragma unroll
       for (int l = 0; l < 32; ++l) {
         const float df = __fsub_rn((float)x[d0 + l], qs[d0 + l]);
@@ -480,21 +511,22 @@ struct FinalizeLayout {
   }
 };
 
+// Four warps per query: warp 0 selects (radix passes over the candidates
+// staged in shared memory), all 128 threads gather and re-rank, warp 0
+// selects the final k.
 template <typename RawT>
-__global__ void __launch_bounds__(256)
-finalize_warp_kernel(const uint64_t* __restrict__ cand, int64_t cap,
-                     const int32_t* __restrict__ counts, const int32_t* __restrict__ nsel,
-                     const int32_t* __restrict__ kq, const int32_t* __restrict__ rerank_on,
-                     int nsel_max, uint64_t* __restrict__ sel, const RawT* __restrict__ raw,
-                     const float* __restrict__ q, int dim, int k_stride, int64_t nq,
-                     FinalizeLayout lay, int64_t* __restrict__ out_ids,
-                     float* __restrict__ out_d, int32_t* err) {
+__global__ void __launch_bounds__(128)
+finalize_kernel(const uint64_t* __restrict__ cand, int64_t cap, const int32_t* __restrict__ counts,
+                const int32_t* __restrict__ nsel, const int32_t* __restrict__ kq,
+                const int32_t* __restrict__ rerank_on, int nsel_max, uint64_t* __restrict__ sel,
+                const RawT* __restrict__ raw, const float* __restrict__ q, int dim, int k_stride,
+                FinalizeLayout lay, int64_t* __restrict__ out_ids, float* __restrict__ out_d,
+                int32_t* err) {
   extern __shared__ __align__(16) uint8_t smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-  if (row >= nq) return;
-  uint8_t* base = smem + (size_t)warp * lay.bytes();
-  uint64_t* s_sel = reinterpret_cast<uint64_t*>(base);
+  __shared__ int s_got;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t row = blockIdx.x;
+  uint64_t* s_sel = reinterpret_cast<uint64_t*>(smem);
   uint64_t* s_top = s_sel + lay.P;
   int* hist = reinterpret_cast<int*>(s_top + lay.PK);
   uint64_t* small = reinterpret_cast<uint64_t*>(hist + 256);
@@ -502,40 +534,49 @@ finalize_warp_kernel(const uint64_t* __restrict__ cand, int64_t cap,
   float* s_q = reinterpret_cast<float*>(s_stage + lay.S);
   int64_t count = counts[row];
   if (count > cap) {
-    if (lane == 0) flag_error(err, kErrCandidateOverflow);
+    if (tid == 0) flag_error(err, kErrCandidateOverflow);
     count = cap;
   }
   const int n_sel = nsel[row];
   const int k = kq[row];
   const bool rerank = rerank_on[row] != 0;
-  // Without re-rank the selection is the answer and is sorted; with re-rank
-  // only the set matters and the exact keys are selected below.
-  // Candidates that fit are read once (independent loads) into the warp's
-  // shared memory; the radix passes then read them there.
+  // Candidates that fit are read once (independent loads) into shared
+  // memory; the radix passes then read them there.
   const uint64_t* src = cand + row * cap;
   if (count <= lay.S && count > n_sel) {
-    for (int i = lane; i < count; i += 32) s_stage[i] = src[i];
-    __syncwarp();
+    for (int i = tid; i < count; i += blockDim.x) s_stage[i] = src[i];
     src = s_stage;
   }
-  const int got = warp_select_smallest(src, (int)count, n_sel, s_sel, hist, small, !rerank);
-  for (int j = lane; j < nsel_max; j += 32) sel[row * nsel_max + j] = (j < got) ? s_sel[j] : kU64Max;
+  for (int d = tid; d < dim; d += blockDim.x) s_q[d] = q[row * dim + d];
+  __syncthreads();
+  // Without re-rank the selection is the answer and is sorted; with re-rank
+  // only the set matters and the exact keys are selected below.
+  if (warp == 0) {
+    const int got = warp_select_smallest(src, (int)count, n_sel, s_sel, hist, small, !rerank);
+    if (lane == 0) s_got = got;
+  }
+  __syncthreads();
+  const int got = s_got;
+  for (int j = tid; j < nsel_max; j += blockDim.x) sel[row * nsel_max + j] = (j < got) ? s_sel[j] : kU64Max;
   const float inf = __int_as_float(0x7f800000);
   const uint64_t* res = s_sel;
   int kk = min(k, got);
   if (rerank) {
-    for (int d = lane; d < dim; d += 32) s_q[d] = q[row * dim + d];
-    __syncwarp();
-    for (int i = lane; i < got; i += 32) {
+    for (int i = tid; i < got; i += blockDim.x) {
       const uint32_t id = (uint32_t)s_sel[i];
       const float dist = exact_dist_lanes<RawT>(raw + (int64_t)id * dim, s_q, dim);
       s_sel[i] = make_key(dist, id);
     }
-    __syncwarp();
-    kk = warp_select_smallest(s_sel, got, k, s_top, hist, small, true);
+    __syncthreads();
+    if (warp == 0) {
+      const int r = warp_select_smallest(s_sel, got, k, s_top, hist, small, true);
+      if (lane == 0) s_got = r;
+    }
+    __syncthreads();
+    kk = s_got;
     res = s_top;
   }
-  for (int j = lane; j < k_stride; j += 32) {
+  for (int j = tid; j < k_stride; j += blockDim.x) {
     const uint64_t key = (j < kk) ? res[j] : kU64Max;
     out_ids[row * k_stride + j] = (key == kU64Max) ? -1 : (int64_t)(uint32_t)key;
     out_d[row * k_stride + j] = (key == kU64Max) ? inf : from_orderable((uint32_t)(key >> 32));
@@ -574,30 +615,27 @@ probe_select_warp_kernel(const uint64_t* __restrict__ pkeys, int nlist, int np, 
   }
 }
 
-// First bound (Section 3.3.3), one warp per query: lists in probe order give
-// the first max(1024, n_sel) candidates; the bound is the n_sel-th smallest
-// orderable estimate among them (all ones when the query has fewer).
+// First bound (Section 3.3.3), four warps per query: lists in probe order
+// give the first max(1024, n_sel) candidates, estimated by all 128 threads;
+// warp 0 takes the n_sel-th smallest orderable estimate (all ones when the
+// query has fewer candidates).
 template <int NW4>
-__global__ void __launch_bounds__(256)
-bound_warp_kernel(const int32_t* __restrict__ probe_ids, const int32_t* __restrict__ nprobe,
-                  int npmax, const int32_t* __restrict__ nsel, const float4* __restrict__ qparams,
-                  const uint32_t* __restrict__ planes, const int64_t* __restrict__ offsets,
-                  const uint8_t* __restrict__ codes, const float2* __restrict__ fac, int dp,
-                  int keys_per_warp, int64_t nq, uint32_t* __restrict__ bound,
-                  const int32_t* __restrict__ no_prune) {
+__global__ void __launch_bounds__(128)
+bound_kernel(const int32_t* __restrict__ probe_ids, const int32_t* __restrict__ nprobe,
+             int npmax, const int32_t* __restrict__ nsel, const float4* __restrict__ qparams,
+             const uint32_t* __restrict__ planes, const int64_t* __restrict__ offsets,
+             const uint8_t* __restrict__ codes, const float2* __restrict__ fac, int dp,
+             uint32_t* __restrict__ bound, const int32_t* __restrict__ no_prune) {
   constexpr int W = 4 * NW4;
-  extern __shared__ __align__(16) uint8_t smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t qi = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-  if (qi >= nq) return;
-  uint8_t* base = smem + (size_t)warp * (keys_per_warp * 4 + 4 * W * 4 + 256 * 4 + 32 * 8);
-  uint32_t* s_keys = reinterpret_cast<uint32_t*>(base);
-  uint32_t* s_pl = s_keys + keys_per_warp;
-  int* hist = reinterpret_cast<int*>(s_pl + 4 * W);
-  uint64_t* small = reinterpret_cast<uint64_t*>(hist + 256);
+  extern __shared__ __align__(16) uint32_t s_bkeys[];
+  __shared__ __align__(16) uint32_t s_pl[4 * W];
+  __shared__ int hist[256];
+  __shared__ uint64_t small[32];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t qi = blockIdx.x;
   const int n_sel = nsel[qi];
   if (*no_prune || n_sel <= 0) {
-    if (lane == 0) bound[qi] = kU32Max;
+    if (tid == 0) bound[qi] = kU32Max;
     return;
   }
   const int cap1 = max(kBoundCandidates, n_sel);
@@ -607,20 +645,22 @@ bound_warp_kernel(const int32_t* __restrict__ probe_ids, const int32_t* __restri
     const int c = probe_ids[pair];
     const int64_t lo = offsets[c];
     const int m = (int)min(offsets[c + 1] - lo, (int64_t)(cap1 - taken));
-    __syncwarp();
-    for (int i = lane; i < 4 * W; i += 32) s_pl[i] = planes[pair * 4 * W + i];
-    __syncwarp();
+    __syncthreads();
+    for (int i = tid; i < 4 * W; i += blockDim.x) s_pl[i] = planes[pair * 4 * W + i];
+    __syncthreads();
     const float4 qp = qparams[pair];
-    for (int i = lane; i < m; i += 32) {
+    for (int i = tid; i < m; i += blockDim.x) {
       const uint4* cp = reinterpret_cast<const uint4*>(codes + (lo + i) * (dp / 8));
-      s_keys[taken + i] = orderable(estimate_code<NW4>(cp, fac[lo + i], s_pl, qp, dp));
+      s_bkeys[taken + i] = orderable(estimate_code<NW4>(cp, __ldg(fac + lo + i), s_pl, qp, dp));
     }
     taken += m;
   }
-  __syncwarp();
-  uint32_t tau = kU32Max;
-  if (taken >= n_sel) tau = warp_kth_u32(s_keys, taken, n_sel, hist, small);
-  if (lane == 0) bound[qi] = tau;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t tau = kU32Max;
+    if (taken >= n_sel) tau = warp_kth_u32(s_bkeys, taken, n_sel, hist, small);
+    if (tid == 0) bound[qi] = tau;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -731,12 +771,9 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
   tm.mark(RQ_STAGE_BOUND, st);
   {
     const int kpw = std::max(kBoundCandidates, sh.nsel_max);
-    const int per_warp = kpw * 4 + 4 * (4 * NW4) * 4 + 256 * 4 + 32 * 8;
-    const int wpb = std::max(1, std::min(8, (48 * 1024) / per_warp));
-    const size_t smem = (size_t)wpb * per_warp;
-    bound_warp_kernel<NW4><<<blocks_for(nq, wpb), wpb * 32, smem, st>>>(
+    bound_kernel<NW4><<<(unsigned)nq, 128, (size_t)kpw * 4, st>>>(
         ws.probe_ids, ws.nprobe, np, ws.nsel, ws.qparams, ws.planes, ix->offsets, ix->codes,
-        ix->fac, dp, kpw, nq, ws.bound, ws.rerank_on + nq);
+        ix->fac, dp, ws.bound, ws.rerank_on + nq);
   }
   RQ_CUDA(cudaMemsetAsync(ws.counts, 0, sizeof(int32_t) * nq, st));
   tm.mark(RQ_STAGE_WORKLIST, st);
@@ -807,28 +844,26 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
   // 5-6. candidate selection and exact re-rank
   tm.mark(RQ_STAGE_SELECT, st);
   {
-    const FinalizeLayout lay{next_pow2_host(sh.nsel_max), next_pow2_host(sh.k_stride), 1024,
+    const FinalizeLayout lay{next_pow2_host(sh.nsel_max), next_pow2_host(sh.k_stride), 2048,
                              ix->dim};
-    const int per_warp = lay.bytes();
-    const int wpb = std::max(1, std::min(8, (64 * 1024) / per_warp));
-    const size_t smem = (size_t)wpb * per_warp;
+    const size_t smem = lay.bytes();
     static bool attr = false;
     if (!attr) {
-      RQ_CUDA(cudaFuncSetAttribute(finalize_warp_kernel<uint8_t>,
+      RQ_CUDA(cudaFuncSetAttribute(finalize_kernel<uint8_t>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      RQ_CUDA(cudaFuncSetAttribute(finalize_warp_kernel<float>,
+      RQ_CUDA(cudaFuncSetAttribute(finalize_kernel<float>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
       attr = true;
     }
     if (ix->raw_dtype == RQ_U8)
-      finalize_warp_kernel<uint8_t><<<blocks_for(nq, wpb), wpb * 32, smem, st>>>(
+      finalize_kernel<uint8_t><<<(unsigned)nq, 128, smem, st>>>(
           ws.cand, ws.cap, ws.counts, ws.nsel, ws.kq, ws.rerank_on, sh.nsel_max, ws.sel,
-          static_cast<const uint8_t*>(ix->raw), ws.q, ix->dim, sh.k_stride, nq, lay, ws.out_ids,
+          static_cast<const uint8_t*>(ix->raw), ws.q, ix->dim, sh.k_stride, lay, ws.out_ids,
           ws.out_d, ix->d_err);
     else
-      finalize_warp_kernel<float><<<blocks_for(nq, wpb), wpb * 32, smem, st>>>(
+      finalize_kernel<float><<<(unsigned)nq, 128, smem, st>>>(
           ws.cand, ws.cap, ws.counts, ws.nsel, ws.kq, ws.rerank_on, sh.nsel_max, ws.sel,
-          static_cast<const float*>(ix->raw), ws.q, ix->dim, sh.k_stride, nq, lay, ws.out_ids,
+          static_cast<const float*>(ix->raw), ws.q, ix->dim, sh.k_stride, lay, ws.out_ids,
           ws.out_d, ix->d_err);
   }
   tm.mark(RQ_STAGE_RERANK, st);

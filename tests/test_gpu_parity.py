@@ -253,3 +253,19 @@ def test_invalid_arguments_rejected(tiny):
     with pytest.raises(rq.RQError):
         ix.search(bad, 8, 10, 100)
     assert ix.device_error() == 0
+
+
+def test_integer_valued_base_kept_as_bytes_is_lossless(rq):
+    mix = W.mixture("sift1m")
+    x = mix.base(20000)
+    q = mix.queries(30)
+    a = rq.rq_build(x, 64, seed=4, kmeans_iters=3)
+    b = rq.rq_build(x, 64, seed=4, kmeans_iters=3, keep_float_raw=True)
+    assert a.stats()["raw_bytes"] == x.size and b.stats()["raw_bytes"] == 4 * x.size
+    for mode in (1, 2, 3):
+        ra = a.search(q, 12, 10, 200, scan_mode=mode)
+        rb = b.search(q, 12, 10, 200, scan_mode=mode)
+        assert np.array_equal(ra[0], rb[0]) and np.array_equal(ra[1], rb[1])
+    # a base that is not integer-valued keeps its float copy
+    t = rq.rq_build(W.mixture("tiny").base(3000), 16, seed=0, kmeans_iters=2)
+    assert t.stats()["raw_bytes"] == 3000 * 128 * 4
