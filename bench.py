@@ -58,6 +58,15 @@ SMS = 152
 TRAFFIC = {}
 
 
+def measured_bf16_tflops() -> float:
+    """Dense bf16 peak measured on this machine (burst), else the stated fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for f in ("rq_search.cu", "rq_scan.cuh", "rq_scan_mma.cu"):
@@ -80,6 +89,8 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="only build and run --warmup + --steps batches per scan mode "
                          "(for ncu captures); prints the stage times")
+    ap.add_argument("--modes", default="plain,grouped,mma",
+                    help="scan modes of --profile (comma separated)")
     return ap.parse_args()
 
 
@@ -335,28 +346,35 @@ def run_ours(args, rank, world, local, pg):
     pairs = scanned_pairs(h_off, pid.cpu().numpy())
     dp = st["dim_pad"]
     code_b = dp // 8
-    popc_per_pair = 4 * dp // 32
     scan_s = stages["scan"] / 1e3
-    achieved_popc = pairs * popc_per_pair / scan_s / 1e12
-    peak_popc = POPC_PER_SM_CLK * SMS * 2070e6 / 1e12
+    tuned = ix.stats()["auto_scan_mode"]
     logical_gbs = pairs * (code_b + 8) / scan_s / 1e9
     unique_bytes = int(np.diff(h_off)[np.unique(pid.cpu().numpy())].sum()) * (code_b + 8)
     key = f"scan:{WORKLOAD}:{kernel_source_hash()}"
-    roofline = {
-        "kernel": "scan (tuned mode)",
-        "bound": "alu",
-        "achieved": round(achieved_popc, 4),
-        "peak": round(peak_popc, 4),
-        "unit": "Tpopc/s",
-        "frac": round(achieved_popc / peak_popc, 4),
+    if tuned == rq.RQ_SCAN_MMA:
+        # tcgen05 kind::f8f6f4: 2 * D_p flops per (query, vector) pair; peak =
+        # measured bf16 dense x the nominal FP8/BF16 ratio (4.5 / 2.25 PFLOP/s).
+        achieved = pairs * 2 * dp / scan_s / 1e12
+        peak = measured_bf16_tflops() * 2.0
+        roofline = {"kernel": "scan_mma_kernel (tcgen05 FP8)", "bound": "tensor",
+                    "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
+                    "frac": round(achieved / peak, 5),
+                    "peak_source": "measured bf16 dense TFLOP/s x 2 (nominal FP8 ratio)"}
+    else:
+        popc_per_pair = 4 * dp // 32
+        achieved = pairs * popc_per_pair / scan_s / 1e12
+        peak = POPC_PER_SM_CLK * SMS * 2070e6 / 1e12
+        roofline = {"kernel": "scan (popcount)", "bound": "alu", "achieved": round(achieved, 4),
+                    "peak": round(peak, 4), "unit": "Tpopc/s", "frac": round(achieved / peak, 4),
+                    "peak_source": "derived: 16 POPC/clk/SM x 152 SMs x 2070 MHz"}
+    roofline.update({
         "traffic": TRAFFIC.get(key),
-        "peak_source": "derived: 16 POPC/clk/SM x 152 SMs x 2070 MHz",
         "scan_ms": round(stages["scan"], 4),
         "pairs_per_launch": pairs,
         "logical_gbs": round(logical_gbs, 1),
         "unique_index_gbs": round(unique_bytes / scan_s / 1e9, 1),
         "plain_scan_ms": round(stages_plain["scan"], 4),
-    }
+    })
     # -- e2e through the C ABI with host buffers
     import torch as _t
 
@@ -453,7 +471,7 @@ def run_serving(rq, ix, q, nprobe, k, nrr, offered, seconds=2.0, seed=3):
         if now < t_next:
             time.sleep(min(t_next - now, 0.0005))
             continue
-        n = int(sizes[i])
+        n = int(sizes[i % sizes.size])
         if lo + n > q.shape[0]:
             lo = 0
         tickets.append((srv.submit(q[lo:lo + n], nprobe, k, nrr), n))
@@ -563,8 +581,9 @@ def run_profile(args):
     ids = torch.empty((q_dev.shape[0], k), dtype=torch.int64, device=dev)
     dist = torch.empty((q_dev.shape[0], k), dtype=torch.float32, device=dev)
     out = {}
-    for mode, name in ((rq.RQ_SCAN_PLAIN, "plain"), (rq.RQ_SCAN_GROUPED, "grouped"),
-                       (rq.RQ_SCAN_MMA, "mma")):
+    modes = {"plain": rq.RQ_SCAN_PLAIN, "grouped": rq.RQ_SCAN_GROUPED, "mma": rq.RQ_SCAN_MMA}
+    for name in args.modes.split(","):
+        mode = modes[name]
         for _ in range(args.warmup + args.steps):
             st = {}
             ix.search(q_dev, nprobe, k, nrr, out_ids=ids, out_dist=dist, scan_mode=mode,

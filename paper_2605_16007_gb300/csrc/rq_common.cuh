@@ -195,13 +195,10 @@ namespace rq {
 // of 32 so that warps stay converged.
 // ---------------------------------------------------------------------------
 
-// Adds 1 to hist[d] for every active lane, one atomic per distinct digit of
-// the warp. All 32 lanes must call it.
+// Adds 1 to hist[d] for every active lane (shared-memory atomics; lanes
+// that hit the same bin are serialised by the hardware).
 __device__ __forceinline__ void hist_add(int* hist, int d, bool active) {
-  const unsigned act = __ballot_sync(0xffffffffu, active);
-  if (!active) return;
-  const unsigned peers = __match_any_sync(act, d);
-  if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[d], __popc(peers));
+  if (active) atomicAdd(&hist[d], 1);
 }
 
 // Sorts 32 uint64 keys held one per lane (ascending by lane) with a bitonic

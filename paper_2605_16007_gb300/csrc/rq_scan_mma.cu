@@ -13,11 +13,12 @@
 // the B tile (the group's query digits, pre-swizzled in their per-list
 // bucket) and the group's parameters into one of two shared-memory stages,
 // completing on that stage's mbarrier, while the block works on the other
-// stage. Per 128-vector tile the codes are expanded to FP8 rows of the A tile
-// (128B swizzle), one thread issues four tcgen05.mma (K = 32 bytes each) into
-// tensor memory, and the eight warps read the accumulators back with
-// tcgen05.ld (warp w: TMEM lanes 32 (w % 4) .., column half w / 4) for the
-// float32 estimator epilogue.
+// stage. Thread t expands the codes of vector t of the item to an FP8 row of
+// the A tile of its 128-vector half (128B swizzle); one thread issues four
+// tcgen05.mma (K = 32 bytes each) per tile into that tile's TMEM accumulator
+// (columns [64 tile, 64 tile + 64)); thread t then reads its own row back
+// with tcgen05.ld (warp w: TMEM lanes 32 (w % 4) .. of tile w / 4) for the
+// float32 estimator epilogue, so all eight warps share the epilogue.
 #include <cuda_runtime.h>
 
 #include "rq_common.cuh"
@@ -32,10 +33,11 @@ constexpr int kMmaK = 128;        // D_p
 constexpr int kItemV = kGroupVectors;  // 256 vectors per work item = 2 tiles
 constexpr int kMmaThreads = 256;  // eight warps
 constexpr uint64_t kWaitNs = 2000000000ull;  // an mbarrier wait gives up after 2 s
+constexpr int kTmemCols = 2 * kMmaNmax;    // one accumulator per tile of the item
 
 // Shared memory of one block (offsets from a 1024-byte aligned base).
-constexpr int kSmA = 0;                                  // 128 x 128 B (128B swizzle)
-constexpr int kSmB = kSmA + kMmaM * kMmaK;               // 2 stages x 64 x 128 B
+constexpr int kSmA = 0;                                  // 2 tiles x 128 x 128 B (128B swizzle)
+constexpr int kSmB = kSmA + 2 * kMmaM * kMmaK;           // 2 stages x 64 x 128 B
 constexpr int kSmCode = kSmB + 2 * kMmaNmax * kMmaK;     // 2 stages x 256 x 16 B
 constexpr int kFacBytes = (kItemV + 2) * 8;              // +1 for alignment, rounded
 constexpr int kSmFac = kSmCode + 2 * kItemV * 16;        // 2 stages x 258 x 8 B
@@ -241,7 +243,7 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
     fence_barrier_init();
   }
   if (warp == 0) {
-    tmem_alloc(sbase + kSmTmem, kMmaNmax);
+    tmem_alloc(sbase + kSmTmem, kTmemCols);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -312,47 +314,51 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
           s_tau[g] = bound[q];
           s_qid[g] = q;
         }
-        for (int t0 = 0; t0 < m.nvec && !abort; t0 += kMmaM) {
-          // A tile: rows = the tile's vectors, codes expanded to FP8.
-          {
-            const int r = tid & (kMmaM - 1), half = tid >> 7;
-            const int v = t0 + r;
-            uint2 cw = make_uint2(0, 0);
-            if (v < m.nvec) cw = *reinterpret_cast<const uint2*>(code_s + v * 16 + half * 8);
-            const uint32_t wd[2] = {cw.x, cw.y};
+        // A tiles: thread t expands vector t of the item (tile t / 128, row
+        // t % 128); they are unchanged across the groups of the item.
+        if (g0 == 0) {
+          const int tile = tid >> 7, r = tid & (kMmaM - 1);
+          uint4 cw = make_uint4(0, 0, 0, 0);
+          if (tid < m.nvec) cw = *reinterpret_cast<const uint4*>(code_s + tid * 16);
+          const uint32_t wd[4] = {cw.x, cw.y, cw.z, cw.w};
 #pragma unroll
-            for (int cc = 0; cc < 4; ++cc) {
-              const uint32_t w16 = wd[cc >> 1] >> ((cc & 1) * 16);
-              const uint4 val = make_uint4(nibble_to_e4m3(w16 & 15u), nibble_to_e4m3((w16 >> 4) & 15u),
-                                           nibble_to_e4m3((w16 >> 8) & 15u),
-                                           nibble_to_e4m3((w16 >> 12) & 15u));
-              *reinterpret_cast<uint4*>(sm + kSmA + sw128_offset(r, half * 4 + cc)) = val;
-            }
+          for (int c = 0; c < 8; ++c) {
+            const uint32_t w16 = wd[c >> 1] >> ((c & 1) * 16);
+            const uint4 val = make_uint4(nibble_to_e4m3(w16 & 15u), nibble_to_e4m3((w16 >> 4) & 15u),
+                                         nibble_to_e4m3((w16 >> 8) & 15u),
+                                         nibble_to_e4m3((w16 >> 12) & 15u));
+            *reinterpret_cast<uint4*>(sm + kSmA + tile * kMmaM * kMmaK + sw128_offset(r, c)) = val;
           }
-          fence_async_smem();
-          tc_fence_before();
-          __syncthreads();
-          tc_fence_after();
-          if (tid == 0) {
-            const uint32_t id = idesc_e4m3_f32(kMmaM, (uint32_t)n);
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        const int ntiles = (m.nvec + kMmaM - 1) / kMmaM;
+        if (tid == 0) {
+          const uint32_t id = idesc_e4m3_f32(kMmaM, (uint32_t)n);
+          for (int tile = 0; tile < ntiles; ++tile) {
+            const uint64_t ad = sdesc_sw128(sbase + kSmA + tile * kMmaM * kMmaK);
 #pragma unroll
             for (int k = 0; k < kMmaK / 32; ++k)
-              mma_e4m3(taddr, adesc + (uint64_t)(2 * k), bdesc + (uint64_t)(2 * k), id, k > 0);
-            mma_commit(bar_mma);
+              mma_e4m3(taddr + (uint32_t)(tile * kMmaNmax), ad + (uint64_t)(2 * k),
+                       bdesc + (uint64_t)(2 * k), id, k > 0);
           }
-          const bool ok3 = mbar_wait_bounded(bar_mma, ph_mma);
-          ph_mma ^= 1u;
-          if (__syncthreads_or(!ok3)) {
-            abort = true;
-            break;
-          }
-          tc_fence_after();
-          // Epilogue: warp w reads TMEM lanes 32 (w % 4).. and columns
-          // [32 (w / 4), 32 (w / 4) + 32).
-          const int quarter = warp & 3, colh = warp >> 2;
-          const int c0 = colh * 32;
-          if (c0 < np) {
-            const int v = t0 + quarter * 32 + lane;
+          mma_commit(bar_mma);
+        }
+        const bool ok3 = mbar_wait_bounded(bar_mma, ph_mma);
+        ph_mma ^= 1u;
+        if (__syncthreads_or(!ok3)) {
+          abort = true;
+          break;
+        }
+        tc_fence_after();
+        // Epilogue: thread t = vector t = TMEM lane 32 (w % 4) + lane of
+        // tile w / 4; 16 pairs per TMEM load.
+        {
+          const int quarter = warp & 3, tile = warp >> 2;
+          if (tile < ntiles) {
+            const int v = tid;
             const bool valid = v < m.nvec;
             const int64_t s = (int64_t)m.lo + v;
             float2 f = make_float2(0.0f, 0.0f);
@@ -363,9 +369,10 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
               pc = __popc(cw.x) + __popc(cw.y) + __popc(cw.z) + __popc(cw.w);
             }
             const float bterm = (float)(2 * pc - kMmaK);
-            for (int c1 = c0; c1 < min(np, c0 + 32); c1 += 16) {
+            for (int c1 = 0; c1 < np; c1 += 16) {
               uint32_t r[16];
-              tmem_ld16(taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c1, r);
+              tmem_ld16(taddr + ((uint32_t)(quarter * 32) << 16) +
+                            (uint32_t)(tile * kMmaNmax + c1), r);
               float d[16];
               uint32_t passbits = 0;
 #pragma unroll
@@ -386,9 +393,9 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
               append_chunk<16>(passbits, d, s_qid + c1, s, ids, counts, cand, cap, lane, err);
             }
           }
-          tc_fence_before();
-          __syncthreads();
         }
+        tc_fence_before();
+        __syncthreads();
       }
     }
     __syncthreads();
@@ -407,7 +414,7 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(taddr, kMmaNmax);
+  if (warp == 0) tmem_dealloc(taddr, kTmemCols);
 }
 
 }  // namespace
@@ -423,8 +430,8 @@ rq_status launch_scan_mma(rq_index* ix, const SearchShape& sh, Workspace& ws, cu
                                  kSmAlloc));
     attr_set = true;
   }
-  // Three blocks per SM (registers; ~53 KB of shared memory each); their
-  // TMEM (64 columns each) stays within the SM's 512 columns.
+  // Three blocks per SM (registers; ~69 KB of shared memory each); their
+  // TMEM (128 columns each) stays within the SM's 512 columns.
   scan_mma_kernel<<<(unsigned)(sms * 3), kMmaThreads, kSmAlloc, st>>>(
       ix->items, ix->n_items, ws.work_count, ws.list_count, ws.list_pairs, sh.nq, ws.qpb, ws.qdig,
       sh.npmax, ix->offsets, ix->codes, ix->fac, ix->ids, ws.bound, ws.counts, ws.cand, ws.cap,
