@@ -330,11 +330,11 @@ int pow2_at_least(int v) {
 // Device bytes a batch shape needs (the search workspace) -- the admission
 // cost of a batch.
 size_t batch_bytes(const rq_index* ix, int64_t nq, int npmax, int nsel, int kst) {
-  const int64_t cap = ix->top_len_prefix[std::min<int64_t>(npmax, ix->nlist)];
+  const int64_t mwords = ix->top_words_prefix[std::min<int64_t>(npmax, ix->nlist)];
   size_t b = 0;
   b += (size_t)nq * (ix->dim + ix->dp) * 4 + (size_t)nq * ix->nlist * 8;
-  b += (size_t)nq * npmax * (4 + 4 + 16 + 16 * (ix->dp / 32) + 4);
-  b += (size_t)nq * cap * 8 + (size_t)nq * nsel * 8 + (size_t)nq * kst * 12;
+  b += (size_t)nq * npmax * (4 + 4 + 16 + 16 * (ix->dp / 32) + 4 + 4);
+  b += (size_t)nq * mwords * (4 + 32 * 8) + (size_t)nq * nsel * 8 + (size_t)nq * kst * 12;
   return b + (1 << 20);
 }
 

@@ -691,7 +691,7 @@ rq_status build_index(const float* d_base, const void* d_raw, rq_dtype dt,
   RQ_TRY(r.alloc(n));
   RQ_TRY(alpha.alloc(n));
   RQ_TRY(fac.alloc(n + 2));  // 16 bytes of tail room for 16-byte bulk copies
-  RQ_TRY(ids.alloc(n));
+  RQ_TRY(ids.alloc(n + 4));  // tail room for 16-byte bulk copies
   RQ_TRY(assign.alloc(n));
   RQ_TRY(err.alloc(1));
   RQ_CUDA(cudaMemset(err.p, 0, sizeof(int32_t)));
@@ -762,7 +762,11 @@ rq_status finish_index_host_side(rq_index* ix) {
   }
   std::sort(len.begin(), len.end(), std::greater<int64_t>());
   ix->top_len_prefix.assign(ix->nlist + 1, 0);
-  for (int l = 0; l < ix->nlist; ++l) ix->top_len_prefix[l + 1] = ix->top_len_prefix[l] + len[l];
+  ix->top_words_prefix.assign(ix->nlist + 1, 0);
+  for (int l = 0; l < ix->nlist; ++l) {
+    ix->top_len_prefix[l + 1] = ix->top_len_prefix[l] + len[l];
+    ix->top_words_prefix[l + 1] = ix->top_words_prefix[l] + (len[l] + 31) / 32;
+  }
   if (ix->items) cudaFree(ix->items);
   ix->items = nullptr;
   ix->n_items = (int)items.size();

@@ -66,8 +66,15 @@ struct Workspace {
   float4* qparams = nullptr;    // nq x npmax: vl, delta, nq2, Sq(bits of int)
   uint32_t* planes = nullptr;   // nq x npmax x 4 x W words
   uint32_t* bound = nullptr;    // nq
-  int32_t* counts = nullptr;    // nq
-  uint64_t* cand = nullptr;     // nq x cap
+  int32_t* counts = nullptr;    // nq: candidates that passed (written by the finalize)
+  // Scan output: for probe p of query q, word w of the probed list's
+  // survivor mask sits at mask[q * mwords + wbase[q * npmax + p] + w] (bit i:
+  // vector 32 w + i passed the bound), and that vector's key at
+  // cand[32 * (that index) + i].
+  uint32_t* mask = nullptr;     // nq x mwords
+  int32_t* wbase = nullptr;     // nq x npmax: first mask word of each probe
+  int32_t* wtotal = nullptr;    // nq: mask words of the query's probes
+  uint64_t* cand = nullptr;     // nq x cap, cap = 32 mwords
   uint64_t* sel = nullptr;      // nq x nsel_max
   int32_t* nprobe = nullptr;    // nq
   int32_t* kq = nullptr;        // nq
@@ -81,7 +88,8 @@ struct Workspace {
   int32_t* work_count = nullptr;  // work-item counter of the persistent scan
   uint8_t* qdig = nullptr;        // nlist x nq x D_p: per-list buckets of FP8 query digits
   float4* qpb = nullptr;          // nlist x nq: per-list buckets of quantisation parameters
-  int64_t cap = 0;                // candidate slots per query
+  int64_t mwords = 0;             // mask words per query
+  int64_t cap = 0;                // key slots per query (32 mwords)
 };
 
 struct Plan {
@@ -119,7 +127,8 @@ struct rq_index {
   int n_items = 0;
   // host copies
   std::vector<int64_t> h_offsets;
-  std::vector<int64_t> top_len_prefix;  // sum of the j largest list lengths
+  std::vector<int64_t> top_len_prefix;    // sum of the j largest list lengths
+  std::vector<int64_t> top_words_prefix;  // sum of the j largest ceil(length / 32)
   // tuned choice for RQ_SCAN_AUTO
   std::atomic<int> auto_mode{RQ_SCAN_GROUPED};
   // plans (workspaces, graphs) per (stream, shape)

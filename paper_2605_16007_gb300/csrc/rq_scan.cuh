@@ -63,64 +63,42 @@ __device__ __forceinline__ float estimate_code(const uint4* __restrict__ cp, flo
   return estimate_regs<NW4>(code, pc, fac, pl, qp, dp);
 }
 
-// Append the lanes' passing candidates (distance, id of slot s) to one
-// query's buffer with one atomic per warp. All 32 lanes must call it.
-__device__ __forceinline__ void append_candidates(bool pass, float d, int64_t s,
-                                                  const uint32_t* __restrict__ ids,
-                                                  int32_t* count, uint64_t* cand, int64_t cap,
-                                                  int lane, int32_t* err) {
-  const unsigned mask = __ballot_sync(0xffffffffu, pass);
-  if (mask == 0) return;
-  const int leader = __ffs(mask) - 1;
-  int base = 0;
-  if (lane == leader) base = atomicAdd(count, __popc(mask));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (pass) {
-    const int64_t pos = (int64_t)base + __popc(mask & ((1u << lane) - 1u));
-    if (pos < cap)
-      cand[pos] = make_key(d, ids[s]);
-    else
-      flag_error(err, kErrCandidateOverflow);
-  }
+// Scan output without atomics. The vectors of a probed list are cut into
+// 32-vector words; word w of probe p of query q has the fixed mask index
+// x = q * mwords + wbase[q, p] + w (bit i set: vector 32 w + i of the list
+// passed the query's bound) and 32 key slots from 32 x, where the keys of the
+// passing vectors are packed in lane order. A warp holds one word (lane i =
+// vector 32 w + i); every word of every probed list is written on every
+// search, so neither buffer is cleared.
+__device__ __forceinline__ void emit_word(bool pass, float d, uint32_t id, int64_t widx,
+                                          uint32_t* __restrict__ mask,
+                                          uint64_t* __restrict__ cand, int lane) {
+  const uint32_t m = __ballot_sync(0xffffffffu, pass);
+  if (lane == 0) mask[widx] = m;
+  if (pass) cand[widx * 32 + __popc(m & ((1u << lane) - 1u))] = make_key(d, id);
 }
 
-// Append for a chunk of J pairs at once: bit j of `passbits` says whether
-// this lane's vector (slot s) passes for pair j, whose query is qid[j] and
-// estimate d[j]. Lane 0 issues the chunk's counter atomics back to back (they
-// are independent), then every lane writes its survivors. All 32 lanes must
-// call it.
+// The same for a chunk of J pairs over one word: bit j of `passbits` says
+// whether this lane's vector passes for pair j, whose first mask index is
+// wrow[j] (the word's index is wrow[j] + word); lane j writes pair j's mask
+// word. Pairs j >= nvalid and words past the list's end (word_valid false,
+// where no lane passes) write no mask. All 32 lanes must call it.
 template <int J>
-__device__ __forceinline__ void append_chunk(uint32_t passbits, const float (&d)[J],
-                                             const int32_t* qid, int64_t s,
-                                             const uint32_t* __restrict__ ids,
-                                             int32_t* counts, uint64_t* cand, int64_t cap,
-                                             int lane, int32_t* err) {
-  uint32_t mk[J];
-  int any = 0;
-#pragma unroll
-  for (int j = 0; j < J; ++j) {
-    mk[j] = __ballot_sync(0xffffffffu, (passbits >> j) & 1u);
-    any |= mk[j] != 0;
-  }
-  if (!any) return;
-  int base[J];
-  if (lane == 0) {
-#pragma unroll
-    for (int j = 0; j < J; ++j) base[j] = mk[j] ? atomicAdd(counts + qid[j], __popc(mk[j])) : 0;
-  }
-  const uint32_t id = passbits ? ids[s] : 0u;
+__device__ __forceinline__ void emit_chunk(uint32_t passbits, const float (&d)[J],
+                                           const int64_t* wrow, int nvalid, int64_t word,
+                                           bool word_valid, uint32_t id,
+                                           uint32_t* __restrict__ mask,
+                                           uint64_t* __restrict__ cand, int lane) {
   const uint32_t lt = (1u << lane) - 1u;
+  uint32_t mine = 0;
 #pragma unroll
   for (int j = 0; j < J; ++j) {
-    const int b = __shfl_sync(0xffffffffu, base[j], 0);
-    if ((passbits >> j) & 1u) {
-      const int64_t pos = (int64_t)b + __popc(mk[j] & lt);
-      if (pos < cap)
-        cand[(int64_t)qid[j] * cap + pos] = make_key(d[j], id);
-      else
-        flag_error(err, kErrCandidateOverflow);
-    }
+    const uint32_t m = __ballot_sync(0xffffffffu, (passbits >> j) & 1u);
+    if (lane == j) mine = m;
+    if ((passbits >> j) & 1u)
+      cand[(wrow[j] + word) * 32 + __popc(m & lt)] = make_key(d[j], id);
   }
+  if (word_valid && lane < J && lane < nvalid) mask[wrow[lane] + word] = mine;
 }
 
 // FP8 E4M3 encoding of an integer 0..15 (exact): v = 2^e (1 + m/8) with

@@ -31,7 +31,8 @@ constexpr int kMmaM = 128;        // vectors per tile (TMEM lanes)
 constexpr int kMmaNmax = 64;      // pairs per MMA group (TMEM columns)
 constexpr int kMmaK = 128;        // D_p
 constexpr int kItemV = kGroupVectors;  // 256 vectors per work item = 2 tiles
-constexpr int kMmaThreads = 256;  // eight warps
+constexpr int kConsumers = 256;   // eight warps: expansion, MMA issue, epilogue
+constexpr int kMmaThreads = kConsumers + 32;  // plus one producer warp
 constexpr uint64_t kWaitNs = 2000000000ull;  // an mbarrier wait gives up after 2 s
 constexpr int kTmemCols = 2 * kMmaNmax;    // one accumulator per tile of the item
 
@@ -42,13 +43,14 @@ constexpr int kSmCode = kSmB + 2 * kMmaNmax * kMmaK;     // 2 stages x 256 x 16 
 constexpr int kFacBytes = (kItemV + 2) * 8;              // +1 for alignment, rounded
 constexpr int kSmFac = kSmCode + 2 * kItemV * 16;        // 2 stages x 258 x 8 B
 constexpr int kSmQp = kSmFac + 2 * kFacBytes;            // 2 stages x 64 x 16 B
-constexpr int kSmTau = kSmQp + 2 * kMmaNmax * 16;        // 64 x uint32
-constexpr int kSmQid = kSmTau + kMmaNmax * 4;            // 64 x int32
-constexpr int kSmBar = kSmQid + kMmaNmax * 4;            // 3 mbarriers: load[2], mma
-constexpr int kSmMeta = kSmBar + 3 * 8;                  // 2 stages x int4 meta
-constexpr int kSmTmem = kSmMeta + 2 * 16;                // TMEM base address
-constexpr int kSmNext = kSmTmem + 4;                     // next item index
-constexpr int kSmBytes = kSmNext + 4;
+constexpr int kSmTau = kSmQp + 2 * kMmaNmax * 16;        // 2 stages x 64 x uint32
+constexpr int kSmWrow = kSmTau + 2 * kMmaNmax * 4;       // 2 stages x 64 x int64 mask rows
+constexpr int kIdBytes = (kItemV + 4) * 4;               // +3 for alignment, rounded
+constexpr int kSmIds = kSmWrow + 2 * kMmaNmax * 8;       // 2 stages x 260 x uint32 row ids
+constexpr int kSmBar = kSmIds + 2 * kIdBytes;            // mbarriers: full[2], empty[2], mma, aux
+constexpr int kSmMeta = kSmBar + 6 * 8;                  // 2 stages x 32-byte meta
+constexpr int kSmTmem = kSmMeta + 2 * 32;                // TMEM base address
+constexpr int kSmBytes = kSmTmem + 4;
 constexpr int kSmAlloc = kSmBytes + 1024;                // room to align the base
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -173,46 +175,88 @@ __device__ __forceinline__ uint32_t nibble_to_e4m3(uint32_t n) {
   return ((n * 0x00204081u) & 0x01010101u) * 0x38u;
 }
 
-// Work item meta of one stage: {list, first slot, vectors, pairs}.
+// Work item meta of one stage: list (-1: no more items), first slot, vectors,
+// pairs, first vector within the list.
 struct Meta {
-  int l, lo, nvec, cnt;
+  int l, lo, nvec, cnt, v0, pad0, pad1, pad2;
 };
 
-// Thread 0: read item `it`, record its meta, and start the TMA copies of
-// its codes, factors, first B tile and parameters into `stage`.
-__device__ __forceinline__ void issue_item(int it, int stage, uint8_t* sm, uint32_t sbase,
-                                           const int2* items, const int32_t* list_count,
-                                           const int64_t* offsets, const uint8_t* codes,
-                                           const float2* fac, const uint8_t* qdb,
-                                           const float4* qpb, int64_t pair_stride) {
-  const int2 w = items[it];
-  const int l = w.x;
-  const int cnt = list_count[l];
-  const int64_t lo = offsets[l] + w.y;
-  const int nvec = (int)min((int64_t)kItemV, offsets[l + 1] - lo);
-  Meta* meta = reinterpret_cast<Meta*>(sm + kSmMeta) + stage;
-  meta->l = l;
-  meta->lo = (int)lo;
-  meta->nvec = nvec;
-  meta->cnt = cnt;
-  const uint32_t bar = sbase + kSmBar + 8 * stage;
-  if (cnt == 0) {
-    mbar_expect_tx_arrive(bar, 0);
-    return;
+__device__ __forceinline__ void named_bar_consumers() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory");
+}
+
+// Producer (one lane): fetch items from the global counter and fill the two
+// stages -- meta, the mask rows and bounds of the first group, then the TMA
+// copies of codes, factors, B tile and parameters, all completing on the
+// stage's `full` barrier. A stage is reused once its `empty` barrier shows
+// the consumers are done with it.
+__device__ void producer_loop(uint8_t* sm, uint32_t sbase, const int2* __restrict__ items,
+                              int n_items, int32_t* __restrict__ work_counter,
+                              const int32_t* __restrict__ list_count,
+                              const int32_t* __restrict__ list_pairs, int64_t pair_stride,
+                              int npmax, const int64_t* __restrict__ offsets,
+                              const uint8_t* __restrict__ codes, const float2* __restrict__ fac,
+                              const uint32_t* __restrict__ ids,
+                              const uint8_t* __restrict__ qdb, const float4* __restrict__ qpb,
+                              const uint32_t* __restrict__ bound,
+                              const int32_t* __restrict__ wbase, int64_t mwords, int32_t* err) {
+  Meta* meta = reinterpret_cast<Meta*>(sm + kSmMeta);
+  for (int i = 0;; ++i) {
+    const int st = i & 1;
+    const uint32_t full = sbase + kSmBar + 8 * st;
+    const uint32_t empty = sbase + kSmBar + 16 + 8 * st;
+    if (i >= 2 && !mbar_wait_bounded(empty, (uint32_t)(((i >> 1) - 1) & 1))) {
+      flag_error(err, kErrMmaTimeout);
+      meta[st].l = -1;
+      mbar_expect_tx_arrive(full, 0);
+      return;
+    }
+    const int it = atomicAdd(work_counter, 1);
+    if (it >= n_items) {
+      meta[st].l = -1;
+      mbar_expect_tx_arrive(full, 0);
+      return;
+    }
+    const int2 w = items[it];
+    const int l = w.x;
+    const int cnt = list_count[l];
+    const int64_t lo = offsets[l] + w.y;
+    const int nvec = (int)min((int64_t)kItemV, offsets[l + 1] - lo);
+    meta[st].l = l;
+    meta[st].lo = (int)lo;
+    meta[st].nvec = nvec;
+    meta[st].cnt = cnt;
+    meta[st].v0 = w.y;
+    if (cnt == 0) {
+      mbar_expect_tx_arrive(full, 0);
+      continue;
+    }
+    const int np = min(kMmaNmax, cnt);
+    const int32_t* lp = list_pairs + (int64_t)l * pair_stride;
+    uint32_t* tau = reinterpret_cast<uint32_t*>(sm + kSmTau) + st * kMmaNmax;
+    int64_t* wrow = reinterpret_cast<int64_t*>(sm + kSmWrow) + st * kMmaNmax;
+    for (int g = 0; g < np; ++g) {
+      const int pair = lp[g];
+      const int q = pair / npmax;
+      wrow[g] = (int64_t)q * mwords + wbase[pair];
+      tau[g] = bound[q];
+    }
+    const int64_t lo_al = lo & ~(int64_t)1;
+    const uint32_t fac_bytes = (uint32_t)((((lo - lo_al) + nvec) * 8 + 15) & ~15);
+    const int64_t lo_al4 = lo & ~(int64_t)3;
+    const uint32_t id_bytes = (uint32_t)((((lo - lo_al4) + nvec) * 4 + 15) & ~15);
+    const uint32_t code_bytes = (uint32_t)nvec * 16;
+    const uint32_t b_bytes = (uint32_t)np * kMmaK;
+    const uint32_t qp_bytes = (uint32_t)np * 16;
+    mbar_expect_tx_arrive(full, code_bytes + fac_bytes + id_bytes + b_bytes + qp_bytes);
+    tma_load_1d(sbase + kSmCode + st * kItemV * 16, codes + lo * 16, code_bytes, full);
+    tma_load_1d(sbase + kSmFac + st * kFacBytes, fac + lo_al, fac_bytes, full);
+    tma_load_1d(sbase + kSmIds + st * kIdBytes, ids + lo_al4, id_bytes, full);
+    tma_load_1d(sbase + kSmB + st * kMmaNmax * kMmaK, qdb + (int64_t)l * pair_stride * kMmaK,
+                b_bytes, full);
+    tma_load_1d(sbase + kSmQp + st * kMmaNmax * 16, qpb + (int64_t)l * pair_stride, qp_bytes,
+                full);
   }
-  const int np = min(kMmaNmax, cnt);
-  const int64_t lo_al = lo & ~(int64_t)1;
-  const uint32_t fac_bytes = (uint32_t)((((lo - lo_al) + nvec) * 8 + 15) & ~15);
-  const uint32_t code_bytes = (uint32_t)nvec * 16;
-  const uint32_t b_bytes = (uint32_t)np * kMmaK;
-  const uint32_t qp_bytes = (uint32_t)np * 16;
-  mbar_expect_tx_arrive(bar, code_bytes + fac_bytes + b_bytes + qp_bytes);
-  tma_load_1d(sbase + kSmCode + stage * kItemV * 16, codes + lo * 16, code_bytes, bar);
-  tma_load_1d(sbase + kSmFac + stage * kFacBytes, fac + lo_al, fac_bytes, bar);
-  tma_load_1d(sbase + kSmB + stage * kMmaNmax * kMmaK, qdb + (int64_t)l * pair_stride * kMmaK,
-              b_bytes, bar);
-  tma_load_1d(sbase + kSmQp + stage * kMmaNmax * 16, qpb + (int64_t)l * pair_stride, qp_bytes,
-              bar);
 }
 
 __global__ void __launch_bounds__(kMmaThreads, 3)
@@ -222,24 +266,20 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
                 const uint8_t* __restrict__ qdb, int npmax, const int64_t* __restrict__ offsets,
                 const uint8_t* __restrict__ codes, const float2* __restrict__ fac,
                 const uint32_t* __restrict__ ids, const uint32_t* __restrict__ bound,
-                int32_t* __restrict__ counts, uint64_t* __restrict__ cand, int64_t cap,
-                int32_t* err) {
+                const int32_t* __restrict__ wbase, int64_t mwords, uint32_t* __restrict__ mask,
+                uint64_t* __restrict__ cand, int32_t* err) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_addr = smem_u32(smem_raw);
   uint8_t* sm = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
   const uint32_t sbase = smem_u32(sm);
-  uint32_t* s_tau = reinterpret_cast<uint32_t*>(sm + kSmTau);
-  int32_t* s_qid = reinterpret_cast<int32_t*>(sm + kSmQid);
   volatile uint32_t* s_tmem = reinterpret_cast<volatile uint32_t*>(sm + kSmTmem);
-  volatile int* s_next = reinterpret_cast<volatile int*>(sm + kSmNext);
   const Meta* meta = reinterpret_cast<const Meta*>(sm + kSmMeta);
-  const uint32_t bar_mma = sbase + kSmBar + 16;
+  const uint32_t bar_mma = sbase + kSmBar + 32;
+  const uint32_t bar_aux = sbase + kSmBar + 40;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
-    mbar_init(sbase + kSmBar, 1);
-    mbar_init(sbase + kSmBar + 8, 1);
-    mbar_init(bar_mma, 1);
+    for (int b = 0; b < 6; ++b) mbar_init(sbase + kSmBar + 8 * b, 1);
     fence_barrier_init();
   }
   if (warp == 0) {
@@ -250,69 +290,55 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
   __syncthreads();
   tc_fence_after();
   const uint32_t taddr = *s_tmem;
-  const uint64_t adesc = sdesc_sw128(sbase + kSmA);
-  uint32_t ph_load[2] = {0u, 0u};
-  uint32_t ph_mma = 0;
-  bool abort = false;
 
-  if (tid == 0) {
-    const int it = atomicAdd(work_counter, 1);
-    *s_next = it;
-    if (it < n_items)
-      issue_item(it, 0, sm, sbase, items, list_count, offsets, codes, fac, qdb, qpb, pair_stride);
-  }
-  __syncthreads();
-  int cur = *s_next;
-  int st = 0;
-  while (cur < n_items && !abort) {
-    __syncthreads();  // everyone has read s_next before it is overwritten
-    if (tid == 0) {
-      const int nx = atomicAdd(work_counter, 1);
-      *s_next = nx;
-      if (nx < n_items)
-        issue_item(nx, st ^ 1, sm, sbase, items, list_count, offsets, codes, fac, qdb, qpb,
-                   pair_stride);
-    }
-    const bool ok = mbar_wait_bounded(sbase + kSmBar + 8 * st, ph_load[st]);
-    ph_load[st] ^= 1u;
-    if (__syncthreads_or(!ok)) {
-      abort = true;
-      break;
-    }
-    const Meta m = meta[st];
-    if (m.cnt > 0) {
+  if (warp == kConsumers / 32) {
+    if (lane == 0)
+      producer_loop(sm, sbase, items, n_items, work_counter, list_count, list_pairs, pair_stride,
+                    npmax, offsets, codes, fac, ids, qdb, qpb, bound, wbase, mwords, err);
+  } else {
+    uint32_t ph_mma = 0, ph_aux = 0;
+    bool abort = false;
+    for (int i = 0;; ++i) {
+      const int st = i & 1;
+      const uint32_t full = sbase + kSmBar + 8 * st;
+      const uint32_t empty = sbase + kSmBar + 16 + 8 * st;
+      if (!mbar_wait_bounded(full, (uint32_t)((i >> 1) & 1))) abort = true;
+      const Meta m = meta[st];
+      if (abort || m.l < 0) break;
       const uint8_t* code_s = sm + kSmCode + st * kItemV * 16;
       const float2* fac_s = reinterpret_cast<const float2*>(sm + kSmFac + st * kFacBytes) +
                             (m.lo & 1);
       const float4* qp_s = reinterpret_cast<const float4*>(sm + kSmQp + st * kMmaNmax * 16);
+      uint32_t* s_tau = reinterpret_cast<uint32_t*>(sm + kSmTau) + st * kMmaNmax;
+      int64_t* s_wrow = reinterpret_cast<int64_t*>(sm + kSmWrow) + st * kMmaNmax;
+      const uint32_t* ids_s = reinterpret_cast<const uint32_t*>(sm + kSmIds + st * kIdBytes) +
+                              (m.lo & 3);
       const int32_t* lp = list_pairs + (int64_t)m.l * pair_stride;
       const uint64_t bdesc = sdesc_sw128(sbase + kSmB + st * kMmaNmax * kMmaK);
       for (int g0 = 0; g0 < m.cnt && !abort; g0 += kMmaNmax) {
         const int np = min(kMmaNmax, m.cnt - g0);
         const int n = max(16, (np + 15) & ~15);
         if (g0 > 0) {
-          // Later groups of a list probed by more than kMmaNmax queries:
-          // the B tile and parameters are reloaded in this stage.
+          // Later groups of a list probed by more than kMmaNmax queries: the
+          // consumers reload this stage's B tile, parameters and bounds.
+          named_bar_consumers();
           if (tid == 0) {
-            const uint32_t bar = sbase + kSmBar + 8 * st;
-            mbar_expect_tx_arrive(bar, (uint32_t)np * (kMmaK + 16));
+            mbar_expect_tx_arrive(bar_aux, (uint32_t)np * (kMmaK + 16));
             tma_load_1d(sbase + kSmB + st * kMmaNmax * kMmaK,
                         qdb + ((int64_t)m.l * pair_stride + g0) * kMmaK, (uint32_t)np * kMmaK,
-                        bar);
+                        bar_aux);
             tma_load_1d(sbase + kSmQp + st * kMmaNmax * 16, qpb + (int64_t)m.l * pair_stride + g0,
-                        (uint32_t)np * 16, bar);
+                        (uint32_t)np * 16, bar_aux);
           }
-          const bool ok2 = mbar_wait_bounded(sbase + kSmBar + 8 * st, ph_load[st]);
-          ph_load[st] ^= 1u;
-          if (__syncthreads_or(!ok2)) {
-            abort = true;
-            break;
+          for (int g = tid; g < np; g += kConsumers) {
+            const int pair = lp[g0 + g];
+            const int q = pair / npmax;
+            s_wrow[g] = (int64_t)q * mwords + wbase[pair];
+            s_tau[g] = bound[q];
           }
-        }
-        for (int g = tid; g < np; g += kMmaThreads) {
-          const int q = lp[g0 + g] / npmax;
-          s_tau[g] = bound[q];
-          s_qid[g] = q;
+          const bool ok2 = mbar_wait_bounded(bar_aux, ph_aux);
+          ph_aux ^= 1u;
+          if (!ok2) abort = true;
         }
         // A tiles: thread t expands vector t of the item (tile t / 128, row
         // t % 128); they are unchanged across the groups of the item.
@@ -332,10 +358,10 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
         }
         fence_async_smem();
         tc_fence_before();
-        __syncthreads();
+        named_bar_consumers();
         tc_fence_after();
         const int ntiles = (m.nvec + kMmaM - 1) / kMmaM;
-        if (tid == 0) {
+        if (tid == 0 && !abort) {
           const uint32_t id = idesc_e4m3_f32(kMmaM, (uint32_t)n);
           for (int tile = 0; tile < ntiles; ++tile) {
             const uint64_t ad = sdesc_sw128(sbase + kSmA + tile * kMmaM * kMmaK);
@@ -346,9 +372,10 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
           }
           mma_commit(bar_mma);
         }
+        if (abort) break;
         const bool ok3 = mbar_wait_bounded(bar_mma, ph_mma);
         ph_mma ^= 1u;
-        if (__syncthreads_or(!ok3)) {
+        if (!ok3) {
           abort = true;
           break;
         }
@@ -360,7 +387,6 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
           if (tile < ntiles) {
             const int v = tid;
             const bool valid = v < m.nvec;
-            const int64_t s = (int64_t)m.lo + v;
             float2 f = make_float2(0.0f, 0.0f);
             int pc = 0;
             if (valid) {
@@ -390,26 +416,26 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
                   if (valid && orderable(dd) <= s_tau[g]) passbits |= 1u << j;
                 }
               }
-              append_chunk<16>(passbits, d, s_qid + c1, s, ids, counts, cand, cap, lane, err);
+              const uint32_t id = passbits ? ids_s[v] : 0u;
+              emit_chunk<16>(passbits, d, s_wrow + c1, np - c1, m.v0 / 32 + warp,
+                             warp * 32 < m.nvec, id, mask, cand, lane);
             }
           }
         }
         tc_fence_before();
-        __syncthreads();
+        named_bar_consumers();
       }
+      if (abort) break;
+      // Every consumer has read this stage's meta and finished with its
+      // buffers before it is handed back to the producer.
+      named_bar_consumers();
+      if (tid == 0) mbar_expect_tx_arrive(empty, 0);
     }
-    __syncthreads();
-    cur = *s_next;
-    st ^= 1;
-  }
-  if (abort) {
-    if (tid == 0) flag_error(err, kErrMmaTimeout);
-    // Copies or an MMA may still be in flight: give them a bounded time.
-    mbar_wait_bounded(bar_mma, ph_mma);
-    mbar_wait_bounded(sbase + kSmBar, ph_load[0]);
-    mbar_wait_bounded(sbase + kSmBar + 8, ph_load[1]);
-  } else if (cur >= n_items) {
-    // The last issued prefetch (of an index past the end) loaded nothing.
+    if (abort && tid == 0) flag_error(err, kErrMmaTimeout);
+    if (abort) {
+      // An MMA may still be in flight: give it a bounded time to land.
+      mbar_wait_bounded(bar_mma, ph_mma);
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -434,8 +460,8 @@ rq_status launch_scan_mma(rq_index* ix, const SearchShape& sh, Workspace& ws, cu
   // TMEM (128 columns each) stays within the SM's 512 columns.
   scan_mma_kernel<<<(unsigned)(sms * 3), kMmaThreads, kSmAlloc, st>>>(
       ix->items, ix->n_items, ws.work_count, ws.list_count, ws.list_pairs, sh.nq, ws.qpb, ws.qdig,
-      sh.npmax, ix->offsets, ix->codes, ix->fac, ix->ids, ws.bound, ws.counts, ws.cand, ws.cap,
-      ix->d_err);
+      sh.npmax, ix->offsets, ix->codes, ix->fac, ix->ids, ws.bound, ws.wbase, ws.mwords, ws.mask,
+      ws.cand, ix->d_err);
   RQ_CUDA(cudaGetLastError());
   return RQ_OK;
 }

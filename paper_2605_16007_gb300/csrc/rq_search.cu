@@ -232,8 +232,8 @@ quantize_kernel(const float* __restrict__ qrot, const int32_t* __restrict__ prob
 
 // ---------------------------------------------------------------------------
 // Plain scan: one block per (query, probed list) -- the query-level schedule
-// of Section 3.3.1. Candidates at or below the query's bound are appended to
-// its candidate buffer.
+// of Section 3.3.1. Each warp writes the survivor mask word and the keys of
+// its 32 vectors (emit_word).
 // ---------------------------------------------------------------------------
 template <int NW4>
 __global__ void __launch_bounds__(128)
@@ -242,8 +242,8 @@ scan_plain_kernel(const int32_t* __restrict__ probe_ids, const int32_t* __restri
                   const uint32_t* __restrict__ planes, const int64_t* __restrict__ offsets,
                   const uint8_t* __restrict__ codes, const float2* __restrict__ fac,
                   const uint32_t* __restrict__ ids, int dp, const uint32_t* __restrict__ bound,
-                  int32_t* __restrict__ counts, uint64_t* __restrict__ cand, int64_t cap,
-                  int32_t* err) {
+                  const int32_t* __restrict__ wbase, int64_t mwords, uint32_t* __restrict__ mask,
+                  uint64_t* __restrict__ cand) {
   constexpr int W = 4 * NW4;
   __shared__ __align__(16) uint32_t s_pl[4 * W];
   const int64_t pair = blockIdx.x;
@@ -256,8 +256,10 @@ scan_plain_kernel(const int32_t* __restrict__ probe_ids, const int32_t* __restri
   const int c = probe_ids[pair];
   const int64_t lo = offsets[c], hi = offsets[c + 1];
   const uint32_t tau = bound[q];
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t wrow = q * mwords + wbase[pair];
   for (int64_t s0 = lo; s0 < hi; s0 += blockDim.x) {
+    if (s0 + warp * 32 >= hi) break;  // warp-uniform: this word is past the list's end
     const int64_t s = s0 + threadIdx.x;
     bool pass = false;
     float d = 0.0f;
@@ -266,7 +268,7 @@ scan_plain_kernel(const int32_t* __restrict__ probe_ids, const int32_t* __restri
       d = estimate_code<NW4>(cp, fac[s], s_pl, qp, dp);
       pass = orderable(d) <= tau;
     }
-    append_candidates(pass, d, s, ids, counts + q, cand + q * cap, cap, lane, err);
+    emit_word(pass, d, pass ? ids[s] : 0u, wrow + (s0 - lo) / 32 + warp, mask, cand, lane);
   }
 }
 
@@ -291,16 +293,16 @@ scan_grouped_kernel(const int2* __restrict__ items, int n_items, int32_t* __rest
                     const uint32_t* __restrict__ planes, int npmax,
                     const int64_t* __restrict__ offsets, const uint8_t* __restrict__ codes,
                     const float2* __restrict__ fac, const uint32_t* __restrict__ ids, int dp,
-                    const uint32_t* __restrict__ bound, int32_t* __restrict__ counts,
-                    uint64_t* __restrict__ cand, int64_t cap, int32_t* err) {
+                    const uint32_t* __restrict__ bound, const int32_t* __restrict__ wbase,
+                    int64_t mwords, uint32_t* __restrict__ mask, uint64_t* __restrict__ cand) {
   constexpr int W = 4 * NW4;
   constexpr int GP = GroupPairs<NW4>::value;
   __shared__ __align__(16) uint32_t s_pl[GP][4 * W];
   __shared__ float4 s_qp[GP];
   __shared__ uint32_t s_tau[GP];
-  __shared__ int32_t s_q[GP];
+  __shared__ int64_t s_wrow[GP];
   __shared__ int s_item;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(work_counter, 1);
     __syncthreads();
@@ -317,6 +319,8 @@ scan_grouped_kernel(const int2* __restrict__ items, int n_items, int32_t* __rest
     const int64_t hi = min(offsets[l + 1], lo + kGroupVectors);
     const int64_t s = lo + threadIdx.x;
     const bool valid = s < hi;
+    const bool word_valid = lo + warp * 32 < hi;
+    const int64_t word = w.y / 32 + warp;
     uint4 code[NW4];
     float2 f = make_float2(0.0f, 0.0f);
     int pc = 0;
@@ -343,7 +347,7 @@ scan_grouped_kernel(const int2* __restrict__ items, int n_items, int32_t* __rest
         const int pair = lp[g0 + g];
         const int q = pair / npmax;
         s_qp[g] = qparams[pair];
-        s_q[g] = q;
+        s_wrow[g] = (int64_t)q * mwords + wbase[pair];
         s_tau[g] = bound[q];
       }
       __syncthreads();
@@ -359,7 +363,9 @@ scan_grouped_kernel(const int2* __restrict__ items, int n_items, int32_t* __rest
             if (orderable(d[j]) <= s_tau[g]) passbits |= 1u << j;
           }
         }
-        append_chunk<16>(passbits, d, s_q + g0c, s, ids, counts, cand, cap, lane, err);
+        const uint32_t id = passbits ? ids[s] : 0u;
+        emit_chunk<16>(passbits, d, s_wrow + g0c, np - g0c, word, word_valid, id, mask, cand,
+                       lane);
       }
       __syncthreads();
     }
@@ -505,25 +511,28 @@ __device__ __forceinline__ float exact_dist_lanes(const RawT* __restrict__ x,
 // Per-warp shared memory of the finalize kernel: selection (P keys), top-k
 // (PK keys), histogram (256 ints), bucket (32 keys), query row (dim floats).
 struct FinalizeLayout {
-  int P, PK, S, dim;  // S: candidate keys staged per warp
+  int P, PK, S, dim;  // S: candidate keys staged per query (>= 2048: 64 mask words)
   __host__ __device__ int bytes() const {
     return (P + PK + S) * 8 + 256 * 4 + 32 * 8 + ((dim * 4 + 15) & ~15);
   }
 };
 
-// Four warps per query: warp 0 selects (radix passes over the candidates
-// staged in shared memory), all 128 threads gather and re-rank, warp 0
-// selects the final k.
+// Four warps per query: the candidates are collected from the scan's
+// survivor masks into shared memory (or compacted in place when there are
+// more than S), warp 0 selects (radix passes), all 128 threads gather and
+// re-rank, warp 0 selects the final k.
 template <typename RawT>
 __global__ void __launch_bounds__(128)
-finalize_kernel(const uint64_t* __restrict__ cand, int64_t cap, const int32_t* __restrict__ counts,
+finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ wtotal,
+                int64_t mwords, uint64_t* __restrict__ cand, int32_t* __restrict__ counts,
                 const int32_t* __restrict__ nsel, const int32_t* __restrict__ kq,
                 const int32_t* __restrict__ rerank_on, int nsel_max, uint64_t* __restrict__ sel,
                 const RawT* __restrict__ raw, const float* __restrict__ q, int dim, int k_stride,
-                FinalizeLayout lay, int64_t* __restrict__ out_ids, float* __restrict__ out_d,
-                int32_t* err) {
+                FinalizeLayout lay, int64_t* __restrict__ out_ids, float* __restrict__ out_d) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ int s_got;
+  __shared__ int s_part[4];
+  __shared__ int s_scan[2];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t row = blockIdx.x;
   uint64_t* s_sel = reinterpret_cast<uint64_t*>(smem);
@@ -532,22 +541,92 @@ finalize_kernel(const uint64_t* __restrict__ cand, int64_t cap, const int32_t* _
   uint64_t* small = reinterpret_cast<uint64_t*>(hist + 256);
   uint64_t* s_stage = small + 32;
   float* s_q = reinterpret_cast<float*>(s_stage + lay.S);
-  int64_t count = counts[row];
-  if (count > cap) {
-    if (tid == 0) flag_error(err, kErrCandidateOverflow);
-    count = cap;
+  const uint32_t* mrow = mask + row * mwords;
+  uint64_t* krow = cand + row * mwords * 32;
+  const int T = wtotal[row];
+  // Thread t takes mask words t, t + 128, ...: up to kRegWords of them are
+  // kept in registers; a block scan of their popcounts gives each thread its
+  // first staging position.
+  constexpr int kRegWords = 8;
+  const bool in_regs = T <= kRegWords * 128;
+  uint32_t mw[kRegWords];
+  int c = 0;
+  if (in_regs) {
+#pragma unroll
+    for (int r = 0; r < kRegWords; ++r) {
+      const int i = tid + 128 * r;
+      mw[r] = i < T ? mrow[i] : 0u;
+      c += __popc(mw[r]);
+    }
+  } else {
+    for (int i = tid; i < T; i += blockDim.x) c += __popc(mrow[i]);
   }
+  int incl = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) s_part[warp] = incl;
+  for (int d = tid; d < dim; d += blockDim.x) s_q[d] = q[row * dim + d];
+  __syncthreads();
+  int pos = incl - c;
+  for (int w = 0; w < warp; ++w) pos += s_part[w];
+  const int count = s_part[0] + s_part[1] + s_part[2] + s_part[3];
+  if (tid == 0) counts[row] = count;
   const int n_sel = nsel[row];
   const int k = kq[row];
   const bool rerank = rerank_on[row] != 0;
-  // Candidates that fit are read once (independent loads) into shared
-  // memory; the radix passes then read them there.
-  const uint64_t* src = cand + row * cap;
-  if (count <= lay.S && count > n_sel) {
-    for (int i = tid; i < count; i += blockDim.x) s_stage[i] = src[i];
-    src = s_stage;
+  const uint64_t* src = s_stage;
+  if (count <= lay.S) {
+    // The keys of a word are packed at the front of its 32 slots.
+    if (in_regs) {
+#pragma unroll
+      for (int r = 0; r < kRegWords; ++r) {
+        const int n = __popc(mw[r]);
+        const uint64_t* kw = krow + (int64_t)(tid + 128 * r) * 32;
+#pragma unroll 4
+        for (int b = 0; b < n; ++b) s_stage[pos + b] = kw[b];
+        pos += n;
+      }
+    } else {
+      for (int i = tid; i < T; i += blockDim.x) {
+        const int n = __popc(mrow[i]);
+        const uint64_t* kw = krow + (int64_t)i * 32;
+#pragma unroll 4
+        for (int b = 0; b < n; ++b) s_stage[pos + b] = kw[b];
+        pos += n;
+      }
+    }
+  } else {
+    // Many: compact the keys to the front of the query's key slots, 64 mask
+    // words (at most S = 2048 keys) at a time through shared memory. The
+    // keys written never reach the slots of words not yet staged.
+    int64_t run = 0;
+    for (int c0 = 0; c0 < T; c0 += 64) {
+      const uint32_t w = (tid < 64 && c0 + tid < T) ? mrow[c0 + tid] : 0u;
+      const int pc = __popc(w);
+      int ps = pc;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, ps, o);
+        if (lane >= o) ps += t;
+      }
+      if (warp < 2 && lane == 31) s_scan[warp] = ps;
+      __syncthreads();
+      const int tot = s_scan[0] + s_scan[1];
+      if (tid < 64 && pc) {
+        const int at = ps - pc + (warp == 1 ? s_scan[0] : 0);
+        const uint64_t* kw = krow + (int64_t)(c0 + tid) * 32;
+        for (int b = 0; b < pc; ++b) s_stage[at + b] = kw[b];
+      }
+      __syncthreads();
+      for (int i = tid; i < tot; i += blockDim.x) krow[run + i] = s_stage[i];
+      __syncthreads();
+      run += tot;
+    }
+    src = krow;
   }
-  for (int d = tid; d < dim; d += blockDim.x) s_q[d] = q[row * dim + d];
   __syncthreads();
   // Without re-rank the selection is the answer and is sorted; with re-rank
   // only the set matters and the exact keys are selected below.
@@ -588,7 +667,9 @@ constexpr int kProbeStageKeys = 2048;
 
 __global__ void __launch_bounds__(256)
 probe_select_warp_kernel(const uint64_t* __restrict__ pkeys, int nlist, int np, int64_t nq,
-                         int32_t* __restrict__ out_ids, float* __restrict__ out_d) {
+                         int32_t* __restrict__ out_ids, float* __restrict__ out_d,
+                         const int64_t* __restrict__ offsets, const int32_t* __restrict__ nprobe,
+                         int32_t* __restrict__ wbase, int32_t* __restrict__ wtotal) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -613,6 +694,28 @@ probe_select_warp_kernel(const uint64_t* __restrict__ pkeys, int nlist, int np, 
     out_d[row * np + j] =
         (k == kU64Max) ? __int_as_float(0x7f800000) : from_orderable((uint32_t)(k >> 32));
   }
+  // First survivor-mask word of each probe: running sum, in probe order, of
+  // the probed lists' 32-vector words (over the query's own nprobe).
+  if (wbase == nullptr) return;
+  const int npq = min(nprobe[row], got);
+  int carry = 0;
+  for (int j0 = 0; j0 < np; j0 += 32) {
+    const int j = j0 + lane;
+    int w = 0;
+    if (j < npq) {
+      const uint32_t l = (uint32_t)dst[j];
+      w = (int)((offsets[l + 1] - offsets[l] + 31) >> 5);
+    }
+    int incl = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (j < np) wbase[row * np + j] = carry + incl - w;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) wtotal[row] = carry;
 }
 
 // First bound (Section 3.3.3), four warps per query: lists in probe order
@@ -687,7 +790,8 @@ void rebase(T*& p, char* base) {
 rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, Workspace& ws) {
   const int64_t nq = sh.nq, np = sh.npmax;
   const int W = ix->dp / 32;
-  ws.cap = std::max<int64_t>(1, ix->top_len_prefix[std::min(np, (int64_t)ix->nlist)]);
+  ws.mwords = std::max<int64_t>(1, ix->top_words_prefix[std::min(np, (int64_t)ix->nlist)]);
+  ws.cap = 32 * ws.mwords;
   Layout L;
   L.take(&ws.q, nq * ix->dim);
   L.take(&ws.qrot, nq * ix->dp);
@@ -698,6 +802,9 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
   L.take(&ws.planes, nq * np * 4 * W);
   L.take(&ws.bound, nq);
   L.take(&ws.counts, nq);
+  L.take(&ws.mask, nq * ws.mwords);
+  L.take(&ws.wbase, nq * np);
+  L.take(&ws.wtotal, nq);
   L.take(&ws.cand, nq * ws.cap);
   L.take(&ws.sel, nq * sh.nsel_max);
   L.take(&ws.nprobe, nq);
@@ -733,6 +840,9 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
   rebase(ws.planes, b);
   rebase(ws.bound, b);
   rebase(ws.counts, b);
+  rebase(ws.mask, b);
+  rebase(ws.wbase, b);
+  rebase(ws.wtotal, b);
   rebase(ws.cand, b);
   rebase(ws.sel, b);
   rebase(ws.nprobe, b);
@@ -775,13 +885,12 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
         ws.probe_ids, ws.nprobe, np, ws.nsel, ws.qparams, ws.planes, ix->offsets, ix->codes,
         ix->fac, dp, ws.bound, ws.rerank_on + nq);
   }
-  RQ_CUDA(cudaMemsetAsync(ws.counts, 0, sizeof(int32_t) * nq, st));
   tm.mark(RQ_STAGE_WORKLIST, st);
   if (sh.mode == RQ_SCAN_PLAIN) {
     tm.mark(RQ_STAGE_SCAN, st);
     scan_plain_kernel<NW4><<<(unsigned)pairs, 128, 0, st>>>(
         ws.probe_ids, ws.nprobe, np, ws.qparams, ws.planes, ix->offsets, ix->codes, ix->fac,
-        ix->ids, dp, ws.bound, ws.counts, ws.cand, ws.cap, ix->d_err);
+        ix->ids, dp, ws.bound, ws.wbase, ws.mwords, ws.mask, ws.cand);
   } else {
     RQ_CUDA(cudaMemsetAsync(ws.work_count, 0, sizeof(int32_t) * 4, st));
     int sms = 148;
@@ -792,8 +901,8 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
     } else {
       scan_grouped_kernel<NW4><<<(unsigned)(sms * 8), kGroupVectors, 0, st>>>(
           ix->items, ix->n_items, ws.work_count, ws.list_count, ws.list_pairs, nq, ws.qparams,
-          ws.planes, np, ix->offsets, ix->codes, ix->fac, ix->ids, dp, ws.bound, ws.counts,
-          ws.cand, ws.cap, ix->d_err);
+          ws.planes, np, ix->offsets, ix->codes, ix->fac, ix->ids, dp, ws.bound, ws.wbase,
+          ws.mwords, ws.mask, ws.cand);
     }
   }
   return RQ_OK;
@@ -823,7 +932,8 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
       attr = true;
     }
     probe_select_warp_kernel<<<blocks_for(nq, wpb), wpb * 32, (size_t)wpb * per_warp, st>>>(
-        ws.pkeys, ix->nlist, np, nq, ws.probe_ids, ws.probe_d);
+        ws.pkeys, ix->nlist, np, nq, ws.probe_ids, ws.probe_d, ix->offsets, ws.nprobe, ws.wbase,
+        ws.wtotal);
   }
   // 3-4. quantisation, bound, scan
   switch (dp / 128) {
@@ -857,14 +967,14 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
     }
     if (ix->raw_dtype == RQ_U8)
       finalize_kernel<uint8_t><<<(unsigned)nq, 128, smem, st>>>(
-          ws.cand, ws.cap, ws.counts, ws.nsel, ws.kq, ws.rerank_on, sh.nsel_max, ws.sel,
-          static_cast<const uint8_t*>(ix->raw), ws.q, ix->dim, sh.k_stride, lay, ws.out_ids,
-          ws.out_d, ix->d_err);
+          ws.mask, ws.wtotal, ws.mwords, ws.cand, ws.counts, ws.nsel, ws.kq, ws.rerank_on,
+          sh.nsel_max, ws.sel, static_cast<const uint8_t*>(ix->raw), ws.q, ix->dim, sh.k_stride, lay,
+          ws.out_ids, ws.out_d);
     else
       finalize_kernel<float><<<(unsigned)nq, 128, smem, st>>>(
-          ws.cand, ws.cap, ws.counts, ws.nsel, ws.kq, ws.rerank_on, sh.nsel_max, ws.sel,
-          static_cast<const float*>(ix->raw), ws.q, ix->dim, sh.k_stride, lay, ws.out_ids,
-          ws.out_d, ix->d_err);
+          ws.mask, ws.wtotal, ws.mwords, ws.cand, ws.counts, ws.nsel, ws.kq, ws.rerank_on,
+          sh.nsel_max, ws.sel, static_cast<const float*>(ix->raw), ws.q, ix->dim, sh.k_stride, lay,
+          ws.out_ids, ws.out_d);
   }
   tm.mark(RQ_STAGE_RERANK, st);
   tm.mark(RQ_STAGE_COUNT, st);

@@ -97,6 +97,8 @@ def replay_and_compare(hix: dict, q: np.ndarray, dump: dict, prune: bool = True,
         n_sel = int(dump["nsel"][i])
         tau = R.first_bound(d2, n_sel) if prune else R.U32_MAX
         assert int(dump["bound"][i]) == int(tau), (i, "bound")
+        npass = int(np.count_nonzero(R.orderable(d2) <= np.uint64(tau)))
+        assert int(dump["n_candidates"][i]) == npass, (i, "candidates passing the bound")
         sel = R.select_candidates(d2, cid, n_sel, prune)
         gsel = np.sort(dump["selected"][i, :n_sel])   # a set when re-ranked
         assert np.array_equal(gsel[:sel.size], sel), (i, "selected keys")

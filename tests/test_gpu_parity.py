@@ -125,6 +125,16 @@ def test_search_stages_replay_bit_exact(tiny, mode, prune):
     assert np.abs(dump["qrot"] - qr).max() <= 1e-5 * np.abs(qr).max()
 
 
+@pytest.mark.parametrize("mode", [1, 2, 3])
+def test_many_candidates_replay_bit_exact(tiny, mode):
+    """No pruning and half of the lists probed: more candidates per query
+    than the finalize stages in shared memory at once (2048)."""
+    _, q, ix, h = tiny
+    dump = search_dump(ix, q[:24], 32, 10, 100, scan_mode=mode, no_prune=True)
+    assert dump["n_candidates"].min() > 2048
+    replay_and_compare(h, q[:24], dump, prune=False)
+
+
 def test_recall_target(tiny):
     x, q, ix, _ = tiny
     _, td = R.exact_knn(x, q, 10)
