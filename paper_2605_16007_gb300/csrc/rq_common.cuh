@@ -415,4 +415,138 @@ __device__ inline uint32_t warp_kth_u32(const uint32_t* src, int m, int rank, in
   return (uint32_t)__shfl_sync(0xffffffffu, v, rank - 1);
 }
 
+// ---------------------------------------------------------------------------
+// Block-level selection: every thread of the block takes part (histograms by
+// shared-memory atomics, the bucket search by warp 0). `hist` is 256 ints,
+// `small` 32 keys and `ctl` 8 ints of shared memory; src is shared memory.
+// ---------------------------------------------------------------------------
+
+// One narrowing step: histogram of the 8-bit digit at `shift` over the keys
+// whose bits under `mask` equal `prefix`, and the bucket holding the rank-th
+// (1-based) of them, as (b, count below b, count in b) in every thread.
+template <typename K>
+__device__ inline void block_narrow(const K* src, int m, int shift, K mask, K prefix, int rank,
+                                    int* hist, int* ctl, int& b, int& below, int& cnt) {
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const K k = src[i];
+    if ((k & mask) == prefix) atomicAdd(&hist[(int)((k >> shift) & 255)], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int bb, bl, bc;
+    warp_find_bucket(hist, rank, bb, bl, bc);
+    if (threadIdx.x == 0) {
+      ctl[0] = bb;
+      ctl[1] = bl;
+      ctl[2] = bc;
+    }
+  }
+  __syncthreads();
+  b = ctl[0];
+  below = ctl[1];
+  cnt = ctl[2];
+}
+
+// Sorts dst[0, n) ascending, dst[n, next_pow2(n)) holding all ones.
+__device__ inline void block_sort_keys(uint64_t* dst, int n) {
+  if (n <= 32) {
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      const uint64_t v = warp_sort32(lane < n ? dst[lane] : kU64Max);
+      if (lane < n) dst[lane] = v;
+    }
+    __syncthreads();
+    return;
+  }
+  block_bitonic_sort(dst, next_pow2(n));
+}
+
+// The n smallest of m distinct uint64 keys into dst[0, n) (ascending if
+// `sorted`, else in no fixed order), dst[n, next_pow2(n)) = all ones; dst
+// holds next_pow2(max(n, 1)) keys. Returns min(n, m).
+__device__ inline int block_select_smallest(const uint64_t* src, int m, int n, uint64_t* dst,
+                                            int* hist, uint64_t* small, int* ctl, bool sorted) {
+  const int tid = threadIdx.x;
+  const int sel = min(n, m);
+  const int mp = next_pow2(max(sel, 1));
+  if (m <= n) {
+    for (int i = tid; i < mp; i += blockDim.x) dst[i] = (i < m) ? src[i] : kU64Max;
+    __syncthreads();
+    if (sorted) block_sort_keys(dst, sel);
+    return sel;
+  }
+  uint64_t prefix = 0, mask = 0;
+  int rank = n, cnt = m;
+  for (int shift = 56; shift >= 0 && cnt > 32; shift -= 8) {
+    int b, below;
+    block_narrow<uint64_t>(src, m, shift, mask, prefix, rank, hist, ctl, b, below, cnt);
+    prefix |= (uint64_t)b << shift;
+    mask |= 0xFFull << shift;
+    rank -= below;
+  }
+  // Keys below the bucket go straight to dst; the bucket (at most 32 keys)
+  // is sorted in one warp and its first `rank` keys complete the selection.
+  if (tid == 0) {
+    ctl[3] = 0;
+    ctl[4] = 0;
+  }
+  __syncthreads();
+  for (int i = tid; i < m; i += blockDim.x) {
+    const uint64_t k = src[i];
+    const uint64_t km = k & mask;
+    if (km < prefix) {
+      dst[atomicAdd(&ctl[3], 1)] = k;
+    } else if (km == prefix) {
+      const int p = atomicAdd(&ctl[4], 1);
+      if (p < 32) small[p] = k;
+    }
+  }
+  __syncthreads();
+  if (tid < 32) {
+    const int ns = min(ctl[4], 32);
+    const uint64_t v = warp_sort32(tid < ns ? small[tid] : kU64Max);
+    if (tid < rank) dst[n - rank + tid] = v;
+  }
+  for (int i = n + tid; i < mp; i += blockDim.x) dst[i] = kU64Max;
+  __syncthreads();
+  if (sorted) block_sort_keys(dst, n);
+  return sel;
+}
+
+// The rank-th smallest (1-based) of m uint32 values (duplicates allowed).
+__device__ inline uint32_t block_kth_u32(const uint32_t* src, int m, int rank, int* hist,
+                                         uint64_t* small, int* ctl) {
+  uint32_t prefix = 0, mask = 0;
+  int cnt = m;
+  for (int shift = 24; shift >= 0 && cnt > 32; shift -= 8) {
+    int b, below;
+    block_narrow<uint32_t>(src, m, shift, mask, prefix, rank, hist, ctl, b, below, cnt);
+    prefix |= (uint32_t)b << shift;
+    mask |= 0xFFu << shift;
+    rank -= below;
+  }
+  if (mask == 0xFFFFFFFFu) return prefix;
+  // At most 32 values left in the bucket: sort them in one warp.
+  if (threadIdx.x == 0) ctl[4] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const uint32_t k = src[i];
+    if ((k & mask) == prefix) {
+      const int p = atomicAdd(&ctl[4], 1);
+      if (p < 32) small[p] = k;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int ns = min(ctl[4], 32);
+    const uint64_t v = warp_sort32(threadIdx.x < ns ? small[threadIdx.x] : kU64Max);
+    const uint64_t r = __shfl_sync(0xffffffffu, v, rank - 1);
+    if (threadIdx.x == 0) ctl[5] = (int)(uint32_t)r;
+  }
+  __syncthreads();
+  return (uint32_t)ctl[5];
+}
+
 }  // namespace rq

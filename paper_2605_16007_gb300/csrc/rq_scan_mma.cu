@@ -153,13 +153,11 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
       : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
+        "=r"(r[7])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -381,7 +379,11 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
         }
         tc_fence_after();
         // Epilogue: thread t = vector t = TMEM lane 32 (w % 4) + lane of
-        // tile w / 4; 16 pairs per TMEM load.
+        // tile w / 4; 8 pairs per TMEM load. The estimator's operations are
+        // the popcount form's, each rounded once: a = 2 ip - Sq is an exact
+        // small integer (one FMA with qp.w = -Sq gives it exactly); the final
+        // + 0 of the popcount form is left out because (nq2 + r^2) - x with
+        // nq2, r^2 >= +0 is never -0.
         {
           const int quarter = warp & 3, tile = warp >> 2;
           if (tile < ntiles) {
@@ -395,30 +397,30 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
               pc = __popc(cw.x) + __popc(cw.y) + __popc(cw.z) + __popc(cw.w);
             }
             const float bterm = (float)(2 * pc - kMmaK);
-            for (int c1 = 0; c1 < np; c1 += 16) {
-              uint32_t r[16];
-              tmem_ld16(taddr + ((uint32_t)(quarter * 32) << 16) +
-                            (uint32_t)(tile * kMmaNmax + c1), r);
-              float d[16];
+            const uint32_t tl = taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tile * kMmaNmax);
+            const int64_t word = m.v0 / 32 + warp;
+            for (int c1 = 0; c1 < np; c1 += 8) {
+              uint32_t r[8];
+              tmem_ld8(tl + (uint32_t)c1, r);
+              float d[8];
               uint32_t passbits = 0;
 #pragma unroll
-              for (int j = 0; j < 16; ++j) {
+              for (int j = 0; j < 8; ++j) {
                 const int g = c1 + j;
                 d[j] = 0.0f;
                 if (g < np) {
-                  const float4 qp = qp_s[g];
-                  const float ip = __uint_as_float(r[j]);
-                  const float a = __fsub_rn(__fmul_rn(2.0f, ip), (float)__float_as_int(qp.w));
+                  const float4 qp = qp_s[g];  // {vl, delta, nq2, -Sq}
+                  const float a = __fmaf_rn(2.0f, __uint_as_float(r[j]), qp.w);
                   const float t = __fadd_rn(__fmul_rn(qp.y, a), __fmul_rn(qp.x, bterm));
-                  float dd = __fsub_rn(__fadd_rn(qp.z, f.x), __fmul_rn(2.0f, __fmul_rn(f.y, t)));
-                  dd = __fadd_rn(dd, 0.0f);
+                  const float dd =
+                      __fsub_rn(__fadd_rn(qp.z, f.x), __fmul_rn(2.0f, __fmul_rn(f.y, t)));
                   d[j] = dd;
                   if (valid && orderable(dd) <= s_tau[g]) passbits |= 1u << j;
                 }
               }
               const uint32_t id = passbits ? ids_s[v] : 0u;
-              emit_chunk<16>(passbits, d, s_wrow + c1, np - c1, m.v0 / 32 + warp,
-                             warp * 32 < m.nvec, id, mask, cand, lane);
+              emit_chunk<8>(passbits, d, s_wrow + c1, np - c1, word, warp * 32 < m.nvec, id, mask,
+                            cand, lane);
             }
           }
         }

@@ -225,7 +225,8 @@ quantize_kernel(const float* __restrict__ qrot, const int32_t* __restrict__ prob
     qparams[pair] = qp;
     if (list_count) {
       list_pairs[(int64_t)c * nq + slot] = (int32_t)pair;
-      if (qpb) qpb[(int64_t)c * nq + slot] = qp;
+      if (qpb)  // the tensor-core scan's copy carries -Sq as a float
+        qpb[(int64_t)c * nq + slot] = make_float4(qp.x, qp.y, qp.z, -(float)__float_as_int(qp.w));
     }
   }
 }
@@ -530,7 +531,7 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
                 const RawT* __restrict__ raw, const float* __restrict__ q, int dim, int k_stride,
                 FinalizeLayout lay, int64_t* __restrict__ out_ids, float* __restrict__ out_d) {
   extern __shared__ __align__(16) uint8_t smem[];
-  __shared__ int s_got;
+  __shared__ int s_ctl[8];
   __shared__ int s_part[4];
   __shared__ int s_scan[2];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -630,12 +631,7 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
   __syncthreads();
   // Without re-rank the selection is the answer and is sorted; with re-rank
   // only the set matters and the exact keys are selected below.
-  if (warp == 0) {
-    const int got = warp_select_smallest(src, (int)count, n_sel, s_sel, hist, small, !rerank);
-    if (lane == 0) s_got = got;
-  }
-  __syncthreads();
-  const int got = s_got;
+  const int got = block_select_smallest(src, count, n_sel, s_sel, hist, small, s_ctl, !rerank);
   for (int j = tid; j < nsel_max; j += blockDim.x) sel[row * nsel_max + j] = (j < got) ? s_sel[j] : kU64Max;
   const float inf = __int_as_float(0x7f800000);
   const uint64_t* res = s_sel;
@@ -647,12 +643,7 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
       s_sel[i] = make_key(dist, id);
     }
     __syncthreads();
-    if (warp == 0) {
-      const int r = warp_select_smallest(s_sel, got, k, s_top, hist, small, true);
-      if (lane == 0) s_got = r;
-    }
-    __syncthreads();
-    kk = s_got;
+    kk = block_select_smallest(s_sel, got, k, s_top, hist, small, s_ctl, true);
     res = s_top;
   }
   for (int j = tid; j < k_stride; j += blockDim.x) {
@@ -662,38 +653,38 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
   }
 }
 
-// Probe selection: the np smallest (distance, list) keys of each query.
-constexpr int kProbeStageKeys = 2048;
+// Probe selection: one block of 128 threads per query selects the np
+// smallest (distance, list) keys of the query's centroid ranking.
+constexpr int kProbeStageKeys = 4096;
 
-__global__ void __launch_bounds__(256)
-probe_select_warp_kernel(const uint64_t* __restrict__ pkeys, int nlist, int np, int64_t nq,
-                         int32_t* __restrict__ out_ids, float* __restrict__ out_d,
-                         const int64_t* __restrict__ offsets, const int32_t* __restrict__ nprobe,
-                         int32_t* __restrict__ wbase, int32_t* __restrict__ wtotal) {
+__global__ void __launch_bounds__(128)
+probe_select_kernel(const uint64_t* __restrict__ pkeys, int nlist, int np, int64_t nq,
+                    int32_t* __restrict__ out_ids, float* __restrict__ out_d,
+                    const int64_t* __restrict__ offsets, const int32_t* __restrict__ nprobe,
+                    int32_t* __restrict__ wbase, int32_t* __restrict__ wtotal) {
   extern __shared__ __align__(16) uint8_t smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-  if (row >= nq) return;
+  __shared__ int hist[256];
+  __shared__ uint64_t small[32];
+  __shared__ int ctl[8];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t row = blockIdx.x;
   const int P = next_pow2(np);
-  const int S = nlist <= kProbeStageKeys ? nlist : 0;
-  uint8_t* base = smem + (size_t)warp * ((P + S) * 8 + 256 * 4 + 32 * 8);
-  uint64_t* dst = reinterpret_cast<uint64_t*>(base);
-  int* hist = reinterpret_cast<int*>(dst + P);
-  uint64_t* small = reinterpret_cast<uint64_t*>(hist + 256);
+  uint64_t* dst = reinterpret_cast<uint64_t*>(smem);
   const uint64_t* src = pkeys + row * nlist;
-  if (S) {
-    uint64_t* stage = small + 32;
-    for (int i = lane; i < nlist; i += 32) stage[i] = src[i];
-    __syncwarp();
+  if (nlist <= kProbeStageKeys) {
+    uint64_t* stage = dst + P;
+    for (int i = tid; i < nlist; i += blockDim.x) stage[i] = src[i];
+    __syncthreads();
     src = stage;
   }
-  const int got = warp_select_smallest(src, nlist, np, dst, hist, small, true);
-  for (int j = lane; j < np; j += 32) {
+  const int got = block_select_smallest(src, nlist, np, dst, hist, small, ctl, true);
+  for (int j = tid; j < np; j += blockDim.x) {
     const uint64_t k = (j < got) ? dst[j] : kU64Max;
     out_ids[row * np + j] = (k == kU64Max) ? -1 : (int32_t)(uint32_t)k;
     out_d[row * np + j] =
         (k == kU64Max) ? __int_as_float(0x7f800000) : from_orderable((uint32_t)(k >> 32));
   }
+  if (wbase == nullptr || warp != 0) return;
   // First survivor-mask word of each probe: running sum, in probe order, of
   // the probed lists' 32-vector words (over the query's own nprobe).
   if (wbase == nullptr) return;
@@ -734,7 +725,8 @@ bound_kernel(const int32_t* __restrict__ probe_ids, const int32_t* __restrict__ 
   __shared__ __align__(16) uint32_t s_pl[4 * W];
   __shared__ int hist[256];
   __shared__ uint64_t small[32];
-  const int tid = threadIdx.x, warp = tid >> 5;
+  __shared__ int ctl[8];
+  const int tid = threadIdx.x;
   const int64_t qi = blockIdx.x;
   const int n_sel = nsel[qi];
   if (*no_prune || n_sel <= 0) {
@@ -759,11 +751,9 @@ bound_kernel(const int32_t* __restrict__ probe_ids, const int32_t* __restrict__ 
     taken += m;
   }
   __syncthreads();
-  if (warp == 0) {
-    uint32_t tau = kU32Max;
-    if (taken >= n_sel) tau = warp_kth_u32(s_bkeys, taken, n_sel, hist, small);
-    if (tid == 0) bound[qi] = tau;
-  }
+  uint32_t tau = kU32Max;
+  if (taken >= n_sel) tau = block_kth_u32(s_bkeys, taken, n_sel, hist, small, ctl);
+  if (tid == 0) bound[qi] = tau;
 }
 
 // ---------------------------------------------------------------------------
@@ -923,17 +913,16 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
       ws.qrot, nq, ix->cR, ix->nlist, dp, nullptr, nullptr, ws.pkeys);
   {
     const int stage = ix->nlist <= kProbeStageKeys ? ix->nlist : 0;
-    const int per_warp = (next_pow2_host(np) + stage) * 8 + 256 * 4 + 32 * 8;
-    const int wpb = std::max(1, std::min(8, (64 * 1024) / per_warp));
+    const size_t smem = (size_t)(next_pow2_host(np) + stage) * 8;
     static bool attr = false;
     if (!attr) {
-      RQ_CUDA(cudaFuncSetAttribute(probe_select_warp_kernel,
+      RQ_CUDA(cudaFuncSetAttribute(probe_select_kernel,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
       attr = true;
     }
-    probe_select_warp_kernel<<<blocks_for(nq, wpb), wpb * 32, (size_t)wpb * per_warp, st>>>(
-        ws.pkeys, ix->nlist, np, nq, ws.probe_ids, ws.probe_d, ix->offsets, ws.nprobe, ws.wbase,
-        ws.wtotal);
+    probe_select_kernel<<<(unsigned)nq, 128, smem, st>>>(ws.pkeys, ix->nlist, np, nq,
+                                                        ws.probe_ids, ws.probe_d, ix->offsets,
+                                                        ws.nprobe, ws.wbase, ws.wtotal);
   }
   // 3-4. quantisation, bound, scan
   switch (dp / 128) {
