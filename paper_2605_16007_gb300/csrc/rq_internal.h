@@ -87,7 +87,8 @@ struct Workspace {
   int32_t* list_pairs = nullptr;  // nlist x nq: pair ids (q * npmax + p) per list
   int32_t* work_count = nullptr;  // work-item counter of the persistent scan
   uint8_t* qdig = nullptr;        // nlist x nq x D_p: per-list buckets of FP8 query digits
-  float4* qpb = nullptr;          // nlist x nq: per-list buckets of {vl, delta, nq2, -Sq}
+  float4* qpb = nullptr;          // nlist x nq (+2): per-list buckets of {vl, delta, nq2, -Sq},
+                                  // interleaved by slot couples
   int64_t mwords = 0;             // mask words per query
   int64_t cap = 0;                // key slots per query (32 mwords)
 };

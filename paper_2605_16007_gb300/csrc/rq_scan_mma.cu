@@ -162,6 +162,35 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Packed two-lane float32 arithmetic (add / mul / fma .rn.f32x2), each lane
+// rounded once to nearest even. A packed multiply whose result feeds a packed
+// add can still come out fused into one rounding, so they are used only where
+// that cannot change the result (an exact product, as in x + (-2) y).
+__device__ __forceinline__ float2 add2_rn(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 mul2_rn(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 fma2_rn(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
 // Byte offset of 16-byte chunk c of row r in a 128B-swizzled K-major tile.
 __device__ __forceinline__ uint32_t sw128_offset(int r, int c) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
@@ -183,11 +212,12 @@ __device__ __forceinline__ void named_bar_consumers() {
   asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory");
 }
 
-// Producer (one lane): fetch items from the global counter and fill the two
-// stages -- meta, the mask rows and bounds of the first group, then the TMA
-// copies of codes, factors, B tile and parameters, all completing on the
-// stage's `full` barrier. A stage is reused once its `empty` barrier shows
-// the consumers are done with it.
+// Producer (the whole warp): fetch items from the global counter (the next
+// index is fetched while the current item is prepared) and fill the two
+// stages -- meta, the mask rows and bounds of the first group (one pair per
+// lane), then lane 0 issues the TMA copies of codes, factors, row ids, B tile
+// and parameters, all completing on the stage's `full` barrier. A stage is
+// reused once its `empty` barrier shows the consumers are done with it.
 __device__ void producer_loop(uint8_t* sm, uint32_t sbase, const int2* __restrict__ items,
                               int n_items, int32_t* __restrict__ work_counter,
                               const int32_t* __restrict__ list_count,
@@ -198,62 +228,80 @@ __device__ void producer_loop(uint8_t* sm, uint32_t sbase, const int2* __restric
                               const uint8_t* __restrict__ qdb, const float4* __restrict__ qpb,
                               const uint32_t* __restrict__ bound,
                               const int32_t* __restrict__ wbase, int64_t mwords, int32_t* err) {
+  const int lane = threadIdx.x & 31;
   Meta* meta = reinterpret_cast<Meta*>(sm + kSmMeta);
+  int it_next = 0;
+  if (lane == 0) it_next = atomicAdd(work_counter, 1);
+  it_next = __shfl_sync(0xffffffffu, it_next, 0);
   for (int i = 0;; ++i) {
     const int st = i & 1;
     const uint32_t full = sbase + kSmBar + 8 * st;
     const uint32_t empty = sbase + kSmBar + 16 + 8 * st;
-    if (i >= 2 && !mbar_wait_bounded(empty, (uint32_t)(((i >> 1) - 1) & 1))) {
-      flag_error(err, kErrMmaTimeout);
-      meta[st].l = -1;
-      mbar_expect_tx_arrive(full, 0);
-      return;
+    if (i >= 2) {
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait_bounded(empty, (uint32_t)(((i >> 1) - 1) & 1)) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        if (lane == 0) {
+          flag_error(err, kErrMmaTimeout);
+          meta[st].l = -1;
+          mbar_expect_tx_arrive(full, 0);
+        }
+        return;
+      }
     }
-    const int it = atomicAdd(work_counter, 1);
+    const int it = it_next;
     if (it >= n_items) {
-      meta[st].l = -1;
-      mbar_expect_tx_arrive(full, 0);
+      if (lane == 0) {
+        meta[st].l = -1;
+        mbar_expect_tx_arrive(full, 0);
+      }
       return;
     }
+    if (lane == 0) it_next = atomicAdd(work_counter, 1);
     const int2 w = items[it];
     const int l = w.x;
     const int cnt = list_count[l];
     const int64_t lo = offsets[l] + w.y;
     const int nvec = (int)min((int64_t)kItemV, offsets[l + 1] - lo);
-    meta[st].l = l;
-    meta[st].lo = (int)lo;
-    meta[st].nvec = nvec;
-    meta[st].cnt = cnt;
-    meta[st].v0 = w.y;
-    if (cnt == 0) {
-      mbar_expect_tx_arrive(full, 0);
-      continue;
-    }
     const int np = min(kMmaNmax, cnt);
     const int32_t* lp = list_pairs + (int64_t)l * pair_stride;
     uint32_t* tau = reinterpret_cast<uint32_t*>(sm + kSmTau) + st * kMmaNmax;
     int64_t* wrow = reinterpret_cast<int64_t*>(sm + kSmWrow) + st * kMmaNmax;
-    for (int g = 0; g < np; ++g) {
+    for (int g = lane; g < np; g += 32) {
       const int pair = lp[g];
       const int q = pair / npmax;
       wrow[g] = (int64_t)q * mwords + wbase[pair];
       tau[g] = bound[q];
     }
-    const int64_t lo_al = lo & ~(int64_t)1;
-    const uint32_t fac_bytes = (uint32_t)((((lo - lo_al) + nvec) * 8 + 15) & ~15);
-    const int64_t lo_al4 = lo & ~(int64_t)3;
-    const uint32_t id_bytes = (uint32_t)((((lo - lo_al4) + nvec) * 4 + 15) & ~15);
-    const uint32_t code_bytes = (uint32_t)nvec * 16;
-    const uint32_t b_bytes = (uint32_t)np * kMmaK;
-    const uint32_t qp_bytes = (uint32_t)np * 16;
-    mbar_expect_tx_arrive(full, code_bytes + fac_bytes + id_bytes + b_bytes + qp_bytes);
-    tma_load_1d(sbase + kSmCode + st * kItemV * 16, codes + lo * 16, code_bytes, full);
-    tma_load_1d(sbase + kSmFac + st * kFacBytes, fac + lo_al, fac_bytes, full);
-    tma_load_1d(sbase + kSmIds + st * kIdBytes, ids + lo_al4, id_bytes, full);
-    tma_load_1d(sbase + kSmB + st * kMmaNmax * kMmaK, qdb + (int64_t)l * pair_stride * kMmaK,
-                b_bytes, full);
-    tma_load_1d(sbase + kSmQp + st * kMmaNmax * 16, qpb + (int64_t)l * pair_stride, qp_bytes,
-                full);
+    __syncwarp();
+    if (lane == 0) {
+      meta[st].l = l;
+      meta[st].lo = (int)lo;
+      meta[st].nvec = nvec;
+      meta[st].cnt = cnt;
+      meta[st].v0 = w.y;
+      if (cnt == 0) {
+        mbar_expect_tx_arrive(full, 0);
+      } else {
+        const int64_t lo_al = lo & ~(int64_t)1;
+        const uint32_t fac_bytes = (uint32_t)((((lo - lo_al) + nvec) * 8 + 15) & ~15);
+        const int64_t lo_al4 = lo & ~(int64_t)3;
+        const uint32_t id_bytes = (uint32_t)((((lo - lo_al4) + nvec) * 4 + 15) & ~15);
+        const uint32_t code_bytes = (uint32_t)nvec * 16;
+        const uint32_t b_bytes = (uint32_t)np * kMmaK;
+        const uint32_t qp_bytes = (uint32_t)((np + 1) & ~1) * 16;
+        mbar_expect_tx_arrive(full, code_bytes + fac_bytes + id_bytes + b_bytes + qp_bytes);
+        tma_load_1d(sbase + kSmCode + st * kItemV * 16, codes + lo * 16, code_bytes, full);
+        tma_load_1d(sbase + kSmFac + st * kFacBytes, fac + lo_al, fac_bytes, full);
+        tma_load_1d(sbase + kSmIds + st * kIdBytes, ids + lo_al4, id_bytes, full);
+        tma_load_1d(sbase + kSmB + st * kMmaNmax * kMmaK, qdb + (int64_t)l * pair_stride * kMmaK,
+                    b_bytes, full);
+        tma_load_1d(sbase + kSmQp + st * kMmaNmax * 16, qpb + (int64_t)l * pair_stride, qp_bytes,
+                    full);
+      }
+    }
+    it_next = __shfl_sync(0xffffffffu, it_next, 0);
   }
 }
 
@@ -290,8 +338,7 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
   const uint32_t taddr = *s_tmem;
 
   if (warp == kConsumers / 32) {
-    if (lane == 0)
-      producer_loop(sm, sbase, items, n_items, work_counter, list_count, list_pairs, pair_stride,
+    producer_loop(sm, sbase, items, n_items, work_counter, list_count, list_pairs, pair_stride,
                     npmax, offsets, codes, fac, ids, qdb, qpb, bound, wbase, mwords, err);
   } else {
     uint32_t ph_mma = 0, ph_aux = 0;
@@ -321,12 +368,12 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
           // consumers reload this stage's B tile, parameters and bounds.
           named_bar_consumers();
           if (tid == 0) {
-            mbar_expect_tx_arrive(bar_aux, (uint32_t)np * (kMmaK + 16));
+            mbar_expect_tx_arrive(bar_aux, (uint32_t)np * kMmaK + (uint32_t)((np + 1) & ~1) * 16);
             tma_load_1d(sbase + kSmB + st * kMmaNmax * kMmaK,
                         qdb + ((int64_t)m.l * pair_stride + g0) * kMmaK, (uint32_t)np * kMmaK,
                         bar_aux);
             tma_load_1d(sbase + kSmQp + st * kMmaNmax * 16, qpb + (int64_t)m.l * pair_stride + g0,
-                        (uint32_t)np * 16, bar_aux);
+                        (uint32_t)((np + 1) & ~1) * 16, bar_aux);
           }
           for (int g = tid; g < np; g += kConsumers) {
             const int pair = lp[g0 + g];
@@ -379,11 +426,13 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
         }
         tc_fence_after();
         // Epilogue: thread t = vector t = TMEM lane 32 (w % 4) + lane of
-        // tile w / 4; 8 pairs per TMEM load. The estimator's operations are
-        // the popcount form's, each rounded once: a = 2 ip - Sq is an exact
-        // small integer (one FMA with qp.w = -Sq gives it exactly); the final
-        // + 0 of the popcount form is left out because (nq2 + r^2) - x with
-        // nq2, r^2 >= +0 is never -0.
+        // tile w / 4; 8 pairs per TMEM load, two at a time, partly in packed
+        // float2 operations. The estimator's operations are the popcount
+        // form's, each rounded once: a = 2 ip - Sq is an exact small integer
+        // (one FMA with -Sq gives it exactly); x - 2 y is x + (-2) y (the
+        // negation and the doubling are exact, so fusing them with the add
+        // rounds the same); the final + 0 of the popcount form is left out
+        // because (nq2 + r^2) - x with nq2, r^2 >= +0 is never -0.
         {
           const int quarter = warp & 3, tile = warp >> 2;
           if (tile < ntiles) {
@@ -397,6 +446,10 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
               pc = __popc(cw.x) + __popc(cw.y) + __popc(cw.z) + __popc(cw.w);
             }
             const float bterm = (float)(2 * pc - kMmaK);
+            const float2 r2 = make_float2(f.x, f.x);
+            const float2 f2 = make_float2(f.y, f.y);
+            const float2 two = make_float2(2.0f, 2.0f), mtwo = make_float2(-2.0f, -2.0f);
+            const uint2* tau2 = reinterpret_cast<const uint2*>(s_tau);
             const uint32_t tl = taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tile * kMmaNmax);
             const int64_t word = m.v0 / 32 + warp;
             for (int c1 = 0; c1 < np; c1 += 8) {
@@ -405,17 +458,27 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
               float d[8];
               uint32_t passbits = 0;
 #pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                const int g = c1 + j;
-                d[j] = 0.0f;
+              for (int h = 0; h < 4; ++h) {
+                const int g = c1 + 2 * h;
+                d[2 * h] = 0.0f;
+                d[2 * h + 1] = 0.0f;
                 if (g < np) {
-                  const float4 qp = qp_s[g];  // {vl, delta, nq2, -Sq}
-                  const float a = __fmaf_rn(2.0f, __uint_as_float(r[j]), qp.w);
-                  const float t = __fadd_rn(__fmul_rn(qp.y, a), __fmul_rn(qp.x, bterm));
-                  const float dd =
-                      __fsub_rn(__fadd_rn(qp.z, f.x), __fmul_rn(2.0f, __fmul_rn(f.y, t)));
-                  d[j] = dd;
-                  if (valid && orderable(dd) <= s_tau[g]) passbits |= 1u << j;
+                  const float4 qa = qp_s[g];      // {vl, vl', delta, delta'}
+                  const float4 qb = qp_s[g + 1];  // {nq2, nq2', -Sq, -Sq'}
+                  const float2 ip = make_float2(__uint_as_float(r[2 * h]), __uint_as_float(r[2 * h + 1]));
+                  const float2 a = fma2_rn(two, ip, make_float2(qb.z, qb.w));
+                  // t in scalar operations: a packed multiply feeding a packed
+                  // add may be contracted into one fused operation.
+                  const float2 t = make_float2(
+                      __fadd_rn(__fmul_rn(qa.z, a.x), __fmul_rn(qa.x, bterm)),
+                      __fadd_rn(__fmul_rn(qa.w, a.y), __fmul_rn(qa.y, bterm)));
+                  const float2 base = add2_rn(make_float2(qb.x, qb.y), r2);
+                  const float2 dd = add2_rn(base, mul2_rn(mtwo, mul2_rn(f2, t)));
+                  d[2 * h] = dd.x;
+                  d[2 * h + 1] = dd.y;
+                  const uint2 tt = tau2[g >> 1];
+                  if (valid && orderable(dd.x) <= tt.x) passbits |= 1u << (2 * h);
+                  if (valid && g + 1 < np && orderable(dd.y) <= tt.y) passbits |= 2u << (2 * h);
                 }
               }
               const uint32_t id = passbits ? ids_s[v] : 0u;

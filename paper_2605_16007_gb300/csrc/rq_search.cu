@@ -225,8 +225,16 @@ quantize_kernel(const float* __restrict__ qrot, const int32_t* __restrict__ prob
     qparams[pair] = qp;
     if (list_count) {
       list_pairs[(int64_t)c * nq + slot] = (int32_t)pair;
-      if (qpb)  // the tensor-core scan's copy carries -Sq as a float
-        qpb[(int64_t)c * nq + slot] = make_float4(qp.x, qp.y, qp.z, -(float)__float_as_int(qp.w));
+      if (qpb) {
+        // The tensor-core scan's copy, interleaved by slot couples for its
+        // packed float2 arithmetic: slots 2k, 2k + 1 of a bucket hold
+        // {vl, vl', delta, delta'} {nq2, nq2', -Sq, -Sq'} (Sq as a float).
+        float* cp = reinterpret_cast<float*>(qpb + (int64_t)c * nq + (slot & ~1)) + (slot & 1);
+        cp[0] = vl;
+        cp[2] = delta;
+        cp[4] = nq2;
+        cp[6] = -(float)sq;
+      }
     }
   }
 }
@@ -810,7 +818,7 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
   }
   if (sh.mode == RQ_SCAN_MMA) {
     L.take(&ws.qdig, (int64_t)ix->nlist * nq * ix->dp);
-    L.take(&ws.qpb, (int64_t)ix->nlist * nq);
+    L.take(&ws.qpb, (int64_t)ix->nlist * nq + 2);  // + a couple read past the last bucket
   }
   ws.bytes = L.off;
   (void)st;
