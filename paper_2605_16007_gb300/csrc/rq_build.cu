@@ -760,6 +760,16 @@ rq_status finish_index_host_side(rq_index* ix) {
     len[l] = ix->h_offsets[l + 1] - ix->h_offsets[l];
     for (int64_t v = 0; v < len[l]; v += kGroupVectors) items.push_back(make_int2(l, (int)v));
   }
+  // Persistent scans take items in this order: blocks of the longest lists
+  // first (longer lists are near more queries, so their items tend to carry
+  // more pairs), full blocks before a list's tail -- the costly items start
+  // early and the cheap ones fill the end.
+  std::stable_sort(items.begin(), items.end(), [&](const int2& a, const int2& b) {
+    const int64_t na = std::min<int64_t>(kGroupVectors, len[a.x] - a.y);
+    const int64_t nb = std::min<int64_t>(kGroupVectors, len[b.x] - b.y);
+    if (len[a.x] != len[b.x]) return len[a.x] > len[b.x];
+    return na > nb;
+  });
   std::sort(len.begin(), len.end(), std::greater<int64_t>());
   ix->top_len_prefix.assign(ix->nlist + 1, 0);
   ix->top_words_prefix.assign(ix->nlist + 1, 0);

@@ -421,17 +421,19 @@ __device__ inline uint32_t warp_kth_u32(const uint32_t* src, int m, int rank, in
 // `small` 32 keys and `ctl` 8 ints of shared memory; src is shared memory.
 // ---------------------------------------------------------------------------
 
-// One narrowing step: histogram of the 8-bit digit at `shift` over the keys
-// whose bits under `mask` equal `prefix`, and the bucket holding the rank-th
-// (1-based) of them, as (b, count below b, count in b) in every thread.
+// One narrowing step: histogram of the digit of `width` (<= 8) bits at
+// `shift` over the keys whose bits under `mask` equal `prefix`, and the
+// bucket holding the rank-th (1-based) of them, as (b, count below b, count
+// in b) in every thread.
 template <typename K>
-__device__ inline void block_narrow(const K* src, int m, int shift, K mask, K prefix, int rank,
-                                    int* hist, int* ctl, int& b, int& below, int& cnt) {
+__device__ inline void block_narrow(const K* src, int m, int shift, int width, K mask, K prefix,
+                                    int rank, int* hist, int* ctl, int& b, int& below, int& cnt) {
+  const K dmask = ((K)1 << width) - 1;
   for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
   __syncthreads();
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     const K k = src[i];
-    if ((k & mask) == prefix) atomicAdd(&hist[(int)((k >> shift) & 255)], 1);
+    if ((k & mask) == prefix) atomicAdd(&hist[(int)((k >> shift) & dmask)], 1);
   }
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -447,6 +449,26 @@ __device__ inline void block_narrow(const K* src, int m, int shift, K mask, K pr
   b = ctl[0];
   below = ctl[1];
   cnt = ctl[2];
+}
+
+// Highest bit in which the m keys differ (-1 when all are equal): the radix
+// passes start there, since the bits above it are common to every key (the
+// leading bits of nearby float32 distances usually are). `red` holds 2 x 32
+// keys of shared memory.
+template <typename K>
+__device__ inline int block_top_diff_bit(const K* src, int m, K* red) {
+  const K k0 = src[0];
+  K x = 0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) x |= src[i] ^ k0;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) x |= __shfl_xor_sync(0xffffffffu, x, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+  __syncthreads();
+  K all = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) all |= red[w];
+  __syncthreads();
+  if (all == 0) return -1;
+  return (int)(sizeof(K) * 8) - 1 - (sizeof(K) == 8 ? __clzll((long long)all) : __clz((int)all));
 }
 
 // Sorts dst[0, n) ascending, dst[n, next_pow2(n)) holding all ones.
@@ -477,14 +499,20 @@ __device__ inline int block_select_smallest(const uint64_t* src, int m, int n, u
     if (sorted) block_sort_keys(dst, sel);
     return sel;
   }
-  uint64_t prefix = 0, mask = 0;
+  // Digits of up to 8 bits from the highest bit where the keys differ; the
+  // bits above it are common and go into the prefix at once.
+  const int top = block_top_diff_bit<uint64_t>(src, m, small);
+  uint64_t mask = top < 0 ? ~0ull : (top >= 63 ? 0 : ~((2ull << top) - 1));
+  uint64_t prefix = src[0] & mask;
   int rank = n, cnt = m;
-  for (int shift = 56; shift >= 0 && cnt > 32; shift -= 8) {
+  for (int hb = top; hb >= 0 && cnt > 32;) {
+    const int shift = max(0, hb - 7), width = hb - shift + 1;
     int b, below;
-    block_narrow<uint64_t>(src, m, shift, mask, prefix, rank, hist, ctl, b, below, cnt);
+    block_narrow<uint64_t>(src, m, shift, width, mask, prefix, rank, hist, ctl, b, below, cnt);
     prefix |= (uint64_t)b << shift;
-    mask |= 0xFFull << shift;
+    mask |= ((1ull << width) - 1) << shift;
     rank -= below;
+    hb = shift - 1;
   }
   // Keys below the bucket go straight to dst; the bucket (at most 32 keys)
   // is sorted in one warp and its first `rank` keys complete the selection.
@@ -518,14 +546,19 @@ __device__ inline int block_select_smallest(const uint64_t* src, int m, int n, u
 // The rank-th smallest (1-based) of m uint32 values (duplicates allowed).
 __device__ inline uint32_t block_kth_u32(const uint32_t* src, int m, int rank, int* hist,
                                          uint64_t* small, int* ctl) {
-  uint32_t prefix = 0, mask = 0;
+  const int top = block_top_diff_bit<uint32_t>(src, m, reinterpret_cast<uint32_t*>(small));
+  if (top < 0) return src[0];
+  uint32_t mask = top >= 31 ? 0u : ~((2u << top) - 1u);
+  uint32_t prefix = src[0] & mask;
   int cnt = m;
-  for (int shift = 24; shift >= 0 && cnt > 32; shift -= 8) {
+  for (int hb = top; hb >= 0 && cnt > 32;) {
+    const int shift = max(0, hb - 7), width = hb - shift + 1;
     int b, below;
-    block_narrow<uint32_t>(src, m, shift, mask, prefix, rank, hist, ctl, b, below, cnt);
+    block_narrow<uint32_t>(src, m, shift, width, mask, prefix, rank, hist, ctl, b, below, cnt);
     prefix |= (uint32_t)b << shift;
-    mask |= 0xFFu << shift;
+    mask |= ((1u << width) - 1u) << shift;
     rank -= below;
+    hb = shift - 1;
   }
   if (mask == 0xFFFFFFFFu) return prefix;
   // At most 32 values left in the bucket: sort them in one warp.

@@ -212,9 +212,9 @@ __device__ __forceinline__ void named_bar_consumers() {
   asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory");
 }
 
-// Producer (the whole warp): fetch items from the global counter (the next
-// index is fetched while the current item is prepared) and fill the two
-// stages -- meta, the mask rows and bounds of the first group (one pair per
+// Producer (the whole warp): once a stage is free, take the next item from
+// the global counter (no earlier, so that near the end no block holds items
+// that another, idle block could run) and fill the stage -- meta, the mask rows and bounds of the first group (one pair per
 // lane), then lane 0 issues the TMA copies of codes, factors, row ids, B tile
 // and parameters, all completing on the stage's `full` barrier. A stage is
 // reused once its `empty` barrier shows the consumers are done with it.
@@ -230,9 +230,6 @@ __device__ void producer_loop(uint8_t* sm, uint32_t sbase, const int2* __restric
                               const int32_t* __restrict__ wbase, int64_t mwords, int32_t* err) {
   const int lane = threadIdx.x & 31;
   Meta* meta = reinterpret_cast<Meta*>(sm + kSmMeta);
-  int it_next = 0;
-  if (lane == 0) it_next = atomicAdd(work_counter, 1);
-  it_next = __shfl_sync(0xffffffffu, it_next, 0);
   for (int i = 0;; ++i) {
     const int st = i & 1;
     const uint32_t full = sbase + kSmBar + 8 * st;
@@ -250,7 +247,9 @@ __device__ void producer_loop(uint8_t* sm, uint32_t sbase, const int2* __restric
         return;
       }
     }
-    const int it = it_next;
+    int it = 0;
+    if (lane == 0) it = atomicAdd(work_counter, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= n_items) {
       if (lane == 0) {
         meta[st].l = -1;
@@ -258,7 +257,6 @@ __device__ void producer_loop(uint8_t* sm, uint32_t sbase, const int2* __restric
       }
       return;
     }
-    if (lane == 0) it_next = atomicAdd(work_counter, 1);
     const int2 w = items[it];
     const int l = w.x;
     const int cnt = list_count[l];
@@ -301,7 +299,6 @@ __device__ void producer_loop(uint8_t* sm, uint32_t sbase, const int2* __restric
                     full);
       }
     }
-    it_next = __shfl_sync(0xffffffffu, it_next, 0);
   }
 }
 

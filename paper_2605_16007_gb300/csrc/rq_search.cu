@@ -681,6 +681,7 @@ probe_select_kernel(const uint64_t* __restrict__ pkeys, int nlist, int np, int64
   const uint64_t* src = pkeys + row * nlist;
   if (nlist <= kProbeStageKeys) {
     uint64_t* stage = dst + P;
+#pragma unroll 8
     for (int i = tid; i < nlist; i += blockDim.x) stage[i] = src[i];
     __syncthreads();
     src = stage;
@@ -718,22 +719,26 @@ probe_select_kernel(const uint64_t* __restrict__ pkeys, int nlist, int np, int64
 }
 
 // First bound (Section 3.3.3), four warps per query: lists in probe order
-// give the first max(1024, n_sel) candidates, estimated by all 128 threads;
-// warp 0 takes the n_sel-th smallest orderable estimate (all ones when the
-// query has fewer candidates).
+// give the first max(1024, n_sel) candidates, estimated by all 128 threads
+// (the list ranges of the first 32 probes read at once, each thread's codes
+// loaded before its estimates); the block then takes the n_sel-th smallest
+// orderable estimate (all ones when the query has fewer candidates).
 template <int NW4>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 8)
 bound_kernel(const int32_t* __restrict__ probe_ids, const int32_t* __restrict__ nprobe,
              int npmax, const int32_t* __restrict__ nsel, const float4* __restrict__ qparams,
              const uint32_t* __restrict__ planes, const int64_t* __restrict__ offsets,
              const uint8_t* __restrict__ codes, const float2* __restrict__ fac, int dp,
              uint32_t* __restrict__ bound, const int32_t* __restrict__ no_prune) {
   constexpr int W = 4 * NW4;
+  constexpr int RB = NW4 >= 4 ? 1 : 4 / NW4;  // codes in flight per thread
   extern __shared__ __align__(16) uint32_t s_bkeys[];
   __shared__ __align__(16) uint32_t s_pl[4 * W];
   __shared__ int hist[256];
   __shared__ uint64_t small[32];
   __shared__ int ctl[8];
+  __shared__ int64_t s_lo[32];
+  __shared__ int64_t s_len[32];
   const int tid = threadIdx.x;
   const int64_t qi = blockIdx.x;
   const int n_sel = nsel[qi];
@@ -741,20 +746,56 @@ bound_kernel(const int32_t* __restrict__ probe_ids, const int32_t* __restrict__ 
     if (tid == 0) bound[qi] = kU32Max;
     return;
   }
+  const int npq = nprobe[qi];
+  if (tid < 32 && tid < npq) {
+    const int c = probe_ids[qi * npmax + tid];
+    const int64_t lo = offsets[c];
+    s_lo[tid] = lo;
+    s_len[tid] = offsets[c + 1] - lo;
+  }
   const int cap1 = max(kBoundCandidates, n_sel);
   int taken = 0;
-  for (int p = 0; p < nprobe[qi] && taken < cap1; ++p) {
+  for (int p = 0; p < npq && taken < cap1; ++p) {
     const int64_t pair = qi * npmax + p;
-    const int c = probe_ids[pair];
-    const int64_t lo = offsets[c];
-    const int m = (int)min(offsets[c + 1] - lo, (int64_t)(cap1 - taken));
     __syncthreads();
+    int64_t lo, len;
+    if (p < 32) {
+      lo = s_lo[p];
+      len = s_len[p];
+    } else {
+      const int c = probe_ids[pair];
+      lo = offsets[c];
+      len = offsets[c + 1] - lo;
+    }
+    const int m = (int)min(len, (int64_t)(cap1 - taken));
     for (int i = tid; i < 4 * W; i += blockDim.x) s_pl[i] = planes[pair * 4 * W + i];
     __syncthreads();
     const float4 qp = qparams[pair];
-    for (int i = tid; i < m; i += blockDim.x) {
-      const uint4* cp = reinterpret_cast<const uint4*>(codes + (lo + i) * (dp / 8));
-      s_bkeys[taken + i] = orderable(estimate_code<NW4>(cp, __ldg(fac + lo + i), s_pl, qp, dp));
+    for (int base = 0; base < m; base += 128 * RB) {
+      uint4 code[RB][NW4];
+      float2 fv[RB];
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        const int i = base + tid + 128 * r;
+        if (i < m) {
+          const uint4* cp = reinterpret_cast<const uint4*>(codes + (lo + i) * (dp / 8));
+#pragma unroll
+          for (int w = 0; w < NW4; ++w) code[r][w] = __ldg(cp + w);
+          fv[r] = __ldg(fac + lo + i);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        const int i = base + tid + 128 * r;
+        if (i < m) {
+          int pc = 0;
+#pragma unroll
+          for (int w = 0; w < NW4; ++w)
+            pc += __popc(code[r][w].x) + __popc(code[r][w].y) + __popc(code[r][w].z) +
+                  __popc(code[r][w].w);
+          s_bkeys[taken + i] = orderable(estimate_regs<NW4>(code[r], pc, fv[r], s_pl, qp, dp));
+        }
+      }
     }
     taken += m;
   }
