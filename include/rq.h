@@ -110,10 +110,12 @@ typedef struct rq_search_dump {
 /* Stages of one search, for rq_search_opts.stage_ms. */
 typedef enum rq_stage {
   RQ_STAGE_ROTATE = 0,   /* q' = P^T q */
-  RQ_STAGE_PROBE = 1,    /* centroid distances + nprobe selection */
-  RQ_STAGE_QUANTIZE = 2, /* residuals to 4-bit planes */
-  RQ_STAGE_BOUND = 3,    /* first pruning bound per query */
-  RQ_STAGE_WORKLIST = 4, /* grouping of (query, list) pairs (grouped modes) */
+  RQ_STAGE_PROBE = 1,    /* centroid distances */
+  RQ_STAGE_QUANTIZE = 2, /* per query, one fused step: nprobe selection,
+                            residuals to 4-bit planes, first pruning bound */
+  RQ_STAGE_BOUND = 3,    /* (runs inside RQ_STAGE_QUANTIZE; reads 0) */
+  RQ_STAGE_WORKLIST = 4, /* (pairs are grouped by list inside
+                            RQ_STAGE_QUANTIZE; reads 0) */
   RQ_STAGE_SCAN = 5,     /* the code scan */
   RQ_STAGE_SELECT = 6,   /* candidate selection fused with the exact re-rank */
   RQ_STAGE_RERANK = 7,   /* (runs inside RQ_STAGE_SELECT; reads 0) */

@@ -151,25 +151,16 @@ select_rows_kernel(const uint64_t* __restrict__ keys, int64_t row_stride,
 // (dimension d -> word d/32, bit d%32).
 // ---------------------------------------------------------------------------
 template <int NW4>
-__global__ void __launch_bounds__(256)
-quantize_kernel(const float* __restrict__ qrot, const int32_t* __restrict__ probe_ids,
-                const int32_t* __restrict__ nprobe, int npmax, int64_t nq,
-                const float* __restrict__ cR, int dp, float4* __restrict__ qparams,
-                uint32_t* __restrict__ planes, int32_t* __restrict__ list_count,
-                int32_t* __restrict__ list_pairs, uint8_t* __restrict__ qdb,
-                float4* __restrict__ qpb, int32_t* err) {
+__device__ __forceinline__ void quantize_pair(int64_t pair, int64_t q, int c, int lane,
+                                              const float* __restrict__ qrot, int64_t nq,
+                                              const float* __restrict__ cR, int dp,
+                                              float4* __restrict__ qparams,
+                                              uint32_t* __restrict__ planes,
+                                              int32_t* __restrict__ list_count,
+                                              int32_t* __restrict__ list_pairs,
+                                              uint8_t* __restrict__ qdb,
+                                              float4* __restrict__ qpb) {
   constexpr int PER = 4 * NW4;  // values per lane (dp / 32)
-  const int64_t pair = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (pair >= nq * npmax) return;
-  const int64_t q = pair / npmax;
-  const int p = (int)(pair % npmax);
-  if (p >= nprobe[q]) return;
-  const int c = probe_ids[pair];
-  if (c < 0) {
-    if (lane == 0) flag_error(err, kErrBadProbe);
-    return;
-  }
   // Grouped scans: the pair takes the next slot of its list's bucket (room
   // for every query of the batch).
   int slot = 0;
@@ -383,13 +374,21 @@ scan_grouped_kernel(const int2* __restrict__ items, int n_items, int32_t* __rest
 
 // ---------------------------------------------------------------------------
 // Rotation with more blocks: 16 queries x 64 output columns per block, K in
-// chunks of 128 staged in shared memory.
+// chunks of 128 staged in shared memory. The first column of blocks also
+// clears the search's counters (zero0[n0], zero1[n1]) for the later stages.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 rotate16_kernel(const float* __restrict__ q, int64_t nq, int dim, const float* __restrict__ P32,
-                int dp, float* __restrict__ qrot) {
+                int dp, float* __restrict__ qrot, int32_t* __restrict__ zero0, int n0,
+                int32_t* __restrict__ zero1, int n1) {
   __shared__ float As[16][129];
   __shared__ float Bs[128][64];
+  if (blockIdx.y == 0) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n0; i += gridDim.x * blockDim.x)
+      zero0[i] = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += gridDim.x * blockDim.x)
+      zero1[i] = 0;
+  }
   const int r = threadIdx.x >> 4, cg = threadIdx.x & 15;
   const int64_t r0 = (int64_t)blockIdx.x * 16;
   const int col0 = blockIdx.y * 64;
@@ -661,26 +660,22 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
   }
 }
 
-// Probe selection: one block of 128 threads per query selects the np
-// smallest (distance, list) keys of the query's centroid ranking.
+// Probe selection: the block selects the np smallest (distance, list) keys
+// of the query's centroid ranking into dst (ascending), writes the probe ids
+// and distances, and (warp 0) each probe's first survivor-mask word: the
+// running sum, in probe order, of the probed lists' 32-vector words over
+// the query's own nprobe. Returns the number of probes found.
 constexpr int kProbeStageKeys = 4096;
 
-__global__ void __launch_bounds__(128)
-probe_select_kernel(const uint64_t* __restrict__ pkeys, int nlist, int np, int64_t nq,
-                    int32_t* __restrict__ out_ids, float* __restrict__ out_d,
-                    const int64_t* __restrict__ offsets, const int32_t* __restrict__ nprobe,
-                    int32_t* __restrict__ wbase, int32_t* __restrict__ wtotal) {
-  extern __shared__ __align__(16) uint8_t smem[];
-  __shared__ int hist[256];
-  __shared__ uint64_t small[32];
-  __shared__ int ctl[8];
+__device__ inline int probe_select_block(const uint64_t* __restrict__ pkeys, int nlist, int np,
+                                         int64_t row, uint64_t* dst, uint64_t* stage,
+                                         int32_t* __restrict__ out_ids, float* __restrict__ out_d,
+                                         const int64_t* __restrict__ offsets, int npq,
+                                         int32_t* __restrict__ wbase, int32_t* __restrict__ wtotal,
+                                         int* hist, uint64_t* small, int* ctl) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t row = blockIdx.x;
-  const int P = next_pow2(np);
-  uint64_t* dst = reinterpret_cast<uint64_t*>(smem);
   const uint64_t* src = pkeys + row * nlist;
   if (nlist <= kProbeStageKeys) {
-    uint64_t* stage = dst + P;
 #pragma unroll 8
     for (int i = tid; i < nlist; i += blockDim.x) stage[i] = src[i];
     __syncthreads();
@@ -693,81 +688,56 @@ probe_select_kernel(const uint64_t* __restrict__ pkeys, int nlist, int np, int64
     out_d[row * np + j] =
         (k == kU64Max) ? __int_as_float(0x7f800000) : from_orderable((uint32_t)(k >> 32));
   }
-  if (wbase == nullptr || warp != 0) return;
-  // First survivor-mask word of each probe: running sum, in probe order, of
-  // the probed lists' 32-vector words (over the query's own nprobe).
-  if (wbase == nullptr) return;
-  const int npq = min(nprobe[row], got);
-  int carry = 0;
-  for (int j0 = 0; j0 < np; j0 += 32) {
-    const int j = j0 + lane;
-    int w = 0;
-    if (j < npq) {
-      const uint32_t l = (uint32_t)dst[j];
-      w = (int)((offsets[l + 1] - offsets[l] + 31) >> 5);
-    }
-    int incl = w;
+  if (warp == 0) {
+    const int nw = min(npq, got);
+    int carry = 0;
+    for (int j0 = 0; j0 < np; j0 += 32) {
+      const int j = j0 + lane;
+      int w = 0;
+      if (j < nw) {
+        const uint32_t l = (uint32_t)dst[j];
+        w = (int)((offsets[l + 1] - offsets[l] + 31) >> 5);
+      }
+      int incl = w;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      if (j < np) wbase[row * np + j] = carry + incl - w;
+      carry += __shfl_sync(0xffffffffu, incl, 31);
     }
-    if (j < np) wbase[row * np + j] = carry + incl - w;
-    carry += __shfl_sync(0xffffffffu, incl, 31);
+    if (lane == 0) wtotal[row] = carry;
   }
-  if (lane == 0) wtotal[row] = carry;
+  return got;
 }
 
-// First bound (Section 3.3.3), four warps per query: lists in probe order
-// give the first max(1024, n_sel) candidates, estimated by all 128 threads
-// (the list ranges of the first 32 probes read at once, each thread's codes
-// loaded before its estimates); the block then takes the n_sel-th smallest
-// orderable estimate (all ones when the query has fewer candidates).
+// First bound (Section 3.3.3): lists in probe order give the first
+// max(1024, n_sel) candidates, estimated by all 128 threads (each thread's
+// codes loaded before its estimates); the block takes the n_sel-th smallest
+// orderable estimate (all ones when the query has fewer candidates). `lists`
+// holds the query's probed list ids (npq of them), `s_bkeys` room for
+// max(1024, n_sel) values.
 template <int NW4>
-__global__ void __launch_bounds__(128, 8)
-bound_kernel(const int32_t* __restrict__ probe_ids, const int32_t* __restrict__ nprobe,
-             int npmax, const int32_t* __restrict__ nsel, const float4* __restrict__ qparams,
-             const uint32_t* __restrict__ planes, const int64_t* __restrict__ offsets,
-             const uint8_t* __restrict__ codes, const float2* __restrict__ fac, int dp,
-             uint32_t* __restrict__ bound, const int32_t* __restrict__ no_prune) {
+__device__ inline uint32_t bound_block(int64_t qi, int npmax, int npq, int n_sel,
+                                       const uint64_t* lists, const float4* __restrict__ qparams,
+                                       const uint32_t* __restrict__ planes,
+                                       const int64_t* __restrict__ offsets,
+                                       const uint8_t* __restrict__ codes,
+                                       const float2* __restrict__ fac, int dp, uint32_t* s_bkeys,
+                                       int* hist, uint64_t* small, int* ctl) {
   constexpr int W = 4 * NW4;
   constexpr int RB = NW4 >= 4 ? 1 : 4 / NW4;  // codes in flight per thread
-  extern __shared__ __align__(16) uint32_t s_bkeys[];
   __shared__ __align__(16) uint32_t s_pl[4 * W];
-  __shared__ int hist[256];
-  __shared__ uint64_t small[32];
-  __shared__ int ctl[8];
-  __shared__ int64_t s_lo[32];
-  __shared__ int64_t s_len[32];
   const int tid = threadIdx.x;
-  const int64_t qi = blockIdx.x;
-  const int n_sel = nsel[qi];
-  if (*no_prune || n_sel <= 0) {
-    if (tid == 0) bound[qi] = kU32Max;
-    return;
-  }
-  const int npq = nprobe[qi];
-  if (tid < 32 && tid < npq) {
-    const int c = probe_ids[qi * npmax + tid];
-    const int64_t lo = offsets[c];
-    s_lo[tid] = lo;
-    s_len[tid] = offsets[c + 1] - lo;
-  }
   const int cap1 = max(kBoundCandidates, n_sel);
   int taken = 0;
   for (int p = 0; p < npq && taken < cap1; ++p) {
     const int64_t pair = qi * npmax + p;
+    const uint32_t c = (uint32_t)lists[p];
+    const int64_t lo = offsets[c];
+    const int m = (int)min(offsets[c + 1] - lo, (int64_t)(cap1 - taken));
     __syncthreads();
-    int64_t lo, len;
-    if (p < 32) {
-      lo = s_lo[p];
-      len = s_len[p];
-    } else {
-      const int c = probe_ids[pair];
-      lo = offsets[c];
-      len = offsets[c + 1] - lo;
-    }
-    const int m = (int)min(len, (int64_t)(cap1 - taken));
     for (int i = tid; i < 4 * W; i += blockDim.x) s_pl[i] = planes[pair * 4 * W + i];
     __syncthreads();
     const float4 qp = qparams[pair];
@@ -800,9 +770,73 @@ bound_kernel(const int32_t* __restrict__ probe_ids, const int32_t* __restrict__ 
     taken += m;
   }
   __syncthreads();
+  return taken >= n_sel ? block_kth_u32(s_bkeys, taken, n_sel, hist, small, ctl) : kU32Max;
+}
+
+// Query preparation, one block of 128 threads per query: probe selection,
+// then the quantisation of each probed residual (a warp per probe), then the
+// first bound. Shared memory: the probe keys (next_pow2(np)), then a region
+// used first to stage the centroid ranking (nlist keys, when at most
+// kProbeStageKeys) and then for the bound's estimates.
+struct PrepArgs {
+  const uint64_t* pkeys;
+  int nlist, npmax;
+  int64_t nq;
+  const int32_t* nprobe;
+  const int32_t* nsel;
+  const int32_t* no_prune;
+  const int64_t* offsets;
+  const float* qrot;
+  const float* cR;
+  int dp;
+  int32_t* probe_ids;
+  float* probe_d;
+  int32_t* wbase;
+  int32_t* wtotal;
+  float4* qparams;
+  uint32_t* planes;
+  int32_t* list_count;
+  int32_t* list_pairs;
+  uint8_t* qdb;
+  float4* qpb;
+  const uint8_t* codes;
+  const float2* fac;
+  uint32_t* bound;
+  int32_t* err;
+};
+
+template <int NW4>
+__global__ void __launch_bounds__(128, NW4 >= 4 ? 4 : 8) prep_kernel(PrepArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ int hist[256];
+  __shared__ uint64_t small[32];
+  __shared__ int ctl[8];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t row = blockIdx.x;
+  const int P = next_pow2(a.npmax);
+  uint64_t* dst = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* region = dst + P;
+  const int npq = min(a.nprobe[row], a.npmax);
+  const int got = probe_select_block(a.pkeys, a.nlist, a.npmax, row, dst, region, a.probe_ids,
+                                     a.probe_d, a.offsets, npq, a.wbase, a.wtotal, hist, small,
+                                     ctl);
+  if (got < npq) {
+    if (tid == 0) flag_error(a.err, kErrBadProbe);
+    return;
+  }
+  for (int p = warp; p < npq; p += 4)
+    quantize_pair<NW4>(row * a.npmax + p, row, (int)(uint32_t)dst[p], lane, a.qrot, a.nq, a.cR,
+                       a.dp, a.qparams, a.planes, a.list_count, a.list_pairs, a.qdb, a.qpb);
+  // The block's own writes of planes and parameters are visible to it
+  // after the barrier.
+  __syncthreads();
+  const int n_sel = a.nsel[row];
   uint32_t tau = kU32Max;
-  if (taken >= n_sel) tau = block_kth_u32(s_bkeys, taken, n_sel, hist, small, ctl);
-  if (tid == 0) bound[qi] = tau;
+  if (!*a.no_prune && n_sel > 0)
+    tau = bound_block<NW4>(row, a.npmax, npq, n_sel, dst, a.qparams, a.planes, a.offsets,
+                           a.codes, a.fac, a.dp, reinterpret_cast<uint32_t*>(region), hist,
+                           small, ctl);
+  if (tid == 0) a.bound[row] = tau;
 }
 
 // ---------------------------------------------------------------------------
@@ -909,21 +943,49 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
   const int np = sh.npmax;
   const int dp = ix->dp;
   const int64_t pairs = nq * np;
+  // probe selection, quantisation and first bound: one fused kernel
   tm.mark(RQ_STAGE_QUANTIZE, st);
   const bool grouped = sh.mode != RQ_SCAN_PLAIN;
-  if (grouped) RQ_CUDA(cudaMemsetAsync(ws.list_count, 0, sizeof(int32_t) * ix->nlist, st));
-  quantize_kernel<NW4><<<blocks_for(pairs * 32, 256), 256, 0, st>>>(
-      ws.qrot, ws.probe_ids, ws.nprobe, np, nq, ix->cR, dp, ws.qparams, ws.planes,
-      grouped ? ws.list_count : nullptr, ws.list_pairs,
-      sh.mode == RQ_SCAN_MMA ? ws.qdig : nullptr, sh.mode == RQ_SCAN_MMA ? ws.qpb : nullptr,
-      ix->d_err);
-  tm.mark(RQ_STAGE_BOUND, st);
   {
+    PrepArgs a;
+    a.pkeys = ws.pkeys;
+    a.nlist = ix->nlist;
+    a.npmax = np;
+    a.nq = nq;
+    a.nprobe = ws.nprobe;
+    a.nsel = ws.nsel;
+    a.no_prune = ws.rerank_on + nq;
+    a.offsets = ix->offsets;
+    a.qrot = ws.qrot;
+    a.cR = ix->cR;
+    a.dp = dp;
+    a.probe_ids = ws.probe_ids;
+    a.probe_d = ws.probe_d;
+    a.wbase = ws.wbase;
+    a.wtotal = ws.wtotal;
+    a.qparams = ws.qparams;
+    a.planes = ws.planes;
+    a.list_count = grouped ? ws.list_count : nullptr;
+    a.list_pairs = ws.list_pairs;
+    a.qdb = sh.mode == RQ_SCAN_MMA ? ws.qdig : nullptr;
+    a.qpb = sh.mode == RQ_SCAN_MMA ? ws.qpb : nullptr;
+    a.codes = ix->codes;
+    a.fac = ix->fac;
+    a.bound = ws.bound;
+    a.err = ix->d_err;
+    const int stage = ix->nlist <= kProbeStageKeys ? ix->nlist : 0;
     const int kpw = std::max(kBoundCandidates, sh.nsel_max);
-    bound_kernel<NW4><<<(unsigned)nq, 128, (size_t)kpw * 4, st>>>(
-        ws.probe_ids, ws.nprobe, np, ws.nsel, ws.qparams, ws.planes, ix->offsets, ix->codes,
-        ix->fac, dp, ws.bound, ws.rerank_on + nq);
+    const size_t smem =
+        (size_t)next_pow2_host(np) * 8 + std::max<size_t>((size_t)stage * 8, (size_t)kpw * 4);
+    static bool attr = false;
+    if (!attr) {
+      RQ_CUDA(cudaFuncSetAttribute(prep_kernel<NW4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   200 * 1024));
+      attr = true;
+    }
+    prep_kernel<NW4><<<(unsigned)nq, 128, smem, st>>>(a);
   }
+  tm.mark(RQ_STAGE_BOUND, st);
   tm.mark(RQ_STAGE_WORKLIST, st);
   if (sh.mode == RQ_SCAN_PLAIN) {
     tm.mark(RQ_STAGE_SCAN, st);
@@ -931,7 +993,6 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
         ws.probe_ids, ws.nprobe, np, ws.qparams, ws.planes, ix->offsets, ix->codes, ix->fac,
         ix->ids, dp, ws.bound, ws.wbase, ws.mwords, ws.mask, ws.cand);
   } else {
-    RQ_CUDA(cudaMemsetAsync(ws.work_count, 0, sizeof(int32_t) * 4, st));
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
     tm.mark(RQ_STAGE_SCAN, st);
@@ -950,30 +1011,18 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
 rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cudaStream_t st,
                          StageTimer& tm) {
   const int64_t nq = sh.nq;
-  const int np = sh.npmax;
   const int dp = ix->dp;
   // 1. rotation, once per query
   tm.mark(RQ_STAGE_ROTATE, st);
-  rotate16_kernel<<<dim3(blocks_for(nq, 16), dp / 64), 256, 0, st>>>(ws.q, nq, ix->dim, ix->P32,
-                                                                    dp, ws.qrot);
-  // 2. centroid ranking and probe selection
+  const bool grouped = sh.mode != RQ_SCAN_PLAIN;
+  rotate16_kernel<<<dim3(blocks_for(nq, 16), dp / 64), 256, 0, st>>>(
+      ws.q, nq, ix->dim, ix->P32, dp, ws.qrot, grouped ? ws.list_count : nullptr,
+      grouped ? ix->nlist : 0, grouped ? ws.work_count : nullptr, grouped ? 4 : 0);
+  // 2. centroid ranking
   tm.mark(RQ_STAGE_PROBE, st);
   pair_dist_kernel<1, 2><<<dim3(blocks_for(nq, 32), blocks_for(ix->nlist, 64)), 256, 0, st>>>(
       ws.qrot, nq, ix->cR, ix->nlist, dp, nullptr, nullptr, ws.pkeys);
-  {
-    const int stage = ix->nlist <= kProbeStageKeys ? ix->nlist : 0;
-    const size_t smem = (size_t)(next_pow2_host(np) + stage) * 8;
-    static bool attr = false;
-    if (!attr) {
-      RQ_CUDA(cudaFuncSetAttribute(probe_select_kernel,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      attr = true;
-    }
-    probe_select_kernel<<<(unsigned)nq, 128, smem, st>>>(ws.pkeys, ix->nlist, np, nq,
-                                                        ws.probe_ids, ws.probe_d, ix->offsets,
-                                                        ws.nprobe, ws.wbase, ws.wtotal);
-  }
-  // 3-4. quantisation, bound, scan
+  // 3-4. probe selection, quantisation, bound, scan
   switch (dp / 128) {
     case 1: RQ_TRY(enqueue_scan_stages<1>(ix, sh, ws, st, tm)); break;
     case 2: RQ_TRY(enqueue_scan_stages<2>(ix, sh, ws, st, tm)); break;
