@@ -399,7 +399,9 @@ def run_ours(args, rank, world, local, pg):
     serving = None
     if not args.no_serving:
         serving = run_serving(rq, ix, q, nprobe, k, nrr, offered=0.5 * value / max(world, 1))
-    launches_per_step = 11 if stages.get("worklist", 0.0) > 0 else 7
+    # this library's kernels per search: rotate, centroid distances, probe
+    # selection, quantise, bound, scan, select + re-rank (memsets not counted)
+    launches_per_step = 7
     ms_per_step = 1e3 * t_dev / args.steps
     res = {
         "metric": METRIC,
