@@ -60,7 +60,9 @@ struct Workspace {
   size_t bytes = 0;
   float* q = nullptr;           // nq x dim (input copy)
   float* qrot = nullptr;        // nq x D_p
-  uint64_t* pkeys = nullptr;    // nq x nlist probe keys
+  uint64_t* pkeys = nullptr;    // nq x nlist exact probe keys, or (nlist <= 4096)
+                                // nq x nlist approximate distances (float)
+  float* cn = nullptr;          // nlist: ||P^T c||^2 (certified probe selection)
   int32_t* probe_ids = nullptr; // nq x npmax
   float* probe_d = nullptr;     // nq x npmax
   float4* qparams = nullptr;    // nq x npmax: vl, delta, nq2, Sq(bits of int)

@@ -373,49 +373,176 @@ scan_grouped_kernel(const int2* __restrict__ items, int n_items, int32_t* __rest
 }
 
 // ---------------------------------------------------------------------------
-// Rotation with more blocks: 16 queries x 64 output columns per block, K in
-// chunks of 128 staged in shared memory. The first column of blocks also
-// clears the search's counters (zero0[n0], zero1[n1]) for the later stages.
+// Rotation q' = P^T q (float32 FMA): 8 queries x 64 output columns per
+// block, K in chunks of 128 staged in shared memory with every load of a
+// chunk in flight at once (16-byte loads when the rows allow). The first
+// column of blocks also clears the search's counters (zero0[n0], zero1[n1])
+// for the later stages.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
-rotate16_kernel(const float* __restrict__ q, int64_t nq, int dim, const float* __restrict__ P32,
-                int dp, float* __restrict__ qrot, int32_t* __restrict__ zero0, int n0,
-                int32_t* __restrict__ zero1, int n1) {
-  __shared__ float As[16][129];
-  __shared__ float Bs[128][64];
+rotate_kernel8(const float* __restrict__ q, int64_t nq, int dim, const float* __restrict__ P32,
+               int dp, float* __restrict__ qrot, int32_t* __restrict__ zero0, int n0,
+               int32_t* __restrict__ zero1, int n1) {
+  __shared__ __align__(16) float As[8][132];
+  __shared__ __align__(16) float Bs[128][64];
+  const int tid = threadIdx.x;
   if (blockIdx.y == 0) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n0; i += gridDim.x * blockDim.x)
-      zero0[i] = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += gridDim.x * blockDim.x)
-      zero1[i] = 0;
+    for (int i = blockIdx.x * blockDim.x + tid; i < n0; i += gridDim.x * blockDim.x) zero0[i] = 0;
+    for (int i = blockIdx.x * blockDim.x + tid; i < n1; i += gridDim.x * blockDim.x) zero1[i] = 0;
   }
-  const int r = threadIdx.x >> 4, cg = threadIdx.x & 15;
-  const int64_t r0 = (int64_t)blockIdx.x * 16;
+  const int r = tid >> 5, cg = tid & 31;
+  const int64_t r0 = (int64_t)blockIdx.x * 8;
   const int col0 = blockIdx.y * 64;
-  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  const bool vec = (dim & 3) == 0;
+  float acc[2] = {0.0f, 0.0f};
   for (int k0 = 0; k0 < dim; k0 += 128) {
-    for (int t = threadIdx.x; t < 16 * 128; t += 256) {
-      const int rr = t >> 7, kk = t & 127;
+    // A: 8 rows x 128 (one float4 per thread); B: 128 x 64 (eight float4)
+    {
+      const int rr = tid >> 5, kk = (tid & 31) * 4;
       const int64_t row = r0 + rr;
-      As[rr][kk] = (row < nq && k0 + kk < dim) ? q[row * dim + k0 + kk] : 0.0f;
+      float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (row < nq) {
+        if (vec && k0 + kk + 3 < dim) {
+          v = __ldg(reinterpret_cast<const float4*>(q + row * dim + k0 + kk));
+        } else {
+          const float* src = q + row * dim + k0 + kk;
+          v.x = (k0 + kk + 0 < dim) ? src[0] : 0.0f;
+          v.y = (k0 + kk + 1 < dim) ? src[1] : 0.0f;
+          v.z = (k0 + kk + 2 < dim) ? src[2] : 0.0f;
+          v.w = (k0 + kk + 3 < dim) ? src[3] : 0.0f;
+        }
+      }
+      *reinterpret_cast<float4*>(&As[rr][kk]) = v;
     }
-    for (int t = threadIdx.x; t < 128 * 64; t += 256) {
-      const int kk = t >> 6, c = t & 63;
-      Bs[kk][c] = (k0 + kk < dim) ? P32[(int64_t)(k0 + kk) * dp + col0 + c] : 0.0f;
+    float4 bv[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int e = tid + 256 * t, kk = e >> 4, c4 = (e & 15) * 4;
+      bv[t] = (k0 + kk < dim)
+                  ? __ldg(reinterpret_cast<const float4*>(P32 + (int64_t)(k0 + kk) * dp + col0 + c4))
+                  : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int e = tid + 256 * t, kk = e >> 4, c4 = (e & 15) * 4;
+      *reinterpret_cast<float4*>(&Bs[kk][c4]) = bv[t];
     }
     __syncthreads();
 #pragma unroll 8
     for (int kk = 0; kk < 128; ++kk) {
-      const float a = As[r][kk];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[j] = fmaf(a, Bs[kk][cg + 16 * j], acc[j]);
+      const float av = As[r][kk];
+      acc[0] = fmaf(av, Bs[kk][cg], acc[0]);
+      acc[1] = fmaf(av, Bs[kk][cg + 32], acc[1]);
     }
     __syncthreads();
   }
   const int64_t row = r0 + r;
   if (row < nq) {
+    qrot[row * dp + col0 + cg] = acc[0];
+    qrot[row * dp + col0 + cg + 32] = acc[1];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Approximate centroid ranking, the filter of the certified probe selection:
+// g[i][j] = ||c_j||^2 - 2 <q'_i, c_j> in float32 with fused multiply-adds,
+// 64 x 64 tiles per block (4 x 4 per thread). All of K (D_p <= 128 here)
+// is loaded into shared memory at once, every load in flight together;
+// blocks of the first row also write cn[j] = ||c_j||^2. Its error is
+// bounded where it is used (probe_select_certified).
+// ---------------------------------------------------------------------------
+constexpr int kApproxMaxDp = 128;
+constexpr int kApproxLd = 68;  // row stride (floats) of the k-major tiles
+
+__global__ void __launch_bounds__(256)
+approx_dist_kernel(const float* __restrict__ A, int64_t na, const float* __restrict__ B, int nb,
+                   int dp, float* __restrict__ g, float* __restrict__ cn) {
+  extern __shared__ __align__(16) float sm_f[];
+  float* As = sm_f;                         // [dp][kApproxLd], k-major
+  float* Bs = sm_f + dp * kApproxLd;        // [dp][kApproxLd]
+  __shared__ float s_cn[4][64];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int lane = tid & 31, w = tid >> 5;
+  const int64_t row0 = (int64_t)blockIdx.x * 64;
+  const int col0 = blockIdx.y * 64;
+  // rows lane and lane + 32 of each tile; warp w takes dimensions 4 (w + 8 t)
+  const int nk4 = dp / 32;
+  for (int h = 0; h < 2; ++h) {
+    const int r = lane + 32 * h;
+    float4 va[kApproxMaxDp / 32], vb[kApproxMaxDp / 32];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) qrot[row * dp + col0 + cg + 16 * j] = acc[j];
+    for (int t = 0; t < kApproxMaxDp / 32; ++t) {
+      va[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      vb[t] = va[t];
+      if (t < nk4) {
+        const int k = 4 * (w + 8 * t);
+        if (row0 + r < na) va[t] = __ldg(reinterpret_cast<const float4*>(A + (row0 + r) * dp + k));
+        if (col0 + r < nb)
+          vb[t] = __ldg(reinterpret_cast<const float4*>(B + (int64_t)(col0 + r) * dp + k));
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kApproxMaxDp / 32; ++t) {
+      if (t < nk4) {
+        const int k = 4 * (w + 8 * t);
+        As[(k + 0) * kApproxLd + r] = va[t].x;
+        As[(k + 1) * kApproxLd + r] = va[t].y;
+        As[(k + 2) * kApproxLd + r] = va[t].z;
+        As[(k + 3) * kApproxLd + r] = va[t].w;
+        Bs[(k + 0) * kApproxLd + r] = vb[t].x;
+        Bs[(k + 1) * kApproxLd + r] = vb[t].y;
+        Bs[(k + 2) * kApproxLd + r] = vb[t].z;
+        Bs[(k + 3) * kApproxLd + r] = vb[t].w;
+      }
+    }
+  }
+  __syncthreads();
+  // ||c||^2 of the block's 64 columns: four threads per column, a quarter of
+  // the dimensions each
+  {
+    const int j = tid & 63, qd = tid >> 6, len = dp / 4;
+    float acc = 0.0f;
+    for (int k = qd * len; k < (qd + 1) * len; ++k)
+      acc = fmaf(Bs[k * kApproxLd + j], Bs[k * kApproxLd + j], acc);
+    s_cn[qd][j] = acc;
+  }
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+#pragma unroll 8
+  for (int k = 0; k < dp; ++k) {
+    const float4 av = *reinterpret_cast<const float4*>(&As[k * kApproxLd + 4 * ty]);
+    const float4 bv = *reinterpret_cast<const float4*>(&Bs[k * kApproxLd + 4 * tx]);
+    const float ar[4] = {av.x, av.y, av.z, av.w};
+    const float br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+  }
+  __syncthreads();
+  float cnv[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c = 4 * tx + j;
+    cnv[j] = (s_cn[0][c] + s_cn[1][c]) + (s_cn[2][c] + s_cn[3][c]);
+  }
+  if (blockIdx.x == 0 && ty == 0) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (col0 + 4 * tx + j < nb) cn[col0 + 4 * tx + j] = cnv[j];
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t r = row0 + 4 * ty + i;
+    if (r >= na) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = col0 + 4 * tx + j;
+      if (c < nb) g[r * nb + c] = fmaf(-2.0f, acc[i][j], cnv[j]);
+    }
   }
 }
 
@@ -660,28 +787,118 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
   }
 }
 
-// Probe selection: the block selects the np smallest (distance, list) keys
-// of the query's centroid ranking into dst (ascending), writes the probe ids
-// and distances, and (warp 0) each probe's first survivor-mask word: the
-// running sum, in probe order, of the probed lists' 32-vector words over
-// the query's own nprobe. Returns the number of probes found.
+// Probe selection. Both forms leave the query's np smallest (distance, list)
+// keys in dst, ascending, and return how many were found; the distance is
+// always the fixed-order float32 one (the terms (q'_d - c_d)^2 added in
+// increasing d, no fused multiply-add).
 constexpr int kProbeStageKeys = 4096;
+constexpr int kProbeCandCap = 256;
 
-__device__ inline int probe_select_block(const uint64_t* __restrict__ pkeys, int nlist, int np,
-                                         int64_t row, uint64_t* dst, uint64_t* stage,
-                                         int32_t* __restrict__ out_ids, float* __restrict__ out_d,
-                                         const int64_t* __restrict__ offsets, int npq,
-                                         int32_t* __restrict__ wbase, int32_t* __restrict__ wtotal,
-                                         int* hist, uint64_t* small, int* ctl) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+// Exact form: select from the full exact ranking (pkeys, nlist keys per
+// query), staged in shared memory when it fits.
+__device__ inline int probe_select_exact(const uint64_t* __restrict__ pkeys, int nlist, int np,
+                                         int64_t row, uint64_t* dst, uint64_t* stage, int* hist,
+                                         uint64_t* small, int* ctl) {
   const uint64_t* src = pkeys + row * nlist;
   if (nlist <= kProbeStageKeys) {
 #pragma unroll 8
-    for (int i = tid; i < nlist; i += blockDim.x) stage[i] = src[i];
+    for (int i = threadIdx.x; i < nlist; i += blockDim.x) stage[i] = src[i];
     __syncthreads();
     src = stage;
   }
-  const int got = block_select_smallest(src, nlist, np, dst, hist, small, ctl, true);
+  return block_select_smallest(src, nlist, np, dst, hist, small, ctl, true);
+}
+
+// The fixed-order squared distance of the query (shared memory) to one
+// centroid row.
+__device__ __forceinline__ float seq_sqdist(const float* qs, const float* __restrict__ c, int dp) {
+  float acc = 0.0f;
+  const float4* c4 = reinterpret_cast<const float4*>(c);
+  for (int d = 0; d < dp; d += 4) {
+    const float4 v = __ldg(c4 + (d >> 2));
+    float df = __fsub_rn(qs[d], v.x);
+    acc = __fadd_rn(acc, __fmul_rn(df, df));
+    df = __fsub_rn(qs[d + 1], v.y);
+    acc = __fadd_rn(acc, __fmul_rn(df, df));
+    df = __fsub_rn(qs[d + 2], v.z);
+    acc = __fadd_rn(acc, __fmul_rn(df, df));
+    df = __fsub_rn(qs[d + 3], v.w);
+    acc = __fadd_rn(acc, __fmul_rn(df, df));
+  }
+  return acc;
+}
+
+// Certified form, for nlist <= kProbeStageKeys. From the approximate
+// ranking g = ||c||^2 - 2 <q', c> (approx_dist_kernel) and ||q'||^2, each
+// centroid's approximate distance a = ||q'||^2 + g has |a - exact| <= e with
+// e = 16 D_p 2^-24 (||q'||^2 + ||c||^2): both the float32 sums of D_p terms
+// behind a and the fixed-order exact distance are within (D_p 2^-24 +
+// O(2^-48)) relative of their terms' magnitudes, which sum to at most
+// ||q'||^2 + ||c||^2 -- a factor of more than 3 to spare. U = the np-th
+// smallest a + e bounds the np-th smallest exact distance from above, so a
+// centroid with a - e > U is not among the np nearest (not even on a tie);
+// the others (a few dozen) get the exact distance and the exact selection.
+// If more than kProbeCandCap remain, every centroid gets the exact distance.
+// Shared memory: `region` holds nlist keys + kProbeCandCap ints + D_p floats.
+__device__ inline int probe_select_certified(const float* __restrict__ g,
+                                             const float* __restrict__ cn,
+                                             const float* __restrict__ qrot,
+                                             const float* __restrict__ cR, int nlist, int np,
+                                             int dp, int64_t row, uint64_t* dst, uint64_t* region,
+                                             int* hist, uint64_t* small, int* ctl) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t* ub = reinterpret_cast<uint32_t*>(region);  // nlist upper-bound keys
+  uint64_t* keys = region;                            // later: exact keys (reuses ub)
+  int* cand = reinterpret_cast<int*>(region + nlist);
+  float* qs = reinterpret_cast<float*>(cand + kProbeCandCap);
+  __shared__ float s_red[4];
+  float part = 0.0f;
+  for (int d = tid; d < dp; d += blockDim.x) {
+    const float v = qrot[row * dp + d];
+    qs[d] = v;
+    part = fmaf(v, v, part);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if (lane == 0) s_red[warp] = part;
+  __syncthreads();
+  const float qn = s_red[0] + s_red[1] + s_red[2] + s_red[3];
+  const float escale = 16.0f * (float)dp * 5.9604645e-8f;
+  const float* grow = g + row * nlist;
+  for (int c = tid; c < nlist; c += blockDim.x) {
+    const float av = qn + grow[c];
+    ub[c] = orderable(av + escale * (qn + cn[c]));
+  }
+  if (tid == 0) ctl[6] = 0;
+  __syncthreads();
+  const uint32_t U = block_kth_u32(ub, nlist, min(np, nlist), hist, small, ctl);
+  for (int c = tid; c < nlist; c += blockDim.x) {
+    const float av = qn + grow[c];
+    if (orderable(av - escale * (qn + cn[c])) <= U) {
+      const int at = atomicAdd(&ctl[6], 1);
+      if (at < kProbeCandCap) cand[at] = c;
+    }
+  }
+  __syncthreads();
+  const int nc = ctl[6];
+  const bool all = nc > kProbeCandCap;
+  const int m = all ? nlist : nc;
+  for (int i = tid; i < m; i += blockDim.x) {
+    const int c = all ? i : cand[i];
+    keys[i] = make_key(seq_sqdist(qs, cR + (int64_t)c * dp, dp), (uint32_t)c);
+  }
+  __syncthreads();
+  return block_select_smallest(keys, m, np, dst, hist, small, ctl, true);
+}
+
+// Writes the selected probes (ids, distances) and, in warp 0, each probe's
+// first survivor-mask word: the running sum, in probe order, of the probed
+// lists' 32-vector words over the query's own nprobe.
+__device__ inline void probe_outputs(const uint64_t* dst, int got, int np, int64_t row,
+                                     int32_t* __restrict__ out_ids, float* __restrict__ out_d,
+                                     const int64_t* __restrict__ offsets, int npq,
+                                     int32_t* __restrict__ wbase, int32_t* __restrict__ wtotal) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int j = tid; j < np; j += blockDim.x) {
     const uint64_t k = (j < got) ? dst[j] : kU64Max;
     out_ids[row * np + j] = (k == kU64Max) ? -1 : (int32_t)(uint32_t)k;
@@ -709,7 +926,6 @@ __device__ inline int probe_select_block(const uint64_t* __restrict__ pkeys, int
     }
     if (lane == 0) wtotal[row] = carry;
   }
-  return got;
 }
 
 // First bound (Section 3.3.3): lists in probe order give the first
@@ -776,10 +992,12 @@ __device__ inline uint32_t bound_block(int64_t qi, int npmax, int npq, int n_sel
 // Query preparation, one block of 128 threads per query: probe selection,
 // then the quantisation of each probed residual (a warp per probe), then the
 // first bound. Shared memory: the probe keys (next_pow2(np)), then a region
-// used first to stage the centroid ranking (nlist keys, when at most
-// kProbeStageKeys) and then for the bound's estimates.
+// used first by the probe selection (nlist keys, plus the certified form's
+// candidates and query row) and then for the bound's estimates.
 struct PrepArgs {
-  const uint64_t* pkeys;
+  const uint64_t* pkeys;  // exact ranking (nlist > kProbeStageKeys), else null
+  const float* g;         // approximate ranking (nlist <= kProbeStageKeys), else null
+  const float* cn;        // ||c||^2 per centroid (with g)
   int nlist, npmax;
   int64_t nq;
   const int32_t* nprobe;
@@ -817,9 +1035,12 @@ __global__ void __launch_bounds__(128, NW4 >= 4 ? 4 : 8) prep_kernel(PrepArgs a)
   uint64_t* dst = reinterpret_cast<uint64_t*>(smem);
   uint64_t* region = dst + P;
   const int npq = min(a.nprobe[row], a.npmax);
-  const int got = probe_select_block(a.pkeys, a.nlist, a.npmax, row, dst, region, a.probe_ids,
-                                     a.probe_d, a.offsets, npq, a.wbase, a.wtotal, hist, small,
-                                     ctl);
+  const int got =
+      a.g ? probe_select_certified(a.g, a.cn, a.qrot, a.cR, a.nlist, a.npmax, a.dp, row, dst,
+                                   region, hist, small, ctl)
+          : probe_select_exact(a.pkeys, a.nlist, a.npmax, row, dst, region, hist, small, ctl);
+  probe_outputs(dst, got, a.npmax, row, a.probe_ids, a.probe_d, a.offsets, npq, a.wbase,
+                a.wtotal);
   if (got < npq) {
     if (tid == 0) flag_error(a.err, kErrBadProbe);
     return;
@@ -869,6 +1090,7 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
   L.take(&ws.q, nq * ix->dim);
   L.take(&ws.qrot, nq * ix->dp);
   L.take(&ws.pkeys, nq * ix->nlist);
+  L.take(&ws.cn, ix->nlist);
   L.take(&ws.probe_ids, nq * np);
   L.take(&ws.probe_d, nq * np);
   L.take(&ws.qparams, nq * np);
@@ -907,6 +1129,7 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
   rebase(ws.q, b);
   rebase(ws.qrot, b);
   rebase(ws.pkeys, b);
+  rebase(ws.cn, b);
   rebase(ws.probe_ids, b);
   rebase(ws.probe_d, b);
   rebase(ws.qparams, b);
@@ -936,6 +1159,13 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
   return RQ_OK;
 }
 
+// The certified probe selection (approximate ranking + exact refinement)
+// serves lists up to kProbeStageKeys and D_p up to kApproxMaxDp; otherwise
+// every centroid distance is computed exactly.
+bool certified_probe(const rq_index* ix) {
+  return ix->nlist <= kProbeStageKeys && ix->dp <= kApproxMaxDp;
+}
+
 template <int NW4>
 rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws,
                               cudaStream_t st, StageTimer& tm) {
@@ -948,7 +1178,10 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
   const bool grouped = sh.mode != RQ_SCAN_PLAIN;
   {
     PrepArgs a;
-    a.pkeys = ws.pkeys;
+    const bool certified = certified_probe(ix);
+    a.pkeys = certified ? nullptr : ws.pkeys;
+    a.g = certified ? reinterpret_cast<const float*>(ws.pkeys) : nullptr;
+    a.cn = ws.cn;
     a.nlist = ix->nlist;
     a.npmax = np;
     a.nq = nq;
@@ -973,10 +1206,10 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
     a.fac = ix->fac;
     a.bound = ws.bound;
     a.err = ix->d_err;
-    const int stage = ix->nlist <= kProbeStageKeys ? ix->nlist : 0;
+    const size_t stage = certified ? (size_t)ix->nlist * 8 + kProbeCandCap * 4 + (size_t)dp * 4
+                                   : 0;
     const int kpw = std::max(kBoundCandidates, sh.nsel_max);
-    const size_t smem =
-        (size_t)next_pow2_host(np) * 8 + std::max<size_t>((size_t)stage * 8, (size_t)kpw * 4);
+    const size_t smem = (size_t)next_pow2_host(np) * 8 + std::max<size_t>(stage, (size_t)kpw * 4);
     static bool attr = false;
     if (!attr) {
       RQ_CUDA(cudaFuncSetAttribute(prep_kernel<NW4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1015,13 +1248,26 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
   // 1. rotation, once per query
   tm.mark(RQ_STAGE_ROTATE, st);
   const bool grouped = sh.mode != RQ_SCAN_PLAIN;
-  rotate16_kernel<<<dim3(blocks_for(nq, 16), dp / 64), 256, 0, st>>>(
+  rotate_kernel8<<<dim3(blocks_for(nq, 8), dp / 64), 256, 0, st>>>(
       ws.q, nq, ix->dim, ix->P32, dp, ws.qrot, grouped ? ws.list_count : nullptr,
       grouped ? ix->nlist : 0, grouped ? ws.work_count : nullptr, grouped ? 4 : 0);
-  // 2. centroid ranking
+  // 2. centroid ranking: approximate (filter of the certified selection)
+  // where certified_probe holds, else exact
   tm.mark(RQ_STAGE_PROBE, st);
-  pair_dist_kernel<1, 2><<<dim3(blocks_for(nq, 32), blocks_for(ix->nlist, 64)), 256, 0, st>>>(
-      ws.qrot, nq, ix->cR, ix->nlist, dp, nullptr, nullptr, ws.pkeys);
+  if (certified_probe(ix)) {
+    const size_t smem = (size_t)2 * dp * kApproxLd * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+      RQ_CUDA(cudaFuncSetAttribute(approx_dist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(2 * kApproxMaxDp * kApproxLd * sizeof(float))));
+      attr = true;
+    }
+    approx_dist_kernel<<<dim3(blocks_for(nq, 64), blocks_for(ix->nlist, 64)), 256, smem, st>>>(
+        ws.qrot, nq, ix->cR, ix->nlist, dp, reinterpret_cast<float*>(ws.pkeys), ws.cn);
+  } else {
+    pair_dist_kernel<1, 2><<<dim3(blocks_for(nq, 32), blocks_for(ix->nlist, 64)), 256, 0, st>>>(
+        ws.qrot, nq, ix->cR, ix->nlist, dp, nullptr, nullptr, ws.pkeys);
+  }
   // 3-4. probe selection, quantisation, bound, scan
   switch (dp / 128) {
     case 1: RQ_TRY(enqueue_scan_stages<1>(ix, sh, ws, st, tm)); break;

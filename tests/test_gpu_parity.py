@@ -125,6 +125,36 @@ def test_search_stages_replay_bit_exact(tiny, mode, prune):
     assert np.abs(dump["qrot"] - qr).max() <= 1e-5 * np.abs(qr).max()
 
 
+def test_probe_ties_between_duplicate_centroids(rq):
+    """Centroids repeated exactly: equal centroid distances, so the probe
+    order rests on the list id, through the approximate filter and the exact
+    selection of the nearest lists."""
+    x = W.mixture("tiny").base(3000)
+    c = R.kmeans(x, 24, 3, seed=7)
+    c = np.concatenate([c, c[:8], c[:8]]).astype(np.float32)   # 40 lists, 16 duplicates
+    P = R.random_orthogonal(11, 128)
+    ix = rq.rq_build_with(x, c, P)
+    h = host_index(ix)
+    q = W.mixture("tiny").queries(32)
+    q[:4] = c[:4]                                              # queries on a centroid
+    for mode in (1, 3):
+        dump = search_dump(ix, q, 12, 10, 60, scan_mode=mode)
+        replay_and_compare(h, q, dump)
+
+
+def test_probe_exact_ranking_path_for_large_nlist(rq):
+    """nlist above 4096: the probe selection ranks all centroids exactly
+    instead of filtering an approximate ranking; replayed bit for bit."""
+    mix = W.mixture("tiny")
+    x = mix.base(30000)
+    q = mix.queries(12)
+    ix = rq.rq_build(x, 4500, seed=1, kmeans_iters=2)
+    h = host_index(ix)
+    for mode in (1, 3):
+        dump = search_dump(ix, q, 8, 10, 50, scan_mode=mode)
+        replay_and_compare(h, q, dump)
+
+
 @pytest.mark.parametrize("mode", [1, 2, 3])
 def test_many_candidates_replay_bit_exact(tiny, mode):
     """No pruning and half of the lists probed: more candidates per query
