@@ -600,6 +600,24 @@ __device__ __forceinline__ float exact_dist_lanes(const RawT* __restrict__ x,
       }
     }
   } else if (sizeof(RawT) == 1 && (dim & 15) == 0) {
+    // bytes: 128 dimensions (eight 16-byte loads, all in flight) per step
+    for (; d0 + 128 <= dim; d0 += 128) {
+      const uint4* x16 = reinterpret_cast<const uint4*>(x + d0);
+      uint4 t[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) t[j] = __ldg(x16 + j);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t w[4] = {t[j].x, t[j].y, t[j].z, t[j].w};
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+          const int l = (16 * j + b) & 31;
+          const float v = (float)((w[b >> 2] >> (8 * (b & 3))) & 255u);
+          const float df = __fsub_rn(v, qs[d0 + 16 * j + b]);
+          acc[l] = __fadd_rn(acc[l], __fmul_rn(df, df));
+        }
+      }
+    }
     for (; d0 + 32 <= dim; d0 += 32) {
       const uint4* x16 = reinterpret_cast<const uint4*>(x + d0);
 #pragma unroll
