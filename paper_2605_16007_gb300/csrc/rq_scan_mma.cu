@@ -312,6 +312,7 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
                 const int32_t* __restrict__ wbase, int64_t mwords, uint32_t* __restrict__ mask,
                 uint64_t* __restrict__ cand, int32_t* err) {
   extern __shared__ uint8_t smem_raw[];
+  __shared__ volatile int s_ok[4];  // results of the polled waits
   const uint32_t raw_addr = smem_u32(smem_raw);
   uint8_t* sm = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
   const uint32_t sbase = smem_u32(sm);
@@ -344,7 +345,11 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
       const int st = i & 1;
       const uint32_t full = sbase + kSmBar + 8 * st;
       const uint32_t empty = sbase + kSmBar + 16 + 8 * st;
-      if (!mbar_wait_bounded(full, (uint32_t)((i >> 1) & 1))) abort = true;
+      // One thread polls each mbarrier; the others wait at the named
+      // barrier, which orders the observed data for them, without issuing.
+      if (tid == 0) s_ok[0] = mbar_wait_bounded(full, (uint32_t)((i >> 1) & 1)) ? 1 : 0;
+      named_bar_consumers();
+      if (!s_ok[0]) abort = true;
       const Meta m = meta[st];
       if (abort || m.l < 0) break;
       const uint8_t* code_s = sm + kSmCode + st * kItemV * 16;
@@ -378,9 +383,10 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
             s_wrow[g] = (int64_t)q * mwords + wbase[pair];
             s_tau[g] = bound[q];
           }
-          const bool ok2 = mbar_wait_bounded(bar_aux, ph_aux);
+          if (tid == 0) s_ok[2] = mbar_wait_bounded(bar_aux, ph_aux) ? 1 : 0;
           ph_aux ^= 1u;
-          if (!ok2) abort = true;
+          named_bar_consumers();
+          if (!s_ok[2]) abort = true;
         }
         // A tiles: thread t expands vector t of the item (tile t / 128, row
         // t % 128); they are unchanged across the groups of the item.
@@ -415,9 +421,10 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
           mma_commit(bar_mma);
         }
         if (abort) break;
-        const bool ok3 = mbar_wait_bounded(bar_mma, ph_mma);
+        if (tid == 0) s_ok[1] = mbar_wait_bounded(bar_mma, ph_mma) ? 1 : 0;
         ph_mma ^= 1u;
-        if (!ok3) {
+        named_bar_consumers();
+        if (!s_ok[1]) {
           abort = true;
           break;
         }
