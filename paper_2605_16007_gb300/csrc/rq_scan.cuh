@@ -82,23 +82,37 @@ __device__ __forceinline__ void emit_word(bool pass, float d, uint32_t id, int64
 // whether this lane's vector passes for pair j, whose first mask index is
 // wrow[j] (the word's index is wrow[j] + word); lane j writes pair j's mask
 // word. Pairs j >= nvalid and words past the list's end (word_valid false,
-// where no lane passes) write no mask. All 32 lanes must call it.
+// where no lane passes) write no mask. The keys are written in a loop that
+// takes one passing pair per lane per round, as many rounds as the lane with
+// the most passing pairs needs (few: most pairs fail). All 32 lanes must
+// call it.
 template <int J>
 __device__ __forceinline__ void emit_chunk(uint32_t passbits, const float (&d)[J],
                                            const int64_t* wrow, int nvalid, int64_t word,
                                            bool word_valid, uint32_t id,
                                            uint32_t* __restrict__ mask,
                                            uint64_t* __restrict__ cand, int lane) {
-  const uint32_t lt = (1u << lane) - 1u;
   uint32_t mine = 0;
 #pragma unroll
   for (int j = 0; j < J; ++j) {
     const uint32_t m = __ballot_sync(0xffffffffu, (passbits >> j) & 1u);
     if (lane == j) mine = m;
-    if ((passbits >> j) & 1u)
-      cand[(wrow[j] + word) * 32 + __popc(m & lt)] = make_key(d[j], id);
   }
   if (word_valid && lane < J && lane < nvalid) mask[wrow[lane] + word] = mine;
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t pb = passbits;
+  while (__any_sync(0xffffffffu, pb != 0)) {
+    const int j = pb ? __ffs(pb) - 1 : 0;
+    const uint32_t mj = __shfl_sync(0xffffffffu, mine, j);
+    if (pb) {
+      pb &= pb - 1;
+      float dj = d[0];
+#pragma unroll
+      for (int k = 1; k < J; ++k)
+        if (j == k) dj = d[k];
+      cand[(wrow[j] + word) * 32 + __popc(mj & lt)] = make_key(dj, id);
+    }
+  }
 }
 
 // FP8 E4M3 encoding of an integer 0..15 (exact): v = 2^e (1 + m/8) with
