@@ -582,4 +582,28 @@ __device__ inline uint32_t block_kth_u32(const uint32_t* src, int m, int rank, i
   return (uint32_t)ctl[5];
 }
 
+// An upper bound on the rank-th smallest (1-based) of m uint32 values: the
+// radix passes stop once the bucket holding it has at most `slack` values,
+// and the bucket's upper edge is returned (the exact value when every bit
+// got resolved). At most `slack` - 1 values lie above the rank-th and at or
+// below the result, unless the values run out of bits first.
+__device__ inline uint32_t block_kth_upper_u32(const uint32_t* src, int m, int rank, int slack,
+                                               int* hist, uint64_t* small, int* ctl) {
+  const int top = block_top_diff_bit<uint32_t>(src, m, reinterpret_cast<uint32_t*>(small));
+  if (top < 0) return src[0];
+  uint32_t mask = top >= 31 ? 0u : ~((2u << top) - 1u);
+  uint32_t prefix = src[0] & mask;
+  int cnt = m;
+  for (int hb = top; hb >= 0 && cnt > slack;) {
+    const int shift = max(0, hb - 7), width = hb - shift + 1;
+    int b, below;
+    block_narrow<uint32_t>(src, m, shift, width, mask, prefix, rank, hist, ctl, b, below, cnt);
+    prefix |= (uint32_t)b << shift;
+    mask |= ((1u << width) - 1u) << shift;
+    rank -= below;
+    hb = shift - 1;
+  }
+  return prefix | ~mask;  // the unresolved low bits all set
+}
+
 }  // namespace rq

@@ -811,6 +811,7 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
 // increasing d, no fused multiply-add).
 constexpr int kProbeStageKeys = 4096;
 constexpr int kProbeCandCap = 256;
+constexpr int kProbeRowStage = 32;  // candidates whose rows are staged in shared memory
 
 // Exact form: select from the full exact ranking (pkeys, nlist keys per
 // query), staged in shared memory when it fits.
@@ -857,7 +858,8 @@ __device__ __forceinline__ float seq_sqdist(const float* qs, const float* __rest
 // centroid with a - e > U is not among the np nearest (not even on a tie);
 // the others (a few dozen) get the exact distance and the exact selection.
 // If more than kProbeCandCap remain, every centroid gets the exact distance.
-// Shared memory: `region` holds nlist keys + kProbeCandCap ints + D_p floats.
+// Shared memory: `region` holds max(nlist keys, kProbeRowStage rows of D_p
+// floats) + kProbeCandCap ints + D_p floats.
 __device__ inline int probe_select_certified(const float* __restrict__ g,
                                              const float* __restrict__ cn,
                                              const float* __restrict__ qrot,
@@ -867,7 +869,9 @@ __device__ inline int probe_select_certified(const float* __restrict__ g,
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t* ub = reinterpret_cast<uint32_t*>(region);  // nlist upper-bound keys
   uint64_t* keys = region;                            // later: exact keys (reuses ub)
-  int* cand = reinterpret_cast<int*>(region + nlist);
+  // in 8-byte units, even so that `cand` and `qs` stay 16-byte aligned
+  const int keys_area = (max(nlist, kProbeRowStage * dp / 2) + 1) & ~1;
+  int* cand = reinterpret_cast<int*>(region + keys_area);
   float* qs = reinterpret_cast<float*>(cand + kProbeCandCap);
   __shared__ float s_red[4];
   float part = 0.0f;
@@ -883,13 +887,18 @@ __device__ inline int probe_select_certified(const float* __restrict__ g,
   const float qn = s_red[0] + s_red[1] + s_red[2] + s_red[3];
   const float escale = 16.0f * (float)dp * 5.9604645e-8f;
   const float* grow = g + row * nlist;
+#pragma unroll 8
   for (int c = tid; c < nlist; c += blockDim.x) {
     const float av = qn + grow[c];
     ub[c] = orderable(av + escale * (qn + cn[c]));
   }
   if (tid == 0) ctl[6] = 0;
   __syncthreads();
-  const uint32_t U = block_kth_u32(ub, nlist, min(np, nlist), hist, small, ctl);
+  // Any U at or above the np-th smallest upper bound keeps the selection
+  // exact; the bucket edge of a partial radix search costs fewer passes and
+  // admits a few more candidates.
+  const uint32_t U = block_kth_upper_u32(ub, nlist, min(np, nlist), 16, hist, small, ctl);
+#pragma unroll 8
   for (int c = tid; c < nlist; c += blockDim.x) {
     const float av = qn + grow[c];
     if (orderable(av - escale * (qn + cn[c])) <= U) {
@@ -901,9 +910,42 @@ __device__ inline int probe_select_certified(const float* __restrict__ g,
   const int nc = ctl[6];
   const bool all = nc > kProbeCandCap;
   const int m = all ? nlist : nc;
-  for (int i = tid; i < m; i += blockDim.x) {
-    const int c = all ? i : cand[i];
-    keys[i] = make_key(seq_sqdist(qs, cR + (int64_t)c * dp, dp), (uint32_t)c);
+  if (!all && nc <= kProbeRowStage) {
+    // The candidates' rows are staged in shared memory (over the dead upper
+    // bounds), every load in flight together, then one thread per candidate
+    // adds its terms in order.
+    float* rows = reinterpret_cast<float*>(region);
+    const int q4 = dp / 4;
+    for (int i = tid; i < nc * q4; i += blockDim.x) {
+      const int j = i / q4, k4 = i - j * q4;
+      reinterpret_cast<float4*>(rows)[i] =
+          __ldg(reinterpret_cast<const float4*>(cR + (int64_t)cand[j] * dp) + k4);
+    }
+    __syncthreads();
+    float dist = 0.0f;
+    if (tid < nc) {
+      const float4* rw = reinterpret_cast<const float4*>(rows + tid * dp);
+      const float4* q4p = reinterpret_cast<const float4*>(qs);
+#pragma unroll 8
+      for (int d4 = 0; d4 < q4; ++d4) {
+        const float4 rv = rw[d4], qv = q4p[d4];
+        float df = __fsub_rn(qv.x, rv.x);
+        dist = __fadd_rn(dist, __fmul_rn(df, df));
+        df = __fsub_rn(qv.y, rv.y);
+        dist = __fadd_rn(dist, __fmul_rn(df, df));
+        df = __fsub_rn(qv.z, rv.z);
+        dist = __fadd_rn(dist, __fmul_rn(df, df));
+        df = __fsub_rn(qv.w, rv.w);
+        dist = __fadd_rn(dist, __fmul_rn(df, df));
+      }
+    }
+    __syncthreads();
+    if (tid < nc) keys[tid] = make_key(dist, (uint32_t)cand[tid]);
+  } else {
+    for (int i = tid; i < m; i += blockDim.x) {
+      const int c = all ? i : cand[i];
+      keys[i] = make_key(seq_sqdist(qs, cR + (int64_t)c * dp, dp), (uint32_t)c);
+    }
   }
   __syncthreads();
   return block_select_smallest(keys, m, np, dst, hist, small, ctl, true);
@@ -1049,7 +1091,7 @@ __global__ void __launch_bounds__(128, NW4 >= 4 ? 4 : 8) prep_kernel(PrepArgs a)
   __shared__ int ctl[8];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t row = blockIdx.x;
-  const int P = next_pow2(a.npmax);
+  const int P = max(2, next_pow2(a.npmax));  // keeps `region` 16-byte aligned
   uint64_t* dst = reinterpret_cast<uint64_t*>(smem);
   uint64_t* region = dst + P;
   const int npq = min(a.nprobe[row], a.npmax);
@@ -1224,10 +1266,13 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
     a.fac = ix->fac;
     a.bound = ws.bound;
     a.err = ix->d_err;
-    const size_t stage = certified ? (size_t)ix->nlist * 8 + kProbeCandCap * 4 + (size_t)dp * 4
-                                   : 0;
+    const size_t stage =
+        certified ? ((std::max<size_t>((size_t)ix->nlist * 8, (size_t)kProbeRowStage * dp * 4) +
+                      15) & ~(size_t)15) + kProbeCandCap * 4 + (size_t)dp * 4
+                  : 0;
     const int kpw = std::max(kBoundCandidates, sh.nsel_max);
-    const size_t smem = (size_t)next_pow2_host(np) * 8 + std::max<size_t>(stage, (size_t)kpw * 4);
+    const size_t smem =
+        (size_t)std::max(2, next_pow2_host(np)) * 8 + std::max<size_t>(stage, (size_t)kpw * 4);
     static bool attr = false;
     if (!attr) {
       RQ_CUDA(cudaFuncSetAttribute(prep_kernel<NW4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
