@@ -85,6 +85,8 @@ def parse():
     ap.add_argument("--nprobe", type=int, default=None, help="skip the sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-hbm", action="store_true",
+                    help="skip the scan measurement on the 10M-vector skewed index")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--profile", action="store_true",
                     help="only build and run --warmup + --steps batches per scan mode "
@@ -446,6 +448,8 @@ def run_ours(args, rank, world, local, pg):
         "clocks": clk,
         "gpu_launches": launches_per_step * (args.steps + args.warmup),
     }
+    if not args.no_hbm:
+        res["hbm_scan"] = run_hbm_scan(rq, dev, flush, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(ix, q[:bs], nprobe, k, nrr, args.cpu_seconds)
     ix_err = ix.device_error()
@@ -494,6 +498,73 @@ def run_serving(rq, ix, q, nprobe, k, nrr, offered, seconds=2.0, seed=3):
             "requests": len(lats), "p50_ms": round(lats[len(lats) // 2], 3),
             "p99_ms": round(lats[min(len(lats) - 1, int(0.99 * len(lats)))], 3),
             "request_sizes": "uniform 1-64 queries, Poisson arrivals"}
+
+
+def measured_hbm_gbs() -> float:
+    """Copy bandwidth measured on this machine, else the stated fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+def run_hbm_scan(rq, dev, flush, stream, n=10_000_000, nq=64, nprobe=32, k=10, nrr=200):
+    """The scan on an index larger than L2: the skewed recipe (N=10M x 96 unit
+    vectors, 1024-component Zipf mixture, nlist 4096, list lengths varying by
+    more than 100x), 64 queries at nprobe 32, L2 flushed before each search.
+    Reports the scan time of each scan mode and the unique index bytes the
+    probed lists hold (codes + {r^2, f}) per unit time against the measured
+    HBM copy bandwidth."""
+    import torch
+
+    wl = W.WORKLOADS["skewed"]
+    mix = wl["mix"]
+    x_dev = torch.from_numpy(mix.base(n)).to(dev)
+    t0 = time.perf_counter()
+    ix = rq.rq_build(x_dev, wl["nlist"], seed=0, kmeans_iters=4, train_size=1_000_000)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    del x_dev
+    q = torch.from_numpy(mix.queries(nq)).to(dev)
+    ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
+    dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    st = ix.stats()
+    scan = {}
+    for name, mode in (("plain", rq.RQ_SCAN_PLAIN), ("grouped", rq.RQ_SCAN_GROUPED),
+                       ("mma", rq.RQ_SCAN_MMA)):
+        for _ in range(2):
+            ix.search(q, nprobe, k, nrr, out_ids=ids, out_dist=dist, scan_mode=mode, stream=stream)
+        ts = []
+        for _ in range(7):
+            flush.zero_()
+            stt = {}
+            ix.search(q, nprobe, k, nrr, out_ids=ids, out_dist=dist, scan_mode=mode,
+                      stream=stream, stage_times=stt)
+            ts.append(stt["scan"])
+        scan[name] = round(sorted(ts)[len(ts) // 2], 4)
+    pid = torch.empty((nq, nprobe), dtype=torch.int32, device=dev)
+    ix.search(q, nprobe, k, nrr, out_ids=ids, out_dist=dist, dump={"probe_ids": pid},
+              stream=stream)
+    torch.cuda.synchronize()
+    lens = np.diff(ix.offsets())
+    p = pid.cpu().numpy()
+    unit = st["dim_pad"] // 8 + 8
+    unique_b = int(lens[np.unique(p)].sum()) * unit
+    pairs = int(lens[p].sum())
+    best = min(scan, key=scan.get)
+    gbs = unique_b / (scan[best] / 1e3) / 1e9
+    peak = measured_hbm_gbs()
+    ix.free()
+    return {"workload": f"skewed-shaped: N={n} D={mix.dim} (D_p {st['dim_pad']}) unit vectors, "
+                        f"Zipf list lengths, nlist={wl['nlist']}, {nq} queries, nprobe={nprobe}, "
+                        f"k={k}, n_rerank={nrr}",
+            "scan_ms": scan, "best_mode": best, "unique_index_bytes": unique_b,
+            "pairs": pairs, "pairs_per_vector": round(pairs / max(1, unique_b // unit), 2),
+            "hbm_gbs": round(gbs, 1), "peak_gbs": peak, "frac": round(gbs / peak, 4),
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+            "list_len": {"min": int(lens.min()), "max": int(lens.max())},
+            "build_s": round(build_s, 2)}
 
 
 def run_serving_saturated(rq, ix, q, nprobe, k, nrr, req=250, rounds=5, slots=4):

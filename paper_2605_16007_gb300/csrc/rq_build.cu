@@ -771,6 +771,7 @@ rq_status finish_index_host_side(rq_index* ix) {
     return na > nb;
   });
   std::sort(len.begin(), len.end(), std::greater<int64_t>());
+  ix->max_list_len = ix->nlist > 0 ? len[0] : 0;
   ix->top_len_prefix.assign(ix->nlist + 1, 0);
   ix->top_words_prefix.assign(ix->nlist + 1, 0);
   for (int l = 0; l < ix->nlist; ++l) {

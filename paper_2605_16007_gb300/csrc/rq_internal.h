@@ -88,6 +88,7 @@ struct Workspace {
   int32_t* list_count = nullptr;  // nlist: pairs probing each list
   int32_t* list_pairs = nullptr;  // nlist x nq: pair ids (q * npmax + p) per list
   int32_t* work_count = nullptr;  // work-item counter of the persistent scan
+  int32_t* nchunks = nullptr;     // plain scan: nq x npmax chunk counts
   uint8_t* qdig = nullptr;        // nlist x nq x D_p: per-list buckets of FP8 query digits
   float4* qpb = nullptr;          // nlist x nq (+2): per-list buckets of {vl, delta, nq2, -Sq},
                                   // interleaved by slot couples
@@ -132,6 +133,7 @@ struct rq_index {
   std::vector<int64_t> h_offsets;
   std::vector<int64_t> top_len_prefix;    // sum of the j largest list lengths
   std::vector<int64_t> top_words_prefix;  // sum of the j largest ceil(length / 32)
+  int64_t max_list_len = 0;
   // tuned choice for RQ_SCAN_AUTO
   std::atomic<int> auto_mode{RQ_SCAN_GROUPED};
   // plans (workspaces, graphs) per (stream, shape)

@@ -231,13 +231,18 @@ __device__ __forceinline__ void quantize_pair(int64_t pair, int64_t q, int c, in
 }
 
 // ---------------------------------------------------------------------------
-// Plain scan: one block per (query, probed list) -- the query-level schedule
-// of Section 3.3.1. Each warp writes the survivor mask word and the keys of
-// its 32 vectors (emit_word).
+// Plain scan: one block per (query, probed list, chunk of kPlainChunk
+// vectors) -- the query-level schedule of Section 3.3.1, with long lists cut
+// into chunks so that they do not leave one block running alone. A thread
+// loads the codes of up to eight 128-vector steps before estimating them;
+// each warp writes the survivor mask word and the keys of its 32 vectors
+// (emit_word).
 // ---------------------------------------------------------------------------
+constexpr int kPlainChunk = 1024;  // vectors of one list per block of the plain scan
+
 template <int NW4>
 __global__ void __launch_bounds__(128)
-scan_plain_kernel(const int32_t* __restrict__ probe_ids, const int32_t* __restrict__ nprobe,
+scan_plain_kernel(const int32_t* __restrict__ nchunks, const int32_t* __restrict__ probe_ids,
                   int npmax, const float4* __restrict__ qparams,
                   const uint32_t* __restrict__ planes, const int64_t* __restrict__ offsets,
                   const uint8_t* __restrict__ codes, const float2* __restrict__ fac,
@@ -245,30 +250,54 @@ scan_plain_kernel(const int32_t* __restrict__ probe_ids, const int32_t* __restri
                   const int32_t* __restrict__ wbase, int64_t mwords, uint32_t* __restrict__ mask,
                   uint64_t* __restrict__ cand) {
   constexpr int W = 4 * NW4;
+  constexpr int RB = NW4 >= 8 ? 1 : 8 / NW4;  // 128-vector steps with their loads in flight
   __shared__ __align__(16) uint32_t s_pl[4 * W];
   const int64_t pair = blockIdx.x;
+  // block-uniform: a chunk past the list's end, or a probe past the query's
+  // nprobe (no chunks), leaves after one load
+  if ((int)blockIdx.y >= nchunks[pair]) return;
   const int64_t q = pair / npmax;
-  const int p = (int)(pair % npmax);
-  if (p >= nprobe[q]) return;
+  const int c = probe_ids[pair];
+  const int64_t lo = offsets[c], hi = offsets[c + 1];
+  const int64_t start = lo + (int64_t)blockIdx.y * kPlainChunk;
+  const int64_t end = min(hi, start + kPlainChunk);
   for (int i = threadIdx.x; i < 4 * W; i += blockDim.x) s_pl[i] = planes[pair * 4 * W + i];
   __syncthreads();
   const float4 qp = qparams[pair];
-  const int c = probe_ids[pair];
-  const int64_t lo = offsets[c], hi = offsets[c + 1];
   const uint32_t tau = bound[q];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t wrow = q * mwords + wbase[pair];
-  for (int64_t s0 = lo; s0 < hi; s0 += blockDim.x) {
-    if (s0 + warp * 32 >= hi) break;  // warp-uniform: this word is past the list's end
-    const int64_t s = s0 + threadIdx.x;
-    bool pass = false;
-    float d = 0.0f;
-    if (s < hi) {
-      const uint4* cp = reinterpret_cast<const uint4*>(codes + s * (dp / 8));
-      d = estimate_code<NW4>(cp, fac[s], s_pl, qp, dp);
-      pass = orderable(d) <= tau;
+  for (int64_t b0 = start; b0 < end; b0 += 128 * RB) {
+    uint4 code[RB][NW4];
+    float2 fv[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const int64_t s = b0 + 128 * r + threadIdx.x;
+      if (s < end) {
+        const uint4* cp = reinterpret_cast<const uint4*>(codes + s * (dp / 8));
+#pragma unroll
+        for (int w = 0; w < NW4; ++w) code[r][w] = __ldg(cp + w);
+        fv[r] = __ldg(fac + s);
+      }
     }
-    emit_word(pass, d, pass ? ids[s] : 0u, wrow + (s0 - lo) / 32 + warp, mask, cand, lane);
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const int64_t s0 = b0 + 128 * r;
+      if (s0 + warp * 32 >= end) break;  // warp-uniform: this word is past the chunk's end
+      const int64_t s = s0 + threadIdx.x;
+      bool pass = false;
+      float d = 0.0f;
+      if (s < end) {
+        int pc = 0;
+#pragma unroll
+        for (int w = 0; w < NW4; ++w)
+          pc += __popc(code[r][w].x) + __popc(code[r][w].y) + __popc(code[r][w].z) +
+                __popc(code[r][w].w);
+        d = estimate_regs<NW4>(code[r], pc, fv[r], s_pl, qp, dp);
+        pass = orderable(d) <= tau;
+      }
+      emit_word(pass, d, pass ? ids[s] : 0u, wrow + (s0 - lo) / 32 + warp, mask, cand, lane);
+    }
   }
 }
 
@@ -1080,6 +1109,7 @@ struct PrepArgs {
   const uint8_t* codes;
   const float2* fac;
   uint32_t* bound;
+  int32_t* nchunks;   // plain scan: kPlainChunk chunks of each probe (null otherwise)
   int32_t* err;
 };
 
@@ -1101,6 +1131,16 @@ __global__ void __launch_bounds__(128, NW4 >= 4 ? 4 : 8) prep_kernel(PrepArgs a)
           : probe_select_exact(a.pkeys, a.nlist, a.npmax, row, dst, region, hist, small, ctl);
   probe_outputs(dst, got, a.npmax, row, a.probe_ids, a.probe_d, a.offsets, npq, a.wbase,
                 a.wtotal);
+  if (a.nchunks) {
+    for (int p = tid; p < a.npmax; p += blockDim.x) {
+      int nc = 0;
+      if (p < npq && p < got) {
+        const uint32_t l = (uint32_t)dst[p];
+        nc = (int)((a.offsets[l + 1] - a.offsets[l] + kPlainChunk - 1) / kPlainChunk);
+      }
+      a.nchunks[row * a.npmax + p] = nc;
+    }
+  }
   if (got < npq) {
     if (tid == 0) flag_error(a.err, kErrBadProbe);
     return;
@@ -1172,6 +1212,8 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
     L.take(&ws.list_count, ix->nlist);
     L.take(&ws.list_pairs, (int64_t)ix->nlist * nq);
     L.take(&ws.work_count, 4);
+  } else {
+    L.take(&ws.nchunks, nq * np);
   }
   if (sh.mode == RQ_SCAN_MMA) {
     L.take(&ws.qdig, (int64_t)ix->nlist * nq * ix->dp);
@@ -1211,6 +1253,8 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
     rebase(ws.list_count, b);
     rebase(ws.list_pairs, b);
     rebase(ws.work_count, b);
+  } else {
+    rebase(ws.nchunks, b);
   }
   if (sh.mode == RQ_SCAN_MMA) {
     rebase(ws.qdig, b);
@@ -1265,6 +1309,7 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
     a.codes = ix->codes;
     a.fac = ix->fac;
     a.bound = ws.bound;
+    a.nchunks = grouped ? nullptr : ws.nchunks;
     a.err = ix->d_err;
     const size_t stage =
         certified ? ((std::max<size_t>((size_t)ix->nlist * 8, (size_t)kProbeRowStage * dp * 4) +
@@ -1285,8 +1330,10 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
   tm.mark(RQ_STAGE_WORKLIST, st);
   if (sh.mode == RQ_SCAN_PLAIN) {
     tm.mark(RQ_STAGE_SCAN, st);
-    scan_plain_kernel<NW4><<<(unsigned)pairs, 128, 0, st>>>(
-        ws.probe_ids, ws.nprobe, np, ws.qparams, ws.planes, ix->offsets, ix->codes, ix->fac,
+    const unsigned chunks =
+        (unsigned)std::max<int64_t>(1, (ix->max_list_len + kPlainChunk - 1) / kPlainChunk);
+    scan_plain_kernel<NW4><<<dim3((unsigned)pairs, chunks), 128, 0, st>>>(
+        ws.nchunks, ws.probe_ids, np, ws.qparams, ws.planes, ix->offsets, ix->codes, ix->fac,
         ix->ids, dp, ws.bound, ws.wbase, ws.mwords, ws.mask, ws.cand);
   } else {
     int sms = 148;
