@@ -154,37 +154,6 @@ __device__ inline uint64_t block_radix_select_u64(const uint64_t* keys,
   return prefix;
 }
 
-// Same over uint32 keys held in shared memory (4 digits of 8 bits).
-__device__ inline uint32_t block_radix_select_u32(const uint32_t* keys,
-                                                  int count, int rank,
-                                                  int* hist, uint32_t* bcast) {
-  uint32_t prefix = 0;
-  for (int shift = 24; shift >= 0; shift -= 8) {
-    const uint32_t hi_mask = (shift == 24) ? 0u : (~0u << (shift + 8));
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < count; i += blockDim.x) {
-      const uint32_t k = keys[i];
-      if ((k & hi_mask) == prefix) atomicAdd(&hist[(k >> shift) & 255], 1);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int cum = 0, b = 0;
-      for (; b < 256; ++b) {
-        if (cum + hist[b] >= rank) break;
-        cum += hist[b];
-      }
-      if (b > 255) b = 255;
-      bcast[0] = prefix | ((uint32_t)b << shift);
-      bcast[1] = (uint32_t)(rank - cum);
-    }
-    __syncthreads();
-    prefix = bcast[0];
-    rank = (int)bcast[1];
-    __syncthreads();
-  }
-  return prefix;
-}
 
 }  // namespace rq
 
@@ -268,152 +237,8 @@ __device__ __forceinline__ void warp_find_bucket(const int* hist, int rank, int&
   cnt = __shfl_sync(0xffffffffu, hb, src);
 }
 
-// Sorts dst[0, n) ascending, dst[n, next_pow2(n)) holding all ones: in
-// registers for n <= 32, else a bitonic network over shared memory.
-__device__ inline void warp_sort_keys(uint64_t* dst, int n) {
-  const int lane = threadIdx.x & 31;
-  if (n <= 32) {
-    const uint64_t v = warp_sort32(lane < n ? dst[lane] : kU64Max);
-    if (lane < n) dst[lane] = v;
-    __syncwarp();
-    return;
-  }
-  const int m = next_pow2(n);
-  for (int k = 2; k <= m; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = lane; i < m; i += 32) {
-        const int l = i ^ j;
-        if (l > i) {
-          const uint64_t a = dst[i], c = dst[l];
-          if ((a > c) == ((i & k) == 0)) {
-            dst[i] = c;
-            dst[l] = a;
-          }
-        }
-      }
-      __syncwarp();
-    }
-  }
-}
 
-// The n smallest of m distinct uint64 keys at src (shared or global memory)
-// into dst[0, n) (ascending if `sorted`) with dst[n, next_pow2(n)) = all
-// ones; dst holds next_pow2(max(n, 1)) keys. Returns min(n, m). Radix passes
-// narrow the bucket of the n-th key to at most 32 keys, which the warp sorts
-// in registers.
-__device__ inline int warp_select_smallest(const uint64_t* src, int m, int n, uint64_t* dst,
-                                           int* hist, uint64_t* small, bool sorted) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t lt = (1u << lane) - 1u;
-  const int sel = min(n, m);
-  const int mp = next_pow2(max(sel, 1));
-  if (m <= n) {
-    for (int i = lane; i < mp; i += 32) dst[i] = (i < m) ? src[i] : kU64Max;
-    __syncwarp();
-    if (sorted) warp_sort_keys(dst, sel);
-    return sel;
-  }
-  uint64_t prefix = 0, mask = 0;
-  int rank = n, cnt = m;
-  for (int shift = 56; shift >= 0 && cnt > 32; shift -= 8) {
-    for (int i = lane; i < 256; i += 32) hist[i] = 0;
-    __syncwarp();
-    for (int base = 0; base < m; base += 32) {
-      const int i = base + lane;
-      uint64_t k = 0;
-      bool act = false;
-      if (i < m) {
-        k = src[i];
-        act = (k & mask) == prefix;
-      }
-      hist_add(hist, (int)((k >> shift) & 255), act);
-    }
-    __syncwarp();
-    int b, below;
-    warp_find_bucket(hist, rank, b, below, cnt);
-    __syncwarp();
-    prefix |= (uint64_t)b << shift;
-    mask |= 0xFFull << shift;
-    rank -= below;
-  }
-  int nd = 0, ns = 0;
-  for (int base = 0; base < m; base += 32) {
-    const int i = base + lane;
-    uint64_t k = kU64Max;
-    if (i < m) k = src[i];
-    const uint64_t km = k & mask;
-    const bool lo = i < m && km < prefix;
-    const bool eq = i < m && km == prefix;
-    const uint32_t mlo = __ballot_sync(0xffffffffu, lo);
-    const uint32_t meq = __ballot_sync(0xffffffffu, eq);
-    if (lo) {
-      const int p = nd + __popc(mlo & lt);
-      if (p < n) dst[p] = k;
-    }
-    if (eq) {
-      const int p = ns + __popc(meq & lt);
-      if (p < 32) small[p] = k;
-    }
-    nd += __popc(mlo);
-    ns += __popc(meq);
-  }
-  __syncwarp();
-  const uint64_t v = warp_sort32(lane < min(ns, 32) ? small[lane] : kU64Max);
-  const int have = n - rank;
-  if (lane < rank) dst[have + lane] = v;
-  for (int i = n + lane; i < mp; i += 32) dst[i] = kU64Max;
-  __syncwarp();
-  if (sorted) warp_sort_keys(dst, n);
-  return sel;
-}
 
-// The rank-th smallest (1-based) of m uint32 values in shared memory
-// (duplicates allowed), by one warp.
-__device__ inline uint32_t warp_kth_u32(const uint32_t* src, int m, int rank, int* hist,
-                                        uint64_t* small) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t lt = (1u << lane) - 1u;
-  uint32_t prefix = 0, mask = 0;
-  int cnt = m;
-  for (int shift = 24; shift >= 0 && cnt > 32; shift -= 8) {
-    for (int i = lane; i < 256; i += 32) hist[i] = 0;
-    __syncwarp();
-    for (int base = 0; base < m; base += 32) {
-      const int i = base + lane;
-      uint32_t k = 0;
-      bool act = false;
-      if (i < m) {
-        k = src[i];
-        act = (k & mask) == prefix;
-      }
-      hist_add(hist, (int)((k >> shift) & 255), act);
-    }
-    __syncwarp();
-    int b, below;
-    warp_find_bucket(hist, rank, b, below, cnt);
-    __syncwarp();
-    prefix |= (uint32_t)b << shift;
-    mask |= 0xFFu << shift;
-    rank -= below;
-  }
-  if (mask == 0xFFFFFFFFu) return prefix;
-  int ns = 0;
-  for (int base = 0; base < m; base += 32) {
-    const int i = base + lane;
-    uint32_t k = 0;
-    if (i < m) k = src[i];
-    const bool eq = i < m && (k & mask) == prefix;
-    const uint32_t meq = __ballot_sync(0xffffffffu, eq);
-    if (eq) {
-      const int p = ns + __popc(meq & lt);
-      if (p < 32) small[p] = k;
-    }
-    ns += __popc(meq);
-  }
-  __syncwarp();
-  const uint64_t v = warp_sort32(lane < min(ns, 32) ? small[lane] : kU64Max);
-  return (uint32_t)__shfl_sync(0xffffffffu, v, rank - 1);
-}
 
 // ---------------------------------------------------------------------------
 // Block-level selection: every thread of the block takes part (histograms by

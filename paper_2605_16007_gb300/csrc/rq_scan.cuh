@@ -1,5 +1,5 @@
 // The RaBitQ estimator on packed codes and query bit-planes (Eqs. 4-5,
-// Section 3.3.2), and the candidate append shared by the scan kernels.
+// Section 3.3.2), and the survivor output shared by the scan kernels.
 #pragma once
 
 #include "rq_common.cuh"
@@ -10,7 +10,6 @@ namespace rq {
 constexpr int kGroupVectors = 256;  // vectors per grouped work item (one per thread)
 
 // Pairs per grouped work item: query planes of the group sit in shared memory.
-inline int group_pairs_for(int dp) { return dp <= 1024 ? 64 : 32; }
 template <int NW4>
 struct GroupPairs {
   static constexpr int value = (NW4 <= 8) ? 64 : 32;
@@ -50,18 +49,6 @@ __device__ __forceinline__ float estimate_regs(const uint4 (&code)[NW4], int pc,
   return __fadd_rn(d, 0.0f);
 }
 
-template <int NW4>
-__device__ __forceinline__ float estimate_code(const uint4* __restrict__ cp, float2 fac,
-                                               const uint32_t* pl, float4 qp, int dp) {
-  uint4 code[NW4];
-  int pc = 0;
-#pragma unroll
-  for (int i = 0; i < NW4; ++i) {
-    code[i] = __ldg(cp + i);
-    pc += __popc(code[i].x) + __popc(code[i].y) + __popc(code[i].z) + __popc(code[i].w);
-  }
-  return estimate_regs<NW4>(code, pc, fac, pl, qp, dp);
-}
 
 // Scan output without atomics. The vectors of a probed list are cut into
 // 32-vector words; word w of probe p of query q has the fixed mask index

@@ -302,16 +302,12 @@ scan_plain_kernel(const int32_t* __restrict__ nchunks, const int32_t* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// Grouped scan: the work list. Pairs (query, probe) are grouped by list; a
-// work item is (list, first vector, first pair, pairs) with at most
-// kGroupVectors vectors and group_pairs_for(D_p) pairs. Items cross query boundaries,
-// so one persistent launch stays balanced over skewed list lengths.
-// ---------------------------------------------------------------------------
 // Grouped scan (Section 3.3.1 block-level schedule, with the queries that
 // probe one list served together): work items are the index's static
-// (list, first vector) blocks of kGroupVectors vectors, taken from a global
-// counter by persistent blocks so that work crosses query boundaries. A
-// thread holds one vector's code in registers and runs the estimator for every
+// (list, first vector) blocks of kGroupVectors vectors, longest lists first,
+// taken from a global counter by persistent blocks so that work crosses
+// query boundaries and stays balanced over skewed list lengths. A thread
+// holds one vector's code in registers and runs the estimator for every
 // (query, list) pair that probes the list, GP pairs at a time with their
 // bit-planes staged in shared memory.
 template <int NW4>
