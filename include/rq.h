@@ -61,8 +61,9 @@ typedef enum rq_status {
 typedef enum rq_dtype { RQ_F32 = 0, RQ_U8 = 1 } rq_dtype;
 
 /* How the code scan (Section 3.3.1-3.3.2) is scheduled.
- *  PLAIN:   one thread block per (query, probed list), launched per batch
- *           (the query-level schedule the paper starts from, Section 3.3.1).
+ *  PLAIN:   one thread block per (query, probed list, chunk of 1024 list
+ *           vectors), launched per batch (the query-level schedule the paper
+ *           starts from, Section 3.3.1); suits few queries per list.
  *  GROUPED: one persistent launch walks a work list of (list, vector block,
  *           group of queries probing that list); the block's codes are loaded
  *           once for the whole group and the popcount estimator runs per pair.
@@ -211,13 +212,17 @@ RQ_API rq_status rq_philox_gaussian(uint64_t seed, uint32_t stream, int64_t coun
 /* rq_search -- k nearest neighbours of nq queries (Section 2.1.2 query
  * processing; Sections 3.3.1-3.3.4):
  *   1. rotate each query once: q' = P^T q (P^T (q - c) = q' - P^T c),
- *   2. rank the centroids by ||q' - P^T c||^2 and keep the nprobe nearest,
+ *   2. rank the centroids by ||q' - P^T c||^2 (float32, terms added in
+ *      increasing dimension) and keep the nprobe nearest by (distance, id);
+ *      for nlist <= 4096 and D_p = 128 an approximate ranking with a proven
+ *      error bound first narrows the centroids that need the exact value,
  *   3. quantise each residual q' - P^T c to 4 bits (vl, delta, bit-planes),
  *   4. scan the probed lists with the estimator of Eqs. 4-5, keep candidates
  *      at or below a per-query bound set from the nearest lists (Section
  *      3.3.3), select the n_rerank smallest estimates,
  *   5. re-rank them with exact float32 distances to the raw vectors, keep k.
- *   queries   host or device, nq x dim float32.
+ *   queries   host or device, nq x dim float32 (host queries are checked to be
+ *             finite; results for non-finite device queries are unspecified).
  *   out_ids   host or device, nq x k int64; out_dist: nq x k float32
  *             (exact distances; estimated ones when n_rerank == 0, in which
  *             case the top k by the estimate are returned without re-rank).
