@@ -248,6 +248,33 @@ def test_uint8_base_and_sift_like_data(rq):
     assert R.recall_at(x, q, dump["ids"], td, 10) >= 0.9
 
 
+def test_full_size_sift_batch_sampled_replay(rq):
+    """The bench's workload at full size (1,000,000 x 128, nlist 1024, a batch
+    of 1000 queries, nprobe 16, k 10, n_rerank 200) in the bench's launch
+    form (tensor-core scan from a captured graph): identical to the
+    uncaptured search with every intermediate dumped, and eight sampled
+    queries replayed stage by stage in the oracle, bit for bit."""
+    wl = W.WORKLOADS["sift1m"]
+    x = torch.from_numpy(wl["mix"].base(wl["n"])).cuda()
+    q = wl["mix"].queries(wl["batch"])
+    ix = rq.rq_build(x, wl["nlist"], seed=0, kmeans_iters=wl["iters"])
+    del x
+    qd = torch.from_numpy(q).cuda()
+    ids = torch.empty((q.shape[0], 10), dtype=torch.int64, device="cuda")
+    dist = torch.empty((q.shape[0], 10), dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        ix.search(qd, 16, 10, 200, out_ids=ids, out_dist=dist, scan_mode=3, use_graph=True)
+    torch.cuda.synchronize()
+    dump = search_dump(ix, q, 16, 10, 200, scan_mode=3)
+    assert np.array_equal(ids.cpu().numpy(), dump["ids"])
+    assert np.array_equal(dist.cpu().numpy().view(np.uint32), dump["dist"].view(np.uint32))
+    rows = np.random.default_rng(5).choice(q.shape[0], 8, replace=False)
+    sub = {kk: (v[rows] if isinstance(v, np.ndarray) and v.shape[:1] == (q.shape[0],) else v)
+           for kk, v in dump.items()}
+    st = replay_and_compare(host_index(ix), q[rows], sub)
+    assert st["pairs"] == 8 * 16
+
+
 def test_export_import_roundtrip(tiny, tmp_path):
     _, q, ix, _ = tiny
     path = str(tmp_path / "ix.rq")
