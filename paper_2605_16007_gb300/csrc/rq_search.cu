@@ -241,7 +241,7 @@ __device__ __forceinline__ void quantize_pair(int64_t pair, int64_t q, int c, in
 constexpr int kPlainChunk = 1024;  // vectors of one list per block of the plain scan
 
 template <int NW4>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, NW4 == 1 ? 8 : 4)  // 8 blocks/SM: 3% faster at D_p 128
 scan_plain_kernel(const int32_t* __restrict__ nchunks, const int32_t* __restrict__ probe_ids,
                   int npmax, const float4* __restrict__ qparams,
                   const uint32_t* __restrict__ planes, const int64_t* __restrict__ offsets,
