@@ -56,7 +56,7 @@ SMS = 152
 # DRAM traffic of one scan launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by kernel; valid only while the kernel source
 # hash matches the one recorded at capture time.
-TRAFFIC = {"scan:sift1m:9078f25a0b1ccd31": 31981312}
+TRAFFIC = {"scan:sift1m:2333b74c9e8dbbfe": 31981312}
 
 
 def measured_bf16_tflops() -> float:
@@ -69,9 +69,13 @@ def measured_bf16_tflops() -> float:
 
 
 def kernel_source_hash() -> str:
+    """Hash of the sources the tensor-core scan kernel is compiled from (its
+    translation unit and the headers it includes)."""
     h = hashlib.sha256()
-    for f in ("rq_search.cu", "rq_scan.cuh", "rq_scan_mma.cu"):
-        with open(os.path.join(ROOT, "paper_2605_16007_gb300", "csrc", f), "rb") as fh:
+    for f in ("paper_2605_16007_gb300/csrc/rq_scan_mma.cu", "paper_2605_16007_gb300/csrc/rq_scan.cuh",
+              "paper_2605_16007_gb300/csrc/rq_common.cuh", "paper_2605_16007_gb300/csrc/rq_internal.h",
+              "include/rq.h"):
+        with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -371,7 +375,7 @@ def run_ours(args, rank, world, local, pg):
                     "peak": round(peak, 4), "unit": "Tpopc/s", "frac": round(achieved / peak, 4),
                     "peak_source": "derived: 16 POPC/clk/SM x 152 SMs x 2070 MHz"}
     roofline.update({
-        "traffic": TRAFFIC.get(key),
+        "traffic": TRAFFIC.get(key) if tuned == rq.RQ_SCAN_MMA else None,
         "scan_ms": round(stages["scan"], 4),
         "pairs_per_launch": pairs,
         "logical_gbs": round(logical_gbs, 1),
