@@ -196,7 +196,7 @@ def test_mixed_batch_equals_alone_and_replays(tiny):
     nq = 40
     npb, kk = W.per_query_params(nq, 5, (1, 64), (1, 10, 33))
     nr = np.where(np.arange(nq) % 5 == 0, 0, np.maximum(kk, 50)).astype(np.int32)
-    for mode in (2, 3):
+    for mode in (1, 2, 3):
         dump = search_dump(ix, q[:nq], npb, kk, nr, mixed=True, scan_mode=mode)
         replay_and_compare(h, q[:nq], dump)
     for i in range(0, nq, 7):
