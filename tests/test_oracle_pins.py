@@ -409,3 +409,81 @@ def test_per_query_params_and_no_rerank(tiny):
         assert np.array_equal(ids[i, :kk[i]], one[0])
     ids0, d0 = R.search(ix, q[:4], 4, 5, 0)
     assert np.all(np.diff(d0, axis=1) >= 0)
+
+
+def _fma32(x, y, z):
+    """float32 fused multiply-add, correctly rounded: the product is exact in
+    float64 and the sum's float64 rounding error is recovered (TwoSum) to
+    break float32 rounding ties the right way."""
+    x, y, z = (np.asarray(v, np.float64) for v in (x, y, z))
+    p = x * y                      # exact: 24 + 24 bits
+    s = p + z
+    bp = s - z
+    e = (p - bp) + (z - (s - bp))  # s + e == p + z exactly
+    r = s.astype(np.float32)
+    back = r.astype(np.float64)
+    # where s is a float32 midpoint, the sign of e decides the rounding
+    up = np.nextafter(r, np.float32(np.inf)).astype(np.float64)
+    dn = np.nextafter(r, np.float32(-np.inf)).astype(np.float64)
+    tie_hi = (s - back) == (up - back) / 2
+    tie_lo = (back - s) == (back - dn) / 2
+    r = np.where(tie_hi & (e > 0), np.float32(up), r)
+    r = np.where(tie_lo & (e < 0), np.float32(dn), r)
+    return r.astype(np.float32)
+
+
+def test_certified_probe_filter_bound():
+    """The centroid filter of the search keeps c unless its approximate
+    distance a = ||q||^2 + (||c||^2 - 2 <q, c>), computed in float32 with
+    fused multiply-adds in any order, is more than
+    e = 16 D_p 2^-24 (||q||^2 + ||c||^2) above a smaller bound; that needs
+    |a - exact| <= e, exact being the fixed-order float32 distance. Checked
+    with sequential and reversed FMA orders on random rows, rows almost equal
+    to the query (cancellation) and large, mixed-sign magnitudes."""
+    rng = np.random.default_rng(17)
+    dp = 128
+    esc = np.float32(16.0 * dp * 2.0 ** -24)
+    cases = []
+    q = rng.normal(0, 1, (8, dp)).astype(np.float32)
+    cases.append((q, rng.normal(0, 1, (64, dp)).astype(np.float32)))
+    cases.append((q, (q[:1] + rng.normal(0, 1e-3, (64, dp))).astype(np.float32)))
+    big = (rng.normal(0, 1, (8, dp)) * 1e6).astype(np.float32)
+    cases.append((big, (big[:1] * rng.uniform(0.999, 1.001, (64, dp))).astype(np.float32)))
+    cases.append((q * 300, rng.normal(0, 300, (64, dp)).astype(np.float32)))
+    for qq, cc in cases:
+        exact = R.seq_sqdist(qq, cc)
+        for order in (range(dp), range(dp - 1, -1, -1)):
+            qn = np.zeros(qq.shape[0], np.float32)
+            cn = np.zeros(cc.shape[0], np.float32)
+            dot = np.zeros((qq.shape[0], cc.shape[0]), np.float32)
+            for d in order:
+                qn = _fma32(qq[:, d], qq[:, d], qn)
+                cn = _fma32(cc[:, d], cc[:, d], cn)
+                dot = _fma32(qq[:, d, None], cc[None, :, d], dot)
+            g = _fma32(np.float32(-2.0), dot, cn[None, :])
+            a = (qn[:, None] + g).astype(np.float32)
+            e = esc * (qn[:, None] + cn[None, :])
+            gap = np.abs(a.astype(np.float64) - exact.astype(np.float64))
+            assert np.all(gap <= e), (gap / e).max()
+
+
+def test_fma32_helper_is_correctly_rounded():
+    """The helper of the bound pin: against exact rationals on random and
+    tie-making inputs."""
+    from fractions import Fraction
+    rng = np.random.default_rng(3)
+    x = rng.normal(0, 1, 300).astype(np.float32)
+    y = rng.normal(0, 1, 300).astype(np.float32)
+    z = rng.normal(0, 1e-3, 300).astype(np.float32)
+    # ties: z chosen so that x*y + z lands halfway between two float32 values
+    x[:20] = np.float32(1.0) + np.float32(2.0 ** -23)
+    y[:20] = np.float32(1.0) + np.float32(2.0 ** -23)
+    z[:20] = np.float32(0.0)
+    r = _fma32(x, y, z)
+    for i in range(300):
+        ex = Fraction(float(x[i])) * Fraction(float(y[i])) + Fraction(float(z[i]))
+        cands = [np.float32(float(ex)), np.nextafter(np.float32(float(ex)), np.float32(np.inf)),
+                 np.nextafter(np.float32(float(ex)), np.float32(-np.inf))]
+        best = min(cands, key=lambda c: (abs(Fraction(float(c)) - ex),
+                                         int(np.float32(c).view(np.uint32)) & 1))
+        assert r[i] == best, (i, r[i], best)
