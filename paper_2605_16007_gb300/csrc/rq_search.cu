@@ -1643,8 +1643,12 @@ rq_status search_run(rq_index* ix, const float* queries, int64_t nq, const int32
 
   const bool q_dev = is_device_ptr(queries);
   if (!q_dev) {
-    for (int64_t i = 0; i < nq * ix->dim; ++i)
-      if (!std::isfinite(queries[i])) return fail(RQ_ERR_INVALID_ARG, "non-finite query value");
+    // branch-free bit test (all-ones exponent: inf or NaN), so that the loop
+    // vectorises
+    const uint32_t* u = reinterpret_cast<const uint32_t*>(queries);
+    uint32_t bad = 0;
+    for (int64_t i = 0; i < nq * ix->dim; ++i) bad |= (uint32_t)((u[i] & 0x7f800000u) == 0x7f800000u);
+    if (bad) return fail(RQ_ERR_INVALID_ARG, "non-finite query value");
   }
   const bool ids_dev = is_device_ptr(out_ids), d_dev = is_device_ptr(out_dist);
 

@@ -315,10 +315,12 @@ def test_invalid_arguments_rejected(tiny):
         with pytest.raises(rq.RQError) as e:
             ix.search(q, *args)
         assert e.value.status == rq.RQ_ERR_INVALID_ARG
-    bad = q.copy()
-    bad[3, 5] = np.nan
-    with pytest.raises(rq.RQError):
-        ix.search(bad, 8, 10, 100)
+    for v in (np.nan, np.inf, -np.inf):
+        bad = q.copy()
+        bad[3, 5] = v
+        with pytest.raises(rq.RQError) as e:
+            ix.search(bad, 8, 10, 100)
+        assert e.value.status == rq.RQ_ERR_INVALID_ARG
     assert ix.device_error() == 0
 
 
