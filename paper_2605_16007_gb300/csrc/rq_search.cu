@@ -1198,10 +1198,10 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
   L.take(&ws.wtotal, nq);
   L.take(&ws.cand, nq * ws.cap);
   L.take(&ws.sel, nq * sh.nsel_max);
-  L.take(&ws.nprobe, nq);
-  L.take(&ws.kq, nq);
-  L.take(&ws.nsel, nq);
-  L.take(&ws.rerank_on, nq + 1);  // last entry: the no-prune flag
+  // the per-query parameters in one region (one copy from the pinned staging
+  // buffer, which has the same layout): nprobe, k, selection size, re-rank
+  // flag (+1: the no-prune flag)
+  L.take(&ws.nprobe, 4 * nq + 1);
   L.take(&ws.out_ids, nq * sh.k_stride);
   L.take(&ws.out_d, nq * sh.k_stride);
   if (sh.mode != RQ_SCAN_PLAIN) {
@@ -1240,9 +1240,9 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
   rebase(ws.cand, b);
   rebase(ws.sel, b);
   rebase(ws.nprobe, b);
-  rebase(ws.kq, b);
-  rebase(ws.nsel, b);
-  rebase(ws.rerank_on, b);
+  ws.kq = ws.nprobe + nq;
+  ws.nsel = ws.nprobe + 2 * nq;
+  ws.rerank_on = ws.nprobe + 3 * nq;
   rebase(ws.out_ids, b);
   rebase(ws.out_d, b);
   if (sh.mode != RQ_SCAN_PLAIN) {
@@ -1676,11 +1676,8 @@ rq_status search_run(rq_index* ix, const float* queries, int64_t nq, const int32
   std::memcpy(hp + nq, h_k.data(), sizeof(int32_t) * nq);
   std::memcpy(hp + 2 * nq, h_ns.data(), sizeof(int32_t) * nq);
   std::memcpy(hp + 3 * nq, h_rr.data(), sizeof(int32_t) * (nq + 1));
-  RQ_CUDA(cudaMemcpyAsync(ws.nprobe, hp, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, run_st));
-  RQ_CUDA(cudaMemcpyAsync(ws.kq, hp + nq, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, run_st));
-  RQ_CUDA(cudaMemcpyAsync(ws.nsel, hp + 2 * nq, sizeof(int32_t) * nq, cudaMemcpyHostToDevice, run_st));
-  RQ_CUDA(cudaMemcpyAsync(ws.rerank_on, hp + 3 * nq, sizeof(int32_t) * (nq + 1),
-                          cudaMemcpyHostToDevice, run_st));
+  RQ_CUDA(cudaMemcpyAsync(ws.nprobe, hp, sizeof(int32_t) * (4 * nq + 1), cudaMemcpyHostToDevice,
+                          run_st));
   RQ_CUDA(cudaEventRecord(plan->params_ready, run_st));
   RQ_CUDA(cudaMemcpyAsync(ws.q, queries, sizeof(float) * nq * ix->dim, cudaMemcpyDefault, run_st));
   if (use_graph) {
