@@ -78,7 +78,6 @@ struct Workspace {
   int32_t* wtotal = nullptr;    // nq: mask words of the query's probes
   uint64_t* cand = nullptr;     // nq x cap, cap = 32 mwords
   uint64_t* sel = nullptr;      // nq x nsel_max
-  uint64_t* io = nullptr;       // 3: addresses of this search's queries, ids, distances
   int32_t* nprobe = nullptr;    // nq
   int32_t* kq = nullptr;        // nq
   int32_t* nsel = nullptr;      // nq

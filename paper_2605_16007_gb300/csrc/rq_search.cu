@@ -400,16 +400,14 @@ scan_grouped_kernel(const int2* __restrict__ items, int n_items, int32_t* __rest
 // ---------------------------------------------------------------------------
 // Rotation q' = P^T q (float32 FMA): 8 queries x 64 output columns per
 // block, K in chunks of 128 staged in shared memory with every load of a
-// chunk in flight at once (16-byte loads when the rows allow). The queries'
-// address is read from device memory (*qsrc), so that one captured graph
-// serves every call. The first column of blocks also clears the search's
-// counters (zero0[n0], zero1[n1]) for the later stages.
+// chunk in flight at once (16-byte loads when the rows allow). The first
+// column of blocks also clears the search's counters (zero0[n0], zero1[n1])
+// for the later stages.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
-rotate_kernel8(const float* const* qsrc, int64_t nq, int dim, const float* __restrict__ P32,
+rotate_kernel8(const float* __restrict__ q, int64_t nq, int dim, const float* __restrict__ P32,
                int dp, float* __restrict__ qrot, int32_t* __restrict__ zero0, int n0,
                int32_t* __restrict__ zero1, int n1) {
-  const float* __restrict__ q = *qsrc;  // this search's queries (device memory)
   __shared__ __align__(16) float As[8][132];
   __shared__ __align__(16) float Bs[128][64];
   const int tid = threadIdx.x;
@@ -707,12 +705,8 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
                 int64_t mwords, uint64_t* __restrict__ cand, int32_t* __restrict__ counts,
                 const int32_t* __restrict__ nsel, const int32_t* __restrict__ kq,
                 const int32_t* __restrict__ rerank_on, int nsel_max, uint64_t* __restrict__ sel,
-                const RawT* __restrict__ raw, const uint64_t* __restrict__ io, int dim,
-                int k_stride, FinalizeLayout lay) {
-  // this search's query rows and result rows (device memory), read from io
-  const float* __restrict__ q = reinterpret_cast<const float*>(io[0]);
-  int64_t* __restrict__ out_ids = reinterpret_cast<int64_t*>(io[1]);
-  float* __restrict__ out_d = reinterpret_cast<float*>(io[2]);
+                const RawT* __restrict__ raw, const float* __restrict__ q, int dim, int k_stride,
+                FinalizeLayout lay, int64_t* __restrict__ out_ids, float* __restrict__ out_d) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ int s_ctl[8];
   __shared__ int s_part[4];
@@ -1207,7 +1201,7 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
   // the per-query parameters in one region (one copy from the pinned staging
   // buffer, which has the same layout): nprobe, k, selection size, re-rank
   // flag (+1: the no-prune flag)
-  L.take(&ws.nprobe, 8 + 4 * nq + 1);  // 8 ints up front: the io addresses
+  L.take(&ws.nprobe, 4 * nq + 1);
   L.take(&ws.out_ids, nq * sh.k_stride);
   L.take(&ws.out_d, nq * sh.k_stride);
   if (sh.mode != RQ_SCAN_PLAIN) {
@@ -1246,8 +1240,6 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
   rebase(ws.cand, b);
   rebase(ws.sel, b);
   rebase(ws.nprobe, b);
-  ws.io = reinterpret_cast<uint64_t*>(ws.nprobe);
-  ws.nprobe += 8;
   ws.kq = ws.nprobe + nq;
   ws.nsel = ws.nprobe + 2 * nq;
   ws.rerank_on = ws.nprobe + 3 * nq;
@@ -1363,8 +1355,7 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
   tm.mark(RQ_STAGE_ROTATE, st);
   const bool grouped = sh.mode != RQ_SCAN_PLAIN;
   rotate_kernel8<<<dim3(blocks_for(nq, 8), dp / 64), 256, 0, st>>>(
-      reinterpret_cast<const float* const*>(ws.io), nq, ix->dim, ix->P32, dp, ws.qrot,
-      grouped ? ws.list_count : nullptr,
+      ws.q, nq, ix->dim, ix->P32, dp, ws.qrot, grouped ? ws.list_count : nullptr,
       grouped ? ix->nlist : 0, grouped ? ws.work_count : nullptr, grouped ? 4 : 0);
   // 2. centroid ranking: approximate (filter of the certified selection)
   // where certified_probe holds, else exact
@@ -1416,13 +1407,13 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
     if (ix->raw_dtype == RQ_U8)
       finalize_kernel<uint8_t><<<(unsigned)nq, 128, smem, st>>>(
           ws.mask, ws.wtotal, ws.mwords, ws.cand, ws.counts, ws.nsel, ws.kq, ws.rerank_on,
-          sh.nsel_max, ws.sel, static_cast<const uint8_t*>(ix->raw), ws.io, ix->dim, sh.k_stride,
-          lay);
+          sh.nsel_max, ws.sel, static_cast<const uint8_t*>(ix->raw), ws.q, ix->dim, sh.k_stride, lay,
+          ws.out_ids, ws.out_d);
     else
       finalize_kernel<float><<<(unsigned)nq, 128, smem, st>>>(
           ws.mask, ws.wtotal, ws.mwords, ws.cand, ws.counts, ws.nsel, ws.kq, ws.rerank_on,
-          sh.nsel_max, ws.sel, static_cast<const float*>(ix->raw), ws.io, ix->dim, sh.k_stride,
-          lay);
+          sh.nsel_max, ws.sel, static_cast<const float*>(ix->raw), ws.q, ix->dim, sh.k_stride, lay,
+          ws.out_ids, ws.out_d);
   }
   tm.mark(RQ_STAGE_RERANK, st);
   tm.mark(RQ_STAGE_COUNT, st);
@@ -1468,7 +1459,7 @@ rq_status get_plan(rq_index* ix, cudaStream_t st, const SearchShape& sh, Plan** 
   p->shape = sh;
   p->stream = st;
   RQ_TRY(alloc_workspace(ix, sh, st, p->ws));
-  if (cudaMallocHost(&p->h_params, sizeof(int32_t) * (8 + 4 * sh.nq + 1)) != cudaSuccess) {
+  if (cudaMallocHost(&p->h_params, sizeof(int32_t) * (4 * sh.nq + 1)) != cudaSuccess) {
     cudaGetLastError();
     destroy_plan(p.get());
     return fail(RQ_ERR_OOM, "pinned parameter buffer");
@@ -1680,24 +1671,15 @@ rq_status search_run(rq_index* ix, const float* queries, int64_t nq, const int32
   // Per-query parameters go through the plan's pinned buffer; the previous
   // call's copy out of it must have run before it is overwritten.
   RQ_CUDA(cudaEventSynchronize(plan->params_ready));
-  // Device queries and results are read and written in place by the kernels
-  // (their addresses travel with the parameters); host ones go through the
-  // workspace with copies.
-  const bool out_in_place = ids_dev && d_dev;
-  const uint64_t io[3] = {(uint64_t)(q_dev ? queries : ws.q),
-                          (uint64_t)(out_in_place ? out_ids : ws.out_ids),
-                          (uint64_t)(out_in_place ? out_dist : ws.out_d)};
-  std::memcpy(plan->h_params, io, sizeof(io));
-  int32_t* hp = plan->h_params + 8;
+  int32_t* hp = plan->h_params;
+  std::memcpy(hp, h_np.data(), sizeof(int32_t) * nq);
   std::memcpy(hp + nq, h_k.data(), sizeof(int32_t) * nq);
   std::memcpy(hp + 2 * nq, h_ns.data(), sizeof(int32_t) * nq);
   std::memcpy(hp + 3 * nq, h_rr.data(), sizeof(int32_t) * (nq + 1));
-  RQ_CUDA(cudaMemcpyAsync(ws.io, plan->h_params, sizeof(int32_t) * (8 + 4 * nq + 1),
-                          cudaMemcpyHostToDevice, run_st));
+  RQ_CUDA(cudaMemcpyAsync(ws.nprobe, hp, sizeof(int32_t) * (4 * nq + 1), cudaMemcpyHostToDevice,
+                          run_st));
   RQ_CUDA(cudaEventRecord(plan->params_ready, run_st));
-  if (!q_dev)
-    RQ_CUDA(cudaMemcpyAsync(ws.q, queries, sizeof(float) * nq * ix->dim, cudaMemcpyHostToDevice,
-                            run_st));
+  RQ_CUDA(cudaMemcpyAsync(ws.q, queries, sizeof(float) * nq * ix->dim, cudaMemcpyDefault, run_st));
   if (use_graph) {
     if (!plan->graph) {
       cudaGraph_t g = nullptr;
@@ -1717,12 +1699,10 @@ rq_status search_run(rq_index* ix, const float* queries, int64_t nq, const int32
   } else {
     RQ_TRY(enqueue_search(ix, sh, ws, run_st, tm));
   }
-  if (!out_in_place) {
-    RQ_CUDA(cudaMemcpyAsync(out_ids, ws.out_ids, sizeof(int64_t) * nq * k_stride,
-                            cudaMemcpyDefault, run_st));
-    RQ_CUDA(cudaMemcpyAsync(out_dist, ws.out_d, sizeof(float) * nq * k_stride, cudaMemcpyDefault,
-                            run_st));
-  }
+  RQ_CUDA(cudaMemcpyAsync(out_ids, ws.out_ids, sizeof(int64_t) * nq * k_stride, cudaMemcpyDefault,
+                          run_st));
+  RQ_CUDA(cudaMemcpyAsync(out_dist, ws.out_d, sizeof(float) * nq * k_stride, cudaMemcpyDefault,
+                          run_st));
   if (dump) {
     const int W = ix->dp / 32;
     auto cp = [&](void* dst, const void* src, size_t bytes) -> rq_status {
