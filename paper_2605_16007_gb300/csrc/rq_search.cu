@@ -234,9 +234,10 @@ __device__ __forceinline__ void quantize_pair(int64_t pair, int64_t q, int c, in
 // Plain scan: one block per (query, probed list, chunk of kPlainChunk
 // vectors) -- the query-level schedule of Section 3.3.1, with long lists cut
 // into chunks so that they do not leave one block running alone. A thread
-// loads the codes of up to eight 128-vector steps before estimating them;
-// each warp writes the survivor mask word and the keys of its 32 vectors
-// (emit_word).
+// loads the codes of up to eight 128-vector steps before estimating them,
+// then the row ids of its passing vectors of all the steps at once (so that
+// no step's survivor write waits alone on its id load); each warp writes the
+// survivor mask word and the keys of its 32 vectors (emit_word).
 // ---------------------------------------------------------------------------
 constexpr int kPlainChunk = 1024;  // vectors of one list per block of the plain scan
 
@@ -280,23 +281,31 @@ scan_plain_kernel(const int32_t* __restrict__ nchunks, const int32_t* __restrict
         fv[r] = __ldg(fac + s);
       }
     }
+    float dv[RB];
+    uint32_t passm = 0;
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
-      const int64_t s0 = b0 + 128 * r;
-      if (s0 + warp * 32 >= end) break;  // warp-uniform: this word is past the chunk's end
-      const int64_t s = s0 + threadIdx.x;
-      bool pass = false;
-      float d = 0.0f;
+      const int64_t s = b0 + 128 * r + threadIdx.x;
+      dv[r] = 0.0f;
       if (s < end) {
         int pc = 0;
 #pragma unroll
         for (int w = 0; w < NW4; ++w)
           pc += __popc(code[r][w].x) + __popc(code[r][w].y) + __popc(code[r][w].z) +
                 __popc(code[r][w].w);
-        d = estimate_regs<NW4>(code[r], pc, fv[r], s_pl, qp, dp);
-        pass = orderable(d) <= tau;
+        dv[r] = estimate_regs<NW4>(code[r], pc, fv[r], s_pl, qp, dp);
+        if (orderable(dv[r]) <= tau) passm |= 1u << r;
       }
-      emit_word(pass, d, pass ? ids[s] : 0u, wrow + (s0 - lo) / 32 + warp, mask, cand, lane);
+    }
+    uint32_t idv[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+      idv[r] = (passm >> r) & 1u ? __ldg(ids + b0 + 128 * r + threadIdx.x) : 0u;
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const int64_t s0 = b0 + 128 * r;
+      if (s0 + warp * 32 >= end) break;  // warp-uniform: this word is past the chunk's end
+      emit_word((passm >> r) & 1u, dv[r], idv[r], wrow + (s0 - lo) / 32 + warp, mask, cand, lane);
     }
   }
 }
