@@ -15,8 +15,8 @@ step is timed with CUDA events on the stream the library launches on.
 Forms measured:
   value  -- batched search, scan mode chosen by the autotuner, launch
             sequence replayed from a CUDA graph;
-  plain  -- one thread block per (query, list), no graph (the query-level
-            schedule);
+  plain  -- one thread block per (query, list, 1024-vector chunk), no graph
+            (the query-level schedule);
   e2e    -- the same batched search with host buffers (query upload and
             result download inside the timed call);
   serving -- the continuous-batching server under a Poisson request stream.
