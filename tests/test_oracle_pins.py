@@ -100,6 +100,30 @@ def test_lane_sum_error_bound_and_small_cases():
     assert np.array_equal(R.lane_sum(v), v.astype(F64).sum(axis=1))
 
 
+def test_lane_sum_order_by_hand():
+    # 2^24 sits where float32 spacing is 2, so 2^24 + 1 rounds back to 2^24
+    # (ties to even) while 2^24 + 2 is exact. Terms 1 at d = 1 and d = 17
+    # meet first at the stride-16 step (lane 1 + lane 17 = 2), then join lane
+    # 0 at stride 1: 2^24 + 2. Summed in d order (or with adjacent lanes
+    # paired first) each 1 is lost against 2^24: 2^24.
+    v = np.zeros((1, 64), F32)
+    v[0, 0], v[0, 1], v[0, 17] = 2.0**24, 1.0, 1.0
+    assert R.lane_sum(v)[0] == 2.0**24 + 2
+    # terms of one lane (d = 1 and 33) add in increasing d before the tree
+    w = np.zeros((1, 64), F32)
+    w[0, 1], w[0, 33], w[0, 0] = 2.0**24, 1.0, 1.0
+    assert R.lane_sum(w)[0] == 2.0**24      # lane 1: 2^24 + 1 -> 2^24; + lane 0's 1 -> 2^24
+
+
+def test_seq_sqdist_order_by_hand():
+    # squares 2^24, 1, 1 added in d order: each 1 is lost (2^24 + 1 -> 2^24);
+    # any order that adds the two ones first gives 2^24 + 2
+    a = np.array([[4096.0, 1.0, 1.0]], F32)
+    assert R.seq_sqdist(a, np.zeros((1, 3), F32))[0, 0] == 2.0**24
+    b = np.array([[1.0, 1.0, 4096.0]], F32)
+    assert R.seq_sqdist(b, np.zeros((1, 3), F32))[0, 0] == 2.0**24 + 2
+
+
 def test_seq_sqdist_error_bound():
     rng = np.random.default_rng(3)
     a = rng.standard_normal((17, 128)).astype(F32)
@@ -345,6 +369,13 @@ def test_probe_all_lists_and_fp64_order(tiny):
     assert np.array_equal(ids[gap_ok], ref[gap_ok])
 
 
+def test_probe_ties_go_to_lower_id():
+    # duplicate centroids: equal distances, the lower id is taken first
+    cR = np.array([[1.0, 0.0], [0.0, 0.0], [1.0, 0.0], [0.0, 0.0], [3.0, 0.0]], F32)
+    ids, d = R.probe(np.zeros((1, 2), F32), cR, 4)
+    assert list(ids[0]) == [1, 3, 0, 2] and list(d[0]) == [0.0, 0.0, 1.0, 1.0]
+
+
 def test_prune_is_lossless_including_ties():
     rng = np.random.default_rng(12)
     d = rng.integers(0, 50, 5000).astype(F32)   # many exact ties
@@ -355,6 +386,14 @@ def test_prune_is_lossless_including_ties():
         assert np.array_equal(a, b)
         full = sorted(zip(d.tolist(), ids.tolist()))[:n_sel]
         assert [int(i) for i in R.key_id(a)] == [i for _, i in full]
+    # distinct estimates, nearest first (the probe order puts the closest
+    # lists first): the first candidates hold the n_sel smallest, so a bound
+    # one rank too low would drop the n_sel-th
+    d = np.arange(5000).astype(F32)
+    for n_sel in (1, 2, 10, 1024, 1025, 3000):
+        a = R.select_candidates(d, ids, n_sel, prune=True)
+        assert np.array_equal(a, R.select_candidates(d, ids, n_sel, prune=False))
+        assert np.array_equal(R.key_id(a), ids[:n_sel])
 
 
 def test_rerank_matches_fp64_and_pads():
