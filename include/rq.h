@@ -275,9 +275,9 @@ RQ_API rq_status rq_device_error(rq_index* ix, int32_t* code);
 /* rq_probe_static -- the query rotation and centroid ranking of rq_search
  * (q' = P^T q, then the nprobe lists of smallest ||q' - P^T c||^2, ties by
  * list id), for callers that cannot allocate device memory when they search:
- * code inside a CUDA stream capture it does not own, processes whose
- * framework owns all device memory through its own allocator, and serving
- * threads that cannot take the device synchronisation of cudaMalloc/cudaFree.
+ * processes whose framework hands all device memory to its own allocator (a
+ * cudaMalloc of ours would compete with it or fail), and serving threads that
+ * cannot take the device-wide synchronisation of cudaMalloc/cudaFree.
  * The paper has no counterpart: it is an interface variant of Phase 1 of the
  * search, which the paper runs as a batch on the NPU.
  * It allocates nothing: its scratch (the rotated queries and the distance

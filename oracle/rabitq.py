@@ -405,6 +405,34 @@ def first_bound(d2: np.ndarray, n_sel: int, cap: int = BOUND_CANDIDATES):
     return int(np.sort(orderable(d2[:m]))[n_sel - 1])
 
 
+def select_running_bound(d2, ids, n_sel: int):
+    """The paper's Top-k with a running upper bound (Section 3.3.3), written
+    out one candidate at a time: candidates arrive in probe order (lists by
+    ascending centroid distance); once n_sel keys are held, the bound is the
+    largest held key, a candidate above it is pruned, and one below it
+    replaces the held maximum. Returns the held keys ascending and how many
+    candidates were pruned.
+
+    The first-bound form used by ``select_candidates`` (one bound fixed from
+    the first candidates) is a different schedule of the same idea; both
+    return the n_sel smallest keys.
+    """
+    keys = make_keys(d2, ids)
+    held: list[int] = []
+    pruned = 0
+    for key in (int(v) for v in keys):
+        if len(held) < n_sel:
+            held.append(key)
+            continue
+        top = max(held)
+        if key > top:
+            pruned += 1
+            continue
+        held.remove(top)
+        held.append(key)
+    return np.array(sorted(held), np.uint64), pruned
+
+
 def select_candidates(d2, ids, n_sel: int, prune: bool = True):
     """The n_sel smallest (distance, id) keys, ascending.
 

@@ -285,8 +285,21 @@ class Index:
 
     def rq_probe_static(self, queries, nprobe: int, out_ids, out_dist, stream=None):
         """Rotation + centroid ranking without any allocation (device arrays
-        only); see rq_probe_static in include/rq.h."""
-        _check(lib().rq_probe_static(self.h, _ptr(queries), _shape(queries)[0], nprobe,
+        only); see rq_probe_static in include/rq.h.
+
+        The C entry point sees bare pointers, so the shapes, dtypes and
+        device are checked here: queries a contiguous float32 CUDA tensor of
+        shape (nq, dim), out_ids int32 and out_dist float32 CUDA tensors of
+        shape (nq, nprobe), all on the current device (the library checks
+        that the current device holds the index)."""
+        import torch
+
+        dev = torch.cuda.current_device()
+        nq = _shape(queries)[0] if hasattr(queries, "shape") else -1
+        _require_cuda(queries, "queries", "torch.float32", (nq, self.stats()["dim"]), dev)
+        _require_cuda(out_ids, "out_ids", "torch.int32", (nq, nprobe), dev)
+        _require_cuda(out_dist, "out_dist", "torch.float32", (nq, nprobe), dev)
+        _check(lib().rq_probe_static(self.h, _ptr(queries), nq, nprobe,
                                      _ptr(out_ids), _ptr(out_dist), _stream_ptr(stream)))
         return out_ids, out_dist
 
@@ -362,14 +375,26 @@ class Index:
             pass
 
 
+def _require_cuda(t, name, dtype, shape, device):
+    """Raises ValueError unless t is a contiguous CUDA tensor of the given
+    dtype (as its str) and shape on CUDA device `device`."""
+    if not (hasattr(t, "is_cuda") and t.is_cuda):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if str(t.dtype) != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, not {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, not {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.device.index != device:
+        raise ValueError(f"{name} is on cuda:{t.device.index}, the index on cuda:{device}")
+
+
 _cudart = None
 
 
-def memcpy_d2h(dst: np.ndarray, src_ptr: int):
-    """Copy device memory at src_ptr into the host array dst (CUDA runtime)."""
+def _load_cudart():
     global _cudart
-    if dst.nbytes == 0:
-        return
     if _cudart is None:
         import torch  # noqa: F401  (loads the CUDA runtime library)
         for name in ("libcudart.so.13", "libcudart.so.12", "libcudart.so"):
@@ -382,7 +407,14 @@ def memcpy_d2h(dst: np.ndarray, src_ptr: int):
             raise RuntimeError("CUDA runtime library not found")
         _cudart.cudaMemcpy.restype = C.c_int
         _cudart.cudaMemcpy.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]
-    rc = _cudart.cudaMemcpy(C.c_void_p(dst.ctypes.data), C.c_void_p(src_ptr), dst.nbytes, 4)
+    return _cudart
+
+
+def memcpy_d2h(dst: np.ndarray, src_ptr: int):
+    """Copy device memory at src_ptr into the host array dst (CUDA runtime)."""
+    if dst.nbytes == 0:
+        return
+    rc = _load_cudart().cudaMemcpy(C.c_void_p(dst.ctypes.data), C.c_void_p(src_ptr), dst.nbytes, 4)
     if rc != 0:
         raise RuntimeError(f"cudaMemcpy failed with {rc}")
 

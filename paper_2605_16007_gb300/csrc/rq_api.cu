@@ -8,6 +8,8 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <set>
+#include <tuple>
 #include <string>
 #include <thread>
 #include <unordered_map>
@@ -34,6 +36,18 @@ rq_status cuda_fail(cudaError_t e, const char* what, const char* file, int line)
   set_error(std::string(what) + ": " + cudaGetErrorString(e) + " (" + (base ? base + 1 : file) +
             ":" + std::to_string(line) + ")");
   return (e == cudaErrorMemoryAllocation) ? RQ_ERR_OOM : RQ_ERR_CUDA;
+}
+
+rq_status allow_dynamic_smem(const void* func, int bytes) {
+  static std::mutex mu;
+  static std::set<std::tuple<const void*, int, int>> done;  // (kernel, device, bytes)
+  int dev = 0;
+  RQ_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count(std::make_tuple(func, dev, bytes))) return RQ_OK;
+  RQ_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.insert(std::make_tuple(func, dev, bytes));
+  return RQ_OK;
 }
 
 namespace {

@@ -170,4 +170,9 @@ void free_plans(rq_index* ix);
 // Memory residence
 bool is_device_ptr(const void* p);
 
+// Lets kernel `func` take up to `bytes` of dynamic shared memory on the
+// current device. The opt-in above 48 KB is a per-device attribute, so it is
+// set once per (kernel, device); safe to call from several threads.
+rq_status allow_dynamic_smem(const void* func, int bytes);
+
 }  // namespace rq

@@ -519,12 +519,7 @@ bool mma_supported(const rq_index* ix) { return ix->dp == kMmaK; }
 rq_status launch_scan_mma(rq_index* ix, const SearchShape& sh, Workspace& ws, cudaStream_t st,
                           int sms) {
   if (ix->dp != kMmaK) return fail(RQ_ERR_NOT_IMPLEMENTED, "tensor-core scan built for D_p = 128");
-  static bool attr_set = false;
-  if (!attr_set) {
-    RQ_CUDA(cudaFuncSetAttribute(scan_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kSmAlloc));
-    attr_set = true;
-  }
+  RQ_TRY(allow_dynamic_smem((const void*)scan_mma_kernel, kSmAlloc));
   // Three blocks per SM (registers; ~69 KB of shared memory each); their
   // TMEM (128 columns each) stays within the SM's 512 columns.
   scan_mma_kernel<<<(unsigned)(sms * 3), kMmaThreads, kSmAlloc, st>>>(

@@ -1323,12 +1323,7 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
     const int kpw = std::max(kBoundCandidates, sh.nsel_max);
     const size_t smem =
         (size_t)std::max(2, next_pow2_host(np)) * 8 + std::max<size_t>(stage, (size_t)kpw * 4);
-    static bool attr = false;
-    if (!attr) {
-      RQ_CUDA(cudaFuncSetAttribute(prep_kernel<NW4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   200 * 1024));
-      attr = true;
-    }
+    RQ_TRY(allow_dynamic_smem((const void*)prep_kernel<NW4>, 200 * 1024));
     prep_kernel<NW4><<<(unsigned)nq, 128, smem, st>>>(a);
   }
   tm.mark(RQ_STAGE_BOUND, st);
@@ -1371,12 +1366,8 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
   tm.mark(RQ_STAGE_PROBE, st);
   if (certified_probe(ix)) {
     const size_t smem = (size_t)2 * dp * kApproxLd * sizeof(float);
-    static bool attr = false;
-    if (!attr) {
-      RQ_CUDA(cudaFuncSetAttribute(approx_dist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(2 * kApproxMaxDp * kApproxLd * sizeof(float))));
-      attr = true;
-    }
+    RQ_TRY(allow_dynamic_smem((const void*)approx_dist_kernel,
+                              (int)(2 * kApproxMaxDp * kApproxLd * sizeof(float))));
     approx_dist_kernel<<<dim3(blocks_for(nq, 64), blocks_for(ix->nlist, 64)), 256, smem, st>>>(
         ws.qrot, nq, ix->cR, ix->nlist, dp, reinterpret_cast<float*>(ws.pkeys), ws.cn);
   } else {
@@ -1405,14 +1396,8 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
     const FinalizeLayout lay{next_pow2_host(sh.nsel_max), next_pow2_host(sh.k_stride), 2048,
                              ix->dim};
     const size_t smem = lay.bytes();
-    static bool attr = false;
-    if (!attr) {
-      RQ_CUDA(cudaFuncSetAttribute(finalize_kernel<uint8_t>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      RQ_CUDA(cudaFuncSetAttribute(finalize_kernel<float>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      attr = true;
-    }
+    RQ_TRY(allow_dynamic_smem((const void*)finalize_kernel<uint8_t>, 200 * 1024));
+    RQ_TRY(allow_dynamic_smem((const void*)finalize_kernel<float>, 200 * 1024));
     if (ix->raw_dtype == RQ_U8)
       finalize_kernel<uint8_t><<<(unsigned)nq, 128, smem, st>>>(
           ws.mask, ws.wtotal, ws.mwords, ws.cand, ws.counts, ws.nsel, ws.kq, ws.rerank_on,
@@ -1525,18 +1510,49 @@ rq_status autotune(rq_index* ix, const float* queries, int64_t nq, int nprobe, i
     }
   }
   const int k = n_rerank > 0 ? std::min(10, n_rerank) : 10;
-  int64_t* d_ids = nullptr;
-  float* d_d = nullptr;
-  float* d_q = nullptr;
-  RQ_CUDA(cudaMalloc(&d_ids, sizeof(int64_t) * nq * k));
-  RQ_CUDA(cudaMalloc(&d_d, sizeof(float) * nq * k));
-  RQ_CUDA(cudaMalloc(&d_q, sizeof(float) * nq * ix->dim));
-  RQ_CUDA(cudaMemcpy(d_q, queries, sizeof(float) * nq * ix->dim, cudaMemcpyDefault));
-  cudaStream_t st;
-  RQ_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  // Everything this call creates is released on every exit path.
+  struct Scratch {
+    rq_index* ix = nullptr;
+    int64_t* d_ids = nullptr;
+    float* d_d = nullptr;
+    float* d_q = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~Scratch() {
+      if (st) {
+        cudaStreamSynchronize(st);
+        // the plans made for this stream go with it
+        std::lock_guard<std::mutex> lk(ix->mu);
+        for (auto it = ix->plans.begin(); it != ix->plans.end();) {
+          if (it->first.first == st) {
+            destroy_plan(it->second.get());
+            it = ix->plans.erase(it);
+          } else {
+            ++it;
+          }
+        }
+      }
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      if (st) cudaStreamDestroy(st);
+      if (d_ids) cudaFree(d_ids);
+      if (d_d) cudaFree(d_d);
+      if (d_q) cudaFree(d_q);
+    }
+  } sc;
+  sc.ix = ix;
+  RQ_CUDA(cudaMalloc(&sc.d_ids, sizeof(int64_t) * nq * k));
+  RQ_CUDA(cudaMalloc(&sc.d_d, sizeof(float) * nq * k));
+  RQ_CUDA(cudaMalloc(&sc.d_q, sizeof(float) * nq * ix->dim));
+  RQ_CUDA(cudaMemcpy(sc.d_q, queries, sizeof(float) * nq * ix->dim, cudaMemcpyDefault));
+  RQ_CUDA(cudaStreamCreateWithFlags(&sc.st, cudaStreamNonBlocking));
+  RQ_CUDA(cudaEventCreate(&sc.e0));
+  RQ_CUDA(cudaEventCreate(&sc.e1));
+  cudaStream_t st = sc.st;
+  cudaEvent_t e0 = sc.e0, e1 = sc.e1;
+  int64_t* d_ids = sc.d_ids;
+  float* d_d = sc.d_d;
+  float* d_q = sc.d_q;
   std::vector<int32_t> a(nq, nprobe), b(nq, k), c(nq, n_rerank);
   int best_mode = RQ_SCAN_GROUPED;
   float best_ms = 1e30f;
@@ -1563,24 +1579,6 @@ rq_status autotune(rq_index* ix, const float* queries, int64_t nq, int nprobe, i
       best_mode = mode;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  {
-    std::lock_guard<std::mutex> lk(ix->mu);
-    for (auto it = ix->plans.begin(); it != ix->plans.end();) {
-      if (it->first.first == st) {
-        destroy_plan(it->second.get());
-        it = ix->plans.erase(it);
-      } else {
-        ++it;
-      }
-    }
-  }
-  cudaStreamSynchronize(st);
-  cudaStreamDestroy(st);
-  cudaFree(d_ids);
-  cudaFree(d_d);
-  cudaFree(d_q);
   if (s != RQ_OK) return s;
   ix->auto_mode.store(best_mode);
   if (cache_path) {
@@ -1753,12 +1751,10 @@ rq_status search_run(rq_index* ix, const float* queries, int64_t nq, const int32
 // ===========================================================================
 // Allocation-free variant of the query rotation and centroid ranking.
 //
-// Some callers cannot allocate device memory at the moment they search: code
-// running inside a CUDA stream capture owned by someone else (an allocation
-// there fails or becomes part of their graph), processes whose framework
-// hands all device memory to its own caching allocator, and latency-critical
-// serving threads that cannot afford the implicit device synchronisation of
-// cudaMalloc / cudaFree. For them, rq_probe_static keeps its scratch (the
+// Some callers cannot allocate device memory at the moment they search:
+// processes whose framework hands all device memory to its own caching
+// allocator, and latency-critical serving threads that cannot afford the
+// implicit device synchronisation of cudaMalloc / cudaFree. For them, rq_probe_static keeps its scratch (the
 // rotated queries and the distance keys) in one fixed array in device memory
 // that exists for as long as the library is loaded.
 // ===========================================================================

@@ -101,6 +101,20 @@ CASES = {
                                                [P.test_update_is_mean_and_reseeds_empty]),
     "kmeans_init: largest keys": (R, "kmeans_init", "rows[np.argsort(keys)[:nlist]]",
                                   "rows[np.argsort(keys)[::-1][:nlist]]", [P.test_kmeans_init_is_smallest_keys]),
+    "train_rows: largest keys": (R, "train_rows", "np.argsort(keys)[:n_train]",
+                                 "np.argsort(keys)[::-1][:n_train]", [P.test_train_rows_are_smallest_keys]),
+    "train_rows: k-means init stream": (R, "train_rows", "philox.STREAM_TRAIN_SAMPLE",
+                                        "philox.STREAM_KMEANS_INIT", [P.test_train_rows_are_smallest_keys]),
+    # ground truth and recall
+    "recall_at: strict comparison": (R, "recall_at", "<= kth * (1 + 1e-12)", "< kth * (1 - 1e-12)",
+                                     [P.test_exact_dist_and_recall_by_hand]),
+    "recall_at: padded ids count as hits": (R, "recall_at", "nan=np.inf", "nan=0.0",
+                                            [P.test_exact_dist_and_recall_by_hand]),
+    "recall_at: first true distance": (R, "recall_at", "true_dist[:, k - 1]", "true_dist[:, 0]",
+                                          [P.test_exact_dist_and_recall_by_hand]),
+    "exact_dist: absolute instead of squared": (R, "exact_dist", "(diff * diff).sum(axis=1)",
+                                                "np.abs(diff).sum(axis=1)",
+                                                [P.test_exact_dist_and_recall_by_hand]),
     # keys, probe, pruning, selection, re-rank
     "orderable: negatives not inverted": (R, "orderable", "np.where(neg, u ^ np.uint64(0xFFFFFFFF)",
                                           "np.where(neg, u ^ np.uint64(0x80000000)",
@@ -113,6 +127,12 @@ CASES = {
                                         [P.test_prune_is_lossless_including_ties]),
     "first_bound: one rank early": (R, "first_bound", "[n_sel - 1])", "[max(0, n_sel - 2)])",
                                     [P.test_prune_is_lossless_including_ties]),
+    "select_running_bound: bound is the held minimum": (R, "select_running_bound", "top = max(held)",
+                                                        "top = min(held)",
+                                                  [P.test_running_bound_form_equals_first_bound_form]),
+    "select_running_bound: keeps the maximum": (R, "select_running_bound", "held.remove(top)",
+                                                "held.remove(min(held))",
+                                                [P.test_running_bound_form_equals_first_bound_form]),
     "rerank: absolute instead of squared": (R, "rerank", "d = lane_sum(diff * diff)", "d = lane_sum(np.abs(diff))",
                                             [P.test_rerank_matches_fp64_and_pads]),
     "list_candidates: residual sign": (R, "list_candidates", 'quantize((qrot_i - index["cR"][c])[None, :])',

@@ -152,6 +152,21 @@ def test_train_subset():
     assert np.array_equal(R.train_rows(9, 1000, 0), np.arange(1000))
 
 
+def test_train_rows_are_smallest_keys():
+    """The training subset is the n_train rows whose Philox word (stream 3)
+    is smallest, ties by row, returned in ascending row order -- checked by
+    ranking the rows here one by one from the raw generator output."""
+    n, n_train, seed = 257, 40, 21
+    w0 = philox.stream_block(seed, philox.STREAM_TRAIN_SAMPLE, np.arange(n))[:, 0]
+    ranked = sorted(range(n), key=lambda i: (int(w0[i]), i))
+    assert list(R.train_rows(seed, n, n_train)) == sorted(ranked[:n_train])
+    # the largest keys, or another stream's keys, give another subset
+    assert sorted(ranked[-n_train:]) != sorted(ranked[:n_train])
+    w_init = philox.stream_block(seed, philox.STREAM_KMEANS_INIT, np.arange(n))[:, 0]
+    other = sorted(sorted(range(n), key=lambda i: (int(w_init[i]), i))[:n_train])
+    assert list(R.train_rows(seed, n, n_train)) != other
+
+
 def test_update_is_mean_and_reseeds_empty():
     # 1-D example worked by hand: centroids 0, 0 (duplicate), 10.
     x = np.array([[-1.0], [1.0], [2.0], [9.0], [11.0], [30.0]], F32)
@@ -396,6 +411,34 @@ def test_prune_is_lossless_including_ties():
         assert np.array_equal(R.key_id(a), ids[:n_sel])
 
 
+def test_running_bound_form_equals_first_bound_form():
+    """Section 3.3.3 keeps a running bound (the largest of the current top
+    n_sel) while candidates arrive in probe order; the search fixes one bound
+    from the first candidates instead. Both schedules, and no pruning at
+    all, select the same n_sel smallest (distance, id) keys, ties included;
+    the running bound prunes a candidate only when it exceeds the held
+    maximum."""
+    rng = np.random.default_rng(31)
+    for trial in range(6):
+        m = int(rng.integers(1, 3000))
+        if trial % 2:
+            d = rng.integers(0, 40, m).astype(F32)          # many ties
+        else:
+            d = np.sort(rng.standard_normal(m).astype(F32))  # nearest first
+            d += rng.standard_normal(m).astype(F32)
+        ids = rng.permutation(m)
+        for n_sel in (1, 7, 100, 1500):
+            run, pruned = R.select_running_bound(d, ids, n_sel)
+            assert np.array_equal(run, R.select_candidates(d, ids, n_sel, prune=True))
+            assert np.array_equal(run, R.select_candidates(d, ids, n_sel, prune=False))
+            assert 0 <= pruned <= max(0, m - n_sel)
+    # by hand: keys arrive 5, 3, 9, 1, 9, 2 (ids 0..5); n_sel 2 holds {5, 3},
+    # then 9 > 5 is pruned, 1 replaces 5, the second 9 > 3 is pruned, 2
+    # replaces 3
+    run, pruned = R.select_running_bound(np.array([5, 3, 9, 1, 9, 2], F32), np.arange(6), 2)
+    assert R.key_id(run).tolist() == [3, 5] and pruned == 2
+
+
 def test_rerank_matches_fp64_and_pads():
     rng = np.random.default_rng(13)
     raw = rng.integers(0, 256, (100, 128)).astype(F32)
@@ -426,6 +469,30 @@ def test_exact_knn_brute_force():
         d = ((x.astype(F64) - q[i]) ** 2).sum(1)
         ref = sorted(range(200), key=lambda j: (d[j], j))[:7]
         assert list(ids[i]) == ref
+
+
+def test_exact_dist_and_recall_by_hand():
+    """Tie-aware recall@k worked by hand. Query 0 at 0 against rows
+    0, 1, 2, 2, 3, 5 has squared distances 0, 1, 4, 4, 9, 25: its true top 3
+    are rows 0, 1, 2 and the 3rd true distance is 4, which row 3 ties.
+    Query 1 at 5: distances 25, 16, 9, 9, 4, 0, 3rd true distance 9."""
+    x = np.array([[0.0], [1.0], [2.0], [2.0], [3.0], [5.0]], F32)
+    q = np.array([[0.0], [5.0]], F32)
+    ti, td = R.exact_knn(x, q, 3)
+    assert ti.tolist() == [[0, 1, 2], [5, 4, 2]] and td[:, 2].tolist() == [4.0, 9.0]
+    d = R.exact_dist(x, q, np.array([[0, 1, 2, -1], [5, 4, 3, 0]]))
+    assert d[0, :3].tolist() == [0.0, 1.0, 4.0] and np.isnan(d[0, 3])
+    assert d[1].tolist() == [0.0, 4.0, 9.0, 25.0]
+    cases = [
+        ([[0, 1, 3], [5, 4, 3]], 1.0),      # row 3 ties the 3rd distance: a hit
+        ([[3, 2, 1], [5, 4, 2]], 1.0),      # at the 3rd distance counts (<=, not <)
+        ([[0, 1, 4], [5, 4, 2]], 5 / 6),    # row 4 (9 > 4) misses
+        ([[0, -1, 2], [5, 4, 2]], 5 / 6),   # a padded id misses
+        ([[0, 1, 2], [5, 4, 0]], 5 / 6),    # row 0 for query 1 (25 > 9) misses
+        ([[-1, -1, -1], [-1, -1, -1]], 0.0),
+    ]
+    for ids, want in cases:
+        assert R.recall_at(x, q, np.array(ids), td, 3) == pytest.approx(want), ids
 
 
 def test_recall_target_on_tiny_workload():

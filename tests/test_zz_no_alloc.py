@@ -1,8 +1,8 @@
 """rq_probe_static: the allocation-free rotation + centroid ranking.
 
 It exists for callers that cannot allocate device memory while they search
-(inside a stream capture they do not own, under a framework that owns all
-device memory, or on a latency-critical thread). Its scratch is a fixed
+(under a framework that owns all device memory, or on a latency-critical
+thread that cannot take cudaMalloc's device synchronisation). Its scratch is a fixed
 device array shared by all calls, so the test checks it twice in a row --
 the second call sees the first call's leftovers -- against the probe stage
 of the existing rq_search entry point, bit for bit (the tolerance the other
@@ -57,6 +57,37 @@ def test_probe_static_refuses_oversized_and_host_buffers(setup):
     with pytest.raises(rq.RQError) as e:
         ix.probe_static(qd, 4, ids, dist)
     assert e.value.status == rq.RQ_ERR_INVALID_ARG and "scratch" in str(e.value)
-    with pytest.raises(rq.RQError) as e:
+    with pytest.raises(ValueError):
         ix.probe_static(q[:4], 4, np.empty((4, 4), np.int32), np.empty((4, 4), np.float32))
-    assert e.value.status == rq.RQ_ERR_INVALID_ARG
+    # the C entry point itself refuses host pointers
+    import ctypes as C
+    qh = np.ascontiguousarray(q[:4])
+    oi, od = np.empty((4, 4), np.int32), np.empty((4, 4), np.float32)
+    st = rq.lib().rq_probe_static(ix.h, rq._ptr(qh), 4, 4, rq._ptr(oi), rq._ptr(od), None)
+    assert st == rq.RQ_ERR_INVALID_ARG
+
+
+def test_probe_static_wrapper_checks_shapes_and_dtypes(setup):
+    """The C entry point sees bare pointers; the binding refuses buffers whose
+    shape, dtype or residence would make the kernels read or write out of
+    bounds, before anything is launched."""
+    rq, ix, q = setup
+    dev = "cuda"
+    qd = torch.from_numpy(np.ascontiguousarray(q[:8])).to(dev)
+    good_i = torch.empty((8, 4), dtype=torch.int32, device=dev)
+    good_d = torch.empty((8, 4), dtype=torch.float32, device=dev)
+    bad = [
+        (qd[:, :64].contiguous(), good_i, good_d),                       # width != dim
+        (qd.double(), good_i, good_d),                                   # float64 queries
+        (qd, torch.empty((8, 3), dtype=torch.int32, device=dev), good_d),  # too few columns
+        (qd, torch.empty((8, 4), dtype=torch.int64, device=dev), good_d),  # int64 ids
+        (qd, good_i, torch.empty((8, 4), dtype=torch.float64, device=dev)),
+        (qd, good_i, torch.empty((7, 4), dtype=torch.float32, device=dev)),
+        (qd.t().contiguous().t(), good_i, good_d),                       # not contiguous
+        (qd.cpu(), good_i, good_d),                                      # host queries
+    ]
+    for a, b, c in bad:
+        with pytest.raises(ValueError):
+            ix.probe_static(a, 4, b, c)
+    ix.probe_static(qd, 4, good_i, good_d)
+    torch.cuda.synchronize()
