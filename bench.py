@@ -1,28 +1,40 @@
 #!/usr/bin/env python
 """Benchmark: IVF-RaBitQ search throughput at recall@10 >= 0.95 on one GB300.
 
-Workload: the SIFT1M-shaped recipe of ``workloads`` (1,000,000 x 128
-integer-valued float32 vectors, nlist 1024, 10,000 queries in batches of
-1000, k 10, n_rerank 200, B_q 4). The nprobe sweep {16, 32, 64, 128} picks
-the cheapest nprobe whose recall@10 (tie-aware, against exact kNN) reaches
-0.95; throughput is measured there.
+Headline workload: the skewed recipe of ``workloads`` at full size --
+10,000,000 x 96 unit vectors (D_p 128) from a 1024-component mixture with
+Zipf (s = 1) component weights, nlist 4096 (k-means: 10 iterations on a
+training sample of 64 x nlist rows). IVF list lengths vary by more than 100x
+and the probed lists do not fit in L2. A pool of 8192 queries from the same
+mixture carries per-query parameters: nprobe = scale x U{8..256} (capped at
+nlist), k in {10, 100}, and one n_rerank per setting. The sweep over
+(scale, n_rerank) settings, cheapest first, takes the first whose recall@10
+(tie-aware, against the exact kNN of the whole pool) reaches 0.95, and every
+form is measured there.
 
-One step = one batch of 1000 queries through the whole search path (rotate,
-probe, quantise, bound, scan, select, re-rank). Inputs and the index are
-resident in HBM; L2 is flushed (a 256 MiB write) between timed steps and each
-step is timed with CUDA events on the stream the library launches on.
+One step = one batch of the schedule 64, 4096, 256, 1024, 128, 2048, 512
+queries (cycled) through the whole search path: rotate, probe, quantise,
+bound, scan, select + re-rank. Inputs and the index are resident in HBM; L2
+is flushed (a 256 MiB write) before each timed step; each step is timed with
+CUDA events on the stream the library launches on.
 
 Forms measured:
-  value  -- batched search, scan mode chosen by the autotuner, launch
-            sequence replayed from a CUDA graph;
-  plain  -- one thread block per (query, list, 1024-vector chunk), no graph
-            (the query-level schedule);
-  e2e    -- the same batched search with host buffers (query upload and
-            result download inside the timed call);
-  serving -- the continuous-batching server under a Poisson request stream.
+  value    -- batched: scan form chosen per batch class by the autotuner,
+              launch sequence replayed from a CUDA graph;
+  plain    -- one thread block per (query, list, 1024-vector chunk), no graph
+              (the query-level schedule);
+  e2e      -- the batched search through the C ABI with host buffers (query
+              upload, per-query parameters and result download inside the
+              timed call);
+  serving  -- the continuous-batching server: Poisson arrivals of 1-64-query
+              requests with their own nprobe and k (p50/p99 latency), and the
+              server kept busy with 256-query requests.
+A secondary key measures the SIFT1M-shaped recipe (1,000,000 x 128
+integer-valued vectors, nlist 1024, batches of 1000, nprobe sweep).
 
-``--impl reference`` times the CPU oracle's search on the same workload
-instead (a bounded sample of queries per step).
+``--impl reference`` times the CPU oracle on the same workload instead, in a
+process that never loads the CUDA library: its own float64 index build (not
+timed), then its search on every host core.
 """
 from __future__ import annotations
 
@@ -33,7 +45,6 @@ import os
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 import numpy as np
@@ -43,62 +54,82 @@ sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
 
-WORKLOAD = "sift1m"
 METRIC = "QPS at recall@10>=0.95 (served vs plain batched), p50/p99 ms, scan HBM GB/s"
 RECALL_TARGET = 0.95
-REFERENCE_NPROBE = 16
 FLUSH_BYTES = 256 << 20
 # Popcount issue rate per SM per clock (32-bit POPC; the CUDA C++ guide's
 # arithmetic-throughput class for integer population count), 152 SMs.
 POPC_PER_SM_CLK = 16
 SMS = 152
+SM_MHZ = 2070.0
+
+# The skewed headline workload.
+SKEW_POOL = 8192
+SKEW_BATCHES = (64, 4096, 256, 1024, 128, 2048, 512)
+SKEW_TRAIN = 64 * 4096
+SKEW_PARAM_SEED = 11
+# (nprobe scale, n_rerank), in order of cost; the first to reach the recall
+# target is measured. The reference arm runs the setting the GPU arm's sweep
+# settles on for this workload (recorded here from that sweep).
+SKEW_SETTINGS = ((1, 1000), (2, 1000), (1, 2000), (2, 2000), (4, 2000), (4, 4000))
+SKEW_REFERENCE_SETTING = (2, 1000)
 
 # DRAM traffic of one scan launch from an ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum), keyed by kernel; valid only while the kernel source
-# hash matches the one recorded at capture time.
-TRAFFIC = {"scan:sift1m:2333b74c9e8dbbfe": 31981312}
+# dram__bytes_write.sum), keyed by kernel and case; valid only while the
+# hash of the kernel's sources matches the one recorded at capture time.
+TRAFFIC = {}
 
 
-def measured_bf16_tflops() -> float:
-    """Dense bf16 peak measured on this machine (burst), else the stated fallback."""
+def measured_peaks() -> dict:
+    """Peaks measured on this machine (MEASURED_PEAKS.json), else the stated
+    fallback (6.8 TB/s copy, 1.9 PFLOP/s dense bf16)."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            return float(json.load(fh)["bf16_tflops"])
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "source": "measured"}
     except (OSError, KeyError, ValueError):
-        return 1900.0
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
 
-def kernel_source_hash() -> str:
-    """Hash of the sources the tensor-core scan kernel is compiled from (its
-    translation unit and the headers it includes)."""
+def kernel_source_hash(files) -> str:
     h = hashlib.sha256()
-    for f in ("paper_2605_16007_gb300/csrc/rq_scan_mma.cu", "paper_2605_16007_gb300/csrc/rq_scan.cuh",
-              "paper_2605_16007_gb300/csrc/rq_common.cuh", "paper_2605_16007_gb300/csrc/rq_internal.h",
-              "include/rq.h"):
+    for f in files:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def parse():
+SCAN_SOURCES = {
+    "plain": ("paper_2605_16007_gb300/csrc/rq_search.cu", "paper_2605_16007_gb300/csrc/rq_scan.cuh",
+              "paper_2605_16007_gb300/csrc/rq_common.cuh"),
+    "grouped": ("paper_2605_16007_gb300/csrc/rq_scan_stream.cu",
+                "paper_2605_16007_gb300/csrc/rq_scan.cuh", "paper_2605_16007_gb300/csrc/rq_async.cuh",
+                "paper_2605_16007_gb300/csrc/rq_common.cuh"),
+    "mma": ("paper_2605_16007_gb300/csrc/rq_scan_mma.cu", "paper_2605_16007_gb300/csrc/rq_scan.cuh",
+            "paper_2605_16007_gb300/csrc/rq_async.cuh", "paper_2605_16007_gb300/csrc/rq_common.cuh"),
+}
+MODE_NAMES = {1: "plain", 2: "grouped", 3: "mma"}
+
+
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=21)
+    ap.add_argument("--warmup", type=int, default=7)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=None, help="override base size (testing)")
-    ap.add_argument("--nprobe", type=int, default=None, help="skip the sweep")
+    ap.add_argument("--n", type=int, default=None, help="override the skewed base size (testing)")
+    ap.add_argument("--setting", default=None, help="scale,n_rerank: skip the sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--no-hbm", action="store_true",
-                    help="skip the scan measurement on the 10M-vector skewed index")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--profile", action="store_true",
-                    help="only build and run --warmup + --steps batches per scan mode "
-                         "(for ncu captures); prints the stage times")
-    ap.add_argument("--modes", default="plain,grouped,mma",
-                    help="scan modes of --profile (comma separated)")
-    return ap.parse_args()
+    ap.add_argument("--no-secondary", action="store_true", help="skip the SIFT1M-shaped key")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--cpu-leg", action="store_true",
+                    help="(internal) the oracle's CPU leg, run in its own CUDA-free process")
+    ap.add_argument("--profile", default=None,
+                    help="only build the skewed index and run --warmup + --steps searches of "
+                         "one case (nq,nprobe,mode[,chunk]), for ncu captures")
+    return ap.parse_args(argv)
 
 
 # ---------------------------------------------------------------- ranks
@@ -204,213 +235,243 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- helpers
-def ground_truth(x_dev, q_dev, k: int, integer_valued: bool):
-    """k-th exact distance of each query (tie-aware recall) and the exact
-    distance function. Integer data in [0, 255] at D = 128: every term and
-    partial sum is an integer below 2^24, so float32 (TF32 off) is exact."""
+def exact_kth(x_dev, q_dev, k: int, integer_valued: bool, shortlist: int = 64):
+    """k-th exact squared distance of each query (float64), for tie-aware
+    recall@k. Integer data in [0, 255] at D = 128: every term and partial sum
+    of the float32 GEMM form is an integer below 2^24, so float32 (TF32 off)
+    is exact and the k-th is read directly. Otherwise the float32 GEMM form
+    picks a shortlist of `shortlist` candidates per query and their distances
+    are recomputed in float64 (the float32 form is off by a few ulps of
+    ||x||^2 + ||q||^2, far less than the gap between the k-th and the
+    shortlist-th neighbour). A GPU test pins this against the oracle's
+    brute-force exact kNN."""
     import torch
 
     torch.backends.cuda.matmul.allow_tf32 = False
-    dt = torch.float32 if integer_valued else torch.float64
-    X = x_dev.to(dt)
+    X = x_dev.to(torch.float32)
     xn = (X * X).sum(1)
     kth = torch.empty(q_dev.shape[0], dtype=torch.float64, device=x_dev.device)
-    for i in range(0, q_dev.shape[0], 256):
-        Q = q_dev[i:i + 256].to(dt)
+    step = max(1, min(256, (1 << 30) // (4 * X.shape[0])))   # ~1 GiB of distances at a time
+    for i in range(0, q_dev.shape[0], step):
+        Q = q_dev[i:i + step].to(torch.float32)
         d = xn[None, :] - 2.0 * (Q @ X.T) + (Q * Q).sum(1)[:, None]
-        kth[i:i + 256] = torch.topk(d, k, dim=1, largest=False).values[:, -1].to(torch.float64)
+        if integer_valued:
+            kth[i:i + step] = torch.topk(d, k, dim=1, largest=False).values[:, -1].to(torch.float64)
+        else:
+            cand = torch.topk(d, max(shortlist, k), dim=1, largest=False).indices
+            ex = ((X[cand].to(torch.float64) - Q[:, None, :].to(torch.float64)) ** 2).sum(-1)
+            kth[i:i + step] = torch.sort(ex, dim=1).values[:, k - 1]
         del d
     return kth
 
 
 def recall_of(x_dev, q_dev, ids, kth, k):
+    """Tie-aware recall@k: a returned id is a hit when its float64 exact
+    distance is at most the k-th exact distance; padded ids (-1) miss."""
     import torch
 
-    ids_t = torch.as_tensor(ids, device=x_dev.device)
+    ids_t = torch.as_tensor(ids, device=x_dev.device)[:, :k]
     ok = ids_t >= 0
     xs = x_dev[ids_t.clamp(min=0)].to(torch.float64)
     d = ((xs - q_dev[:, None, :].to(torch.float64)) ** 2).sum(-1)
     hit = (d <= kth[:, None] * (1 + 1e-12)) & ok
-    return float(hit[:, :k].sum().item()) / (ids_t.shape[0] * k)
+    return float(hit.sum().item()) / (ids_t.shape[0] * k)
+
+
 
 
 def scanned_pairs(h_offsets: np.ndarray, probe_ids: np.ndarray) -> int:
     lens = np.diff(h_offsets)
-    return int(lens[probe_ids].sum())
+    ok = probe_ids >= 0
+    return int(lens[probe_ids[ok]].sum())
 
 
-# ---------------------------------------------------------------- ours
-def run_ours(args, rank, world, local, pg):
+def unique_list_vectors(h_offsets: np.ndarray, probe_ids: np.ndarray) -> int:
+    lens = np.diff(h_offsets)
+    return int(lens[np.unique(probe_ids[probe_ids >= 0])].sum())
+
+
+# ---------------------------------------------------------------- skewed
+def skew_params(nq: int, scale: int, nrr: int, nlist: int):
+    """Per-query (nprobe, k, n_rerank) of the pool at one setting."""
+    base, kk = W.per_query_params(nq, SKEW_PARAM_SEED, (8, 256), (10, 100))
+    npb = np.minimum(base.astype(np.int64) * scale, nlist).astype(np.int32)
+    return npb, kk.astype(np.int32), np.full(nq, nrr, np.int32)
+
+
+def skew_schedule(steps: int, start: int = 0):
+    """(batch size, first pool row) of steps start, start + 1, ...: the
+    batch sizes cycle, the rows advance through the pool and wrap."""
+    out = []
+    row = 0
+    for i in range(start + steps):
+        b = SKEW_BATCHES[i % len(SKEW_BATCHES)]
+        if row + b > SKEW_POOL:
+            row = 0
+        if i >= start:
+            out.append((b, row))
+        row += b
+    return out
+
+
+def run_skewed(rq, args, rank, world, local, pg, dev, flush, stream):
     import torch
 
-    import paper_2605_16007_gb300 as rq
-
-    rq.build()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    wl = W.WORKLOADS[WORKLOAD]
+    wl = W.WORKLOADS["skewed"]
     mix = wl["mix"]
     n = args.n or wl["n"]
-    nq, bs, k, nrr = wl["nq"], wl["batch"], wl["k"], wl["n_rerank"]
+    t0 = time.perf_counter()
     x = mix.base(n)
-    q = mix.queries(nq)
-    integer_valued = mix.kind == "uint8"
+    gen_s = time.perf_counter() - t0
     x_dev = torch.from_numpy(x).to(dev)
-    q_dev = torch.from_numpy(q).to(dev)
+    del x
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ix = rq.rq_build(x_dev, wl["nlist"], seed=0, kmeans_iters=wl["iters"])
+    ix = rq.rq_build(x_dev, wl["nlist"], seed=0, kmeans_iters=wl["iters"], train_size=SKEW_TRAIN)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     st = ix.stats()
-    kth = ground_truth(x_dev, q_dev, k, integer_valued)
-    stream = torch.cuda.current_stream()
-    n_batches = nq // bs
-    batches = [q_dev[b * bs:(b + 1) * bs].contiguous() for b in range(n_batches)]
+    nlist = st["nlist"]
+    q = mix.queries(SKEW_POOL)
+    q_dev = torch.from_numpy(q).to(dev)
+    kth = exact_kth(x_dev, q_dev, 10, False)
+    kmax = 100
+    ids_pool = torch.empty((SKEW_POOL, kmax), dtype=torch.int64, device=dev)
+    d_pool = torch.empty((SKEW_POOL, kmax), dtype=torch.float32, device=dev)
 
-    def search_all(nprobe, mode, graph):
-        ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
-        dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
-        for b in range(n_batches):
-            ix.search(batches[b], nprobe, k, nrr, out_ids=ids[b * bs:(b + 1) * bs],
-                      out_dist=dist[b * bs:(b + 1) * bs], scan_mode=mode, use_graph=graph,
-                      stream=stream)
+    def run_pool(npb, kk, nr, mode=rq.RQ_SCAN_AUTO, graph=True):
+        for b0 in range(0, SKEW_POOL, 1024):
+            sl = slice(b0, b0 + 1024)
+            ix.search_mixed(q_dev[sl], npb[sl], kk[sl], nr[sl], k_stride=kmax,
+                            out_ids=ids_pool[sl], out_dist=d_pool[sl], scan_mode=mode,
+                            use_graph=graph, stream=stream)
         torch.cuda.synchronize()
-        return ids, dist
+        return recall_of(x_dev, q_dev, ids_pool, kth, 10)
 
+    # -- recall sweep, cheapest setting first
     sweep = {}
-    nprobe = args.nprobe
-    for npb in ([nprobe] if nprobe else wl["nprobe"]):
-        ids, _ = search_all(npb, rq.RQ_SCAN_GROUPED, True)
-        sweep[npb] = recall_of(x_dev, q_dev, ids, kth, k)
-        if nprobe is None and sweep[npb] >= RECALL_TARGET:
-            nprobe = npb
+    setting = None
+    candidates = [tuple(int(v) for v in args.setting.split(","))] if args.setting else SKEW_SETTINGS
+    for sc, nrr in candidates:
+        npb, kk, nr = skew_params(SKEW_POOL, sc, nrr, nlist)
+        sweep[f"{sc},{nrr}"] = round(run_pool(npb, kk, nr), 4)
+        if sweep[f"{sc},{nrr}"] >= RECALL_TARGET:
+            setting = (sc, nrr)
             break
-    if nprobe is None:
-        nprobe = max(sweep)
-    recall = sweep[nprobe]
-    ix.autotune(batches[0], nprobe, nrr)
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    out_ids = torch.empty((bs, k), dtype=torch.int64, device=dev)
-    out_d = torch.empty((bs, k), dtype=torch.float32, device=dev)
-    order = rank_batches(n_batches, rank, world)
+    if setting is None:
+        setting = candidates[-1]
+    scale, nrr = setting
+    npb, kk, nr = skew_params(SKEW_POOL, scale, nrr, nlist)
+    recall = sweep[f"{scale},{nrr}"]
+    # -- autotune one choice per batch class of the schedule
+    cache = tempfile.mktemp(suffix=".tune")
+    tuned = {}
+    for b in SKEW_BATCHES:
+        mean_np = int(round(float(npb[:b].mean())))
+        ix.autotune(q_dev[:b].contiguous(), mean_np, nrr, cache_path=cache)
+    if os.path.exists(cache):
+        for ln in open(cache):
+            parts = dict(p.split("=", 1) for p in ln.split() if "=" in p)
+            tuned[f"nq_class={parts.get('nq_class')},density_class={parts.get('density_class')}"] = (
+                f"{MODE_NAMES.get(int(parts.get('mode', 0)), '?')}"
+                + (f"/chunk {parts.get('chunk')}" if parts.get("mode") == "1" else ""))
+        os.unlink(cache)
+    # -- per-batch buffers
+    batches = {}
+    for b, row in skew_schedule(len(SKEW_BATCHES) * 2):
+        key = (b, row)
+        if key in batches:
+            continue
+        sl = slice(row, row + b)
+        batches[key] = dict(q=q_dev[sl].contiguous(), npb=np.ascontiguousarray(npb[sl]),
+                            kk=np.ascontiguousarray(kk[sl]), nr=np.ascontiguousarray(nr[sl]),
+                            ids=torch.empty((b, kmax), dtype=torch.int64, device=dev),
+                            d=torch.empty((b, kmax), dtype=torch.float32, device=dev))
+
+    def batch_of(key):
+        if key not in batches:
+            b, row = key
+            sl = slice(row, row + b)
+            batches[key] = dict(q=q_dev[sl].contiguous(), npb=np.ascontiguousarray(npb[sl]),
+                                kk=np.ascontiguousarray(kk[sl]), nr=np.ascontiguousarray(nr[sl]),
+                                ids=torch.empty((b, kmax), dtype=torch.int64, device=dev),
+                                d=torch.empty((b, kmax), dtype=torch.float32, device=dev))
+        return batches[key]
+
+    def step(key, mode, graph):
+        bt = batch_of(key)
+        ix.search_mixed(bt["q"], bt["npb"], bt["kk"], bt["nr"], k_stride=kmax, out_ids=bt["ids"],
+                        out_dist=bt["d"], scan_mode=mode, use_graph=graph, stream=stream)
 
     def timed(mode, graph, steps, warmup):
-        for i in range(warmup):
-            ix.search(batches[order[i % n_batches]], nprobe, k, nrr, out_ids=out_ids,
-                      out_dist=out_d, scan_mode=mode, use_graph=graph, stream=stream)
+        # every batch shape once (workspaces, graphs), then the warm-up steps
+        for key in skew_schedule(len(SKEW_BATCHES)):
+            step(key, mode, graph)
+        sched = skew_schedule(warmup + steps, start=rank * len(SKEW_BATCHES))
+        for key in sched[:warmup]:
+            step(key, mode, graph)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(steps)]
         torch.cuda.synchronize()
         barrier(pg)
         torch.cuda.synchronize()
-        w0 = time.perf_counter()
-        for i in range(steps):
+        for i, key in enumerate(sched[warmup:]):
             flush.zero_()
             evs[i][0].record(stream)
-            ix.search(batches[order[i % n_batches]], nprobe, k, nrr, out_ids=out_ids,
-                      out_dist=out_d, scan_mode=mode, use_graph=graph, stream=stream)
+            step(key, mode, graph)
             evs[i][1].record(stream)
         torch.cuda.synchronize()
         barrier(pg)
-        wall = time.perf_counter() - w0
         ms = [a.elapsed_time(b) for a, b in evs]
-        return sum(ms) / 1e3, ms, wall
+        nqs = sum(b for b, _ in sched[warmup:])
+        return sum(ms) / 1e3, nqs, ms
 
-    # -- batched (tuned mode, graph): the headline value
+    # -- batched: the headline value
     clocks = ClockSampler(local)
     clocks.start()
-    t_dev, ms_list, wall = timed(rq.RQ_SCAN_AUTO, True, args.steps, args.warmup)
+    t_dev, nq_timed, ms_list = timed(rq.RQ_SCAN_AUTO, True, args.steps, args.warmup)
     clk = clocks.stop()
-    t_max = max_over_ranks(pg, t_dev)
-    total_q = sum_over_ranks(pg, args.steps * bs)
-    value = total_q / t_max
+    value = sum_over_ranks(pg, nq_timed) / max_over_ranks(pg, t_dev)
     # -- plain form
-    t_plain, _, _ = timed(rq.RQ_SCAN_PLAIN, False, max(10, args.steps // 4), args.warmup)
-    plain_qps = sum_over_ranks(pg, max(10, args.steps // 4) * bs) / max_over_ranks(pg, t_plain)
-    # -- stage times of the tuned mode and of the plain scan (no graph)
-    def stage_profile(mode, reps=10):
-        acc = {}
-        for i in range(reps):
-            flush.zero_()
-            stt = {}
-            ix.search(batches[order[i % n_batches]], nprobe, k, nrr, out_ids=out_ids,
-                      out_dist=out_d, scan_mode=mode, stream=stream, stage_times=stt)
-            for kk_, v in stt.items():
-                acc[kk_] = acc.get(kk_, 0.0) + v / reps
-        return acc
-
-    stages = stage_profile(rq.RQ_SCAN_AUTO)
-    stages_plain = stage_profile(rq.RQ_SCAN_PLAIN)
-    stages_grouped = stage_profile(rq.RQ_SCAN_GROUPED)
-    stages_mma = stage_profile(rq.RQ_SCAN_MMA)
-    # scanned (query, vector) pairs per batch from the probe lists
-    h_off = ix.offsets()
-    pid = torch.empty((bs, nprobe), dtype=torch.int32, device=dev)
-    ix.search(batches[0], nprobe, k, nrr, out_ids=out_ids, out_dist=out_d,
-              dump={"probe_ids": pid}, stream=stream)
-    torch.cuda.synchronize()
-    pairs = scanned_pairs(h_off, pid.cpu().numpy())
-    dp = st["dim_pad"]
-    code_b = dp // 8
-    scan_s = stages["scan"] / 1e3
-    tuned = ix.stats()["auto_scan_mode"]
-    logical_gbs = pairs * (code_b + 8) / scan_s / 1e9
-    unique_bytes = int(np.diff(h_off)[np.unique(pid.cpu().numpy())].sum()) * (code_b + 8)
-    key = f"scan:{WORKLOAD}:{kernel_source_hash()}"
-    if tuned == rq.RQ_SCAN_MMA:
-        # tcgen05 kind::f8f6f4: 2 * D_p flops per (query, vector) pair; peak =
-        # measured bf16 dense x the nominal FP8/BF16 ratio (4.5 / 2.25 PFLOP/s).
-        achieved = pairs * 2 * dp / scan_s / 1e12
-        peak = measured_bf16_tflops() * 2.0
-        roofline = {"kernel": "scan_mma_kernel (tcgen05 FP8)", "bound": "tensor",
-                    "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
-                    "frac": round(achieved / peak, 5),
-                    "peak_source": "measured bf16 dense TFLOP/s x 2 (nominal FP8 ratio)"}
-    else:
-        popc_per_pair = 4 * dp // 32
-        achieved = pairs * popc_per_pair / scan_s / 1e12
-        peak = POPC_PER_SM_CLK * SMS * 2070e6 / 1e12
-        roofline = {"kernel": "scan (popcount)", "bound": "alu", "achieved": round(achieved, 4),
-                    "peak": round(peak, 4), "unit": "Tpopc/s", "frac": round(achieved / peak, 4),
-                    "peak_source": "derived: 16 POPC/clk/SM x 152 SMs x 2070 MHz"}
-    roofline.update({
-        "traffic": TRAFFIC.get(key) if tuned == rq.RQ_SCAN_MMA else None,
-        "scan_ms": round(stages["scan"], 4),
-        "pairs_per_launch": pairs,
-        "logical_gbs": round(logical_gbs, 1),
-        "unique_index_gbs": round(unique_bytes / scan_s / 1e9, 1),
-        "plain_scan_ms": round(stages_plain["scan"], 4),
-    })
+    t_plain, nq_plain, _ = timed(rq.RQ_SCAN_PLAIN, False, len(SKEW_BATCHES), 2)
+    plain_qps = sum_over_ranks(pg, nq_plain) / max_over_ranks(pg, t_plain)
     # -- e2e through the C ABI with host buffers
-    import torch as _t
-
-    hq = _t.empty((bs, wl["mix"].dim), dtype=_t.float32, pin_memory=True)
-    hi = _t.empty((bs, k), dtype=_t.int64, pin_memory=True)
-    hd = _t.empty((bs, k), dtype=_t.float32, pin_memory=True)
-    e2e_steps = max(10, args.steps // 4)
-    host_batches = [q[b * bs:(b + 1) * bs] for b in range(n_batches)]
-    for i in range(args.warmup):
-        hq.numpy()[:] = host_batches[order[i % n_batches]]
-        ix.search(hq, nprobe, k, nrr, out_ids=hi, out_dist=hd, use_graph=True, stream=stream)
-    e2e_t = 0.0
-    for i in range(e2e_steps):
-        hq.numpy()[:] = host_batches[order[i % n_batches]]
-        flush.zero_()
+    e2e = run_skew_e2e(rq, ix, q, npb, kk, nr, kmax, args, rank, pg, flush)
+    # -- per batch size: stage times of the tuned form and of each scan form,
+    # and the scan's bytes / pairs
+    per_batch = {}
+    for b, row in skew_schedule(len(SKEW_BATCHES)):
+        bt = batch_of((b, row))
+        prof = {}
+        for name, mode in (("auto", rq.RQ_SCAN_AUTO), ("plain", rq.RQ_SCAN_PLAIN),
+                           ("grouped", rq.RQ_SCAN_GROUPED), ("mma", rq.RQ_SCAN_MMA)):
+            acc = {}
+            for rep in range(3):
+                flush.zero_()
+                stt = {}
+                ix.search_mixed(bt["q"], bt["npb"], bt["kk"], bt["nr"], k_stride=kmax,
+                                out_ids=bt["ids"], out_dist=bt["d"], scan_mode=mode,
+                                stream=stream, stage_times=stt)
+                if rep:
+                    for a_, v in stt.items():
+                        acc[a_] = acc.get(a_, 0.0) + v / 2
+            prof[name] = acc
+        pid = torch.empty((b, int(bt["npb"].max())), dtype=torch.int32, device=dev)
+        ix.search_mixed(bt["q"], bt["npb"], bt["kk"], bt["nr"], k_stride=kmax, out_ids=bt["ids"],
+                        out_dist=bt["d"], dump={"probe_ids": pid}, stream=stream)
         torch.cuda.synchronize()
-        w0 = time.perf_counter()
-        ix.search(hq, nprobe, k, nrr, out_ids=hi, out_dist=hd, use_graph=True, stream=stream)
-        e2e_t += time.perf_counter() - w0
-    e2e_qps = sum_over_ranks(pg, e2e_steps * bs) / max_over_ranks(pg, e2e_t)
-    # -- serving: continuous batching under a Poisson request stream
+        p = pid.cpu().numpy()
+        for i in range(b):
+            p[i, bt["npb"][i]:] = -1
+        per_batch[b] = dict(stages=prof, pairs=scanned_pairs(ix.offsets(), p),
+                            unique_vectors=unique_list_vectors(ix.offsets(), p))
+    roofline, scan_table = skew_roofline(per_batch, st)
     serving = None
     if not args.no_serving:
-        serving = run_serving(rq, ix, q, nprobe, k, nrr, offered=0.5 * value / max(world, 1))
-        serving["saturated"] = run_serving_saturated(rq, ix, q, nprobe, k, nrr)
-    # this library's kernels per search: rotate, centroid distances, probe
-    # selection, quantise, bound, scan, select + re-rank (memsets not counted)
-    launches_per_step = 7
+        serving = run_skew_serving(rq, ix, q, npb, kk, nrr, offered=0.5 * value / max(world, 1))
+        serving["saturated"] = run_skew_saturated(rq, ix, q, npb, kk, nrr)
     ms_per_step = 1e3 * t_dev / args.steps
+    lens = np.diff(ix.offsets())
     res = {
         "metric": METRIC,
         "value": round(value, 1),
@@ -425,54 +486,160 @@ def run_ours(args, rank, world, local, pg):
         "dtype": "f32",
         "data": "synthetic",
         "config": {
-            "workload": f"{WORKLOAD}-shaped: N={n} D={mix.dim} integer-valued float32 in "
-                        f"[0,255], nlist={wl['nlist']}, batch={bs} queries, k={k}, "
-                        f"n_rerank={nrr}, B_q=4",
-            "nprobe": nprobe,
-            "recall_at_10": round(recall, 4),
-            "recall_sweep": {str(a): round(b, 4) for a, b in sweep.items()},
-            "l2": "flushed (256 MiB write) between timed steps",
-            "scan_mode_auto": MODE_NAMES.get(ix.stats()["auto_scan_mode"]),
+            "workload": f"skewed-shaped: N={n} D={mix.dim} (D_p {st['dim_pad']}) unit vectors, "
+                        f"1024-component mixture with Zipf (s=1) weights, nlist={nlist} "
+                        f"(list lengths {int(lens.min())}..{int(lens.max())}), batches "
+                        f"{'/'.join(str(b) for b in SKEW_BATCHES)} queries cycled, per-query "
+                        f"nprobe = {scale} x U{{8..256}}, k in {{10,100}}, n_rerank={nrr}, B_q=4",
+            "setting": {"nprobe_scale": scale, "n_rerank": nrr,
+                        "mean_nprobe": round(float(npb.mean()), 1)},
+            "recall_at_10": recall,
+            "recall_sweep": sweep,
+            "l2": "flushed (256 MiB write) before each timed step; index (403 MB) larger than L2",
             "graph": True,
+            "tuned": tuned,
             "parallelism": f"replicas x{world} (query batches per rank)",
+            "queries_timed": nq_timed,
         },
         "plain": {"value": round(plain_qps, 1), "unit": "queries/s",
-                  "ms_per_step": round(1e3 * t_plain / max(10, args.steps // 4), 4)},
+                  "ms_per_step": round(1e3 * t_plain / len(SKEW_BATCHES), 4)},
         "serving": serving,
-        "e2e": {"value": round(e2e_qps, 1), "unit": "queries/s",
-                "h2d_bytes_per_step": bs * mix.dim * 4 + 16 * bs + 4,
-                "d2h_bytes_per_step": bs * k * 12},
+        "e2e": e2e,
         "roofline": roofline,
-        "stage_ms": {a: round(b, 4) for a, b in stages.items()},
-        "stage_ms_plain": {a: round(b, 4) for a, b in stages_plain.items()},
-        "stage_ms_grouped": {a: round(b, 4) for a, b in stages_grouped.items()},
-        "stage_ms_mma": {a: round(b, 4) for a, b in stages_mma.items()},
+        "scan_by_batch": scan_table,
+        "step_ms_by_batch": {str(b): round(float(np.median([m for (bb, _), m in zip(
+            skew_schedule(args.warmup + args.steps, start=rank * len(SKEW_BATCHES))[args.warmup:],
+            ms_list) if bb == b] or [0.0])), 4) for b in SKEW_BATCHES},
         "build_s": round(build_s, 3),
-        "index": {"bytes": st["index_bytes"], "min_list": st["min_list"],
-                  "max_list": st["max_list"]},
+        "gen_s": round(gen_s, 2),
+        "index": {"bytes": st["index_bytes"], "raw_bytes": st["raw_bytes"],
+                  "min_list": st["min_list"], "max_list": st["max_list"]},
         "clocks": clk,
-        "gpu_launches": launches_per_step * (args.steps + args.warmup),
+        # this library's kernels per search: rotate, centroid ranking,
+        # preparation, scan, finalize
+        "gpu_launches": 5 * args.steps,
     }
-    if not args.no_hbm:
-        res["hbm_scan"] = run_hbm_scan(rq, dev, flush, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(ix, q[:bs], nprobe, k, nrr, args.cpu_seconds)
-    ix_err = ix.device_error()
-    if ix_err:
-        res["device_error"] = ix_err
+        res["cpu_baseline"] = cpu_baseline_threads(ix, q, npb, kk, nr, args.cpu_seconds)
+    err = ix.device_error()
+    if err:
+        res["device_error"] = err
+    ix.free()
+    del x_dev, q_dev
     return res
 
 
-MODE_NAMES = {1: "plain", 2: "grouped-popcount", 3: "grouped-tcgen05"}
+def skew_roofline(per_batch, st):
+    """The scan's roofline per batch size, and the headline object: the
+    HBM-bound end of the schedule (the smallest batch, whose probed lists are
+    read about once). Algorithmic bytes of a launch: C + 8 bytes (code and
+    {r^2, f}) per vector of the probed lists, each list once (what a grouped
+    scan must read), and the same per (query, vector) pair (what a
+    query-level scan reads through L2). Compute: 16 POPC per pair
+    (popcount forms), 2 D_p flops per pair (tensor-core form)."""
+    pk = measured_peaks()
+    unit = st["dim_pad"] // 8 + 8
+    popc_peak = POPC_PER_SM_CLK * SMS * SM_MHZ * 1e6
+    fp8_peak = pk["bf16_tflops"] * 2.0
+    table = {}
+    for b, rec in sorted(per_batch.items()):
+        row = {}
+        for name in ("auto", "plain", "grouped", "mma"):
+            s = rec["stages"][name]["scan"] / 1e3
+            row[name] = {"scan_ms": round(s * 1e3, 4),
+                         "unique_gbs": round(rec["unique_vectors"] * unit / s / 1e9, 1),
+                         "pair_gbs": round(rec["pairs"] * unit / s / 1e9, 1)}
+        row["pairs"] = rec["pairs"]
+        row["unique_bytes"] = rec["unique_vectors"] * unit
+        row["pairs_per_vector"] = round(rec["pairs"] / max(1, rec["unique_vectors"]), 2)
+        table[str(b)] = row
+    b0 = min(per_batch)
+    rec = per_batch[b0]
+    best = min(("plain", "grouped", "mma"), key=lambda m: rec["stages"][m]["scan"])
+    s = rec["stages"][best]["scan"] / 1e3
+    achieved = rec["unique_vectors"] * unit / s / 1e9
+    key = f"scan:{best}:skewed:{b0}:{kernel_source_hash(SCAN_SOURCES[best])}"
+    roof = {"kernel": {"plain": "scan_plain_kernel", "grouped": "scan_stream_kernel",
+                       "mma": "scan_mma_kernel"}[best],
+            "case": f"{b0}-query batch of the schedule", "bound": "hbm",
+            "achieved": round(achieved, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": round(achieved / pk["hbm_gbs"], 4),
+            "traffic": TRAFFIC.get(key),
+            "algorithmic_bytes": rec["unique_vectors"] * unit,
+            "scan_ms": round(s * 1e3, 4),
+            "peak_source": f"{pk['source']} (MEASURED_PEAKS.json hbm_gbs)"}
+    # the largest batch: the scan is compute-bound there
+    b1 = max(per_batch)
+    rec1 = per_batch[b1]
+    best1 = min(("plain", "grouped", "mma"), key=lambda m: rec1["stages"][m]["scan"])
+    s1 = rec1["stages"][best1]["scan"] / 1e3
+    if best1 == "mma":
+        ach = rec1["pairs"] * 2 * st["dim_pad"] / s1 / 1e12
+        roof["compute_end"] = {"kernel": "scan_mma_kernel", "case": f"{b1}-query batch",
+                               "bound": "tensor", "achieved": round(ach, 2),
+                               "peak": round(fp8_peak, 1), "unit": "TFLOP/s",
+                               "frac": round(ach / fp8_peak, 4),
+                               "peak_source": "measured bf16 dense x 2 (nominal FP8/BF16)"}
+    else:
+        ach = rec1["pairs"] * 4 * st["dim_pad"] // 32 / s1
+        roof["compute_end"] = {"kernel": best1, "case": f"{b1}-query batch", "bound": "alu",
+                               "achieved": round(ach / 1e12, 3),
+                               "peak": round(popc_peak / 1e12, 3), "unit": "Tpopc/s",
+                               "frac": round(ach / popc_peak, 4),
+                               "peak_source": "derived: 16 POPC/clk/SM x 152 SMs x 2070 MHz"}
+    return roof, table
 
 
-def run_serving(rq, ix, q, nprobe, k, nrr, offered, seconds=2.0, seed=3):
-    """Poisson arrivals of requests of 1-64 queries at `offered` queries/s."""
-    srv = rq.Server(ix, slots=4, max_batch=1024)
+def run_skew_e2e(rq, ix, q, npb, kk, nr, kmax, args, rank, pg, flush):
+    """The batched search through the C ABI with host (pinned) buffers: each
+    timed call uploads the batch's queries and per-query parameters and
+    downloads its results."""
+    import torch
+
+    steps = max(len(SKEW_BATCHES), args.steps)
+    sched = skew_schedule(steps + len(SKEW_BATCHES), start=rank * len(SKEW_BATCHES))
+    bufs = {}
+    for b in SKEW_BATCHES:
+        bufs[b] = (torch.empty((b, q.shape[1]), dtype=torch.float32, pin_memory=True),
+                   torch.empty((b, kmax), dtype=torch.int64, pin_memory=True),
+                   torch.empty((b, kmax), dtype=torch.float32, pin_memory=True))
+
+    def call(b, row):
+        hq, hi, hd = bufs[b]
+        hq.numpy()[:] = q[row:row + b]
+        ix.search_mixed(hq, npb[row:row + b], kk[row:row + b], nr[row:row + b], k_stride=kmax,
+                        out_ids=hi, out_dist=hd, use_graph=True)
+
+    for b, row in sched[:len(SKEW_BATCHES)]:
+        call(b, row)
+    tot = 0.0
+    nqs = 0
+    h2d = d2h = 0
+    for b, row in sched[len(SKEW_BATCHES):]:
+        flush.zero_()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        call(b, row)
+        tot += time.perf_counter() - w0
+        nqs += b
+        h2d += b * q.shape[1] * 4 + 16 * b + 4
+        d2h += b * kmax * 12 + 4
+    return {"value": round(sum_over_ranks(pg, nqs) / max_over_ranks(pg, tot), 1),
+            "unit": "queries/s", "h2d_bytes_per_step": int(h2d / steps),
+            "d2h_bytes_per_step": int(d2h / steps)}
+
+
+def run_skew_serving(rq, ix, q, npb, kk, nrr, offered, seconds=2.0, seed=3):
+    """Poisson arrivals of requests of 1-64 queries at `offered` queries/s;
+    each request takes the nprobe and k of its first pool query."""
+    srv = rq.Server(ix, slots=4, max_batch=4096)
     rng = np.random.default_rng(seed)
-    sizes = rng.integers(1, 65, 100000)
-    mean_size = sizes.mean()
-    rate = offered / mean_size  # requests per second
+    sizes = rng.integers(1, 65, 200000)
+    rate = offered / sizes.mean()
+    # warm the server's batch shapes
+    for t in [srv.submit(q[i * 64:(i + 1) * 64], int(npb[i * 64]), int(kk[i * 64]), nrr)
+              for i in range(8)]:
+        srv.wait(t)
     tickets = []
     t_start = time.perf_counter()
     t_next = t_start
@@ -486,7 +653,7 @@ def run_serving(rq, ix, q, nprobe, k, nrr, offered, seconds=2.0, seed=3):
         n = int(sizes[i % sizes.size])
         if lo + n > q.shape[0]:
             lo = 0
-        tickets.append((srv.submit(q[lo:lo + n], nprobe, k, nrr), n))
+        tickets.append((srv.submit(q[lo:lo + n], int(npb[lo]), int(kk[lo]), nrr), n))
         lo += n
         i += 1
         t_next += rng.exponential(1.0 / rate)
@@ -502,87 +669,19 @@ def run_serving(rq, ix, q, nprobe, k, nrr, offered, seconds=2.0, seed=3):
     return {"qps": round(nq_done / (t_end - t_start), 1), "offered_qps": round(offered, 1),
             "requests": len(lats), "p50_ms": round(lats[len(lats) // 2], 3),
             "p99_ms": round(lats[min(len(lats) - 1, int(0.99 * len(lats)))], 3),
-            "request_sizes": "uniform 1-64 queries, Poisson arrivals"}
+            "request_sizes": "uniform 1-64 queries, Poisson arrivals, per-request nprobe and k"}
 
 
-def measured_hbm_gbs() -> float:
-    """Copy bandwidth measured on this machine, else the stated fallback."""
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            return float(json.load(fh)["hbm_gbs"])
-    except (OSError, KeyError, ValueError):
-        return 6800.0
-
-
-def run_hbm_scan(rq, dev, flush, stream, n=10_000_000, nq=64, nprobe=32, k=10, nrr=200):
-    """The scan on an index larger than L2: the skewed recipe (N=10M x 96 unit
-    vectors, 1024-component Zipf mixture, nlist 4096, list lengths varying by
-    more than 100x), 64 queries at nprobe 32, L2 flushed before each search.
-    Reports the scan time of each scan mode and the unique index bytes the
-    probed lists hold (codes + {r^2, f}) per unit time against the measured
-    HBM copy bandwidth."""
-    import torch
-
-    wl = W.WORKLOADS["skewed"]
-    mix = wl["mix"]
-    x_dev = torch.from_numpy(mix.base(n)).to(dev)
-    t0 = time.perf_counter()
-    ix = rq.rq_build(x_dev, wl["nlist"], seed=0, kmeans_iters=4, train_size=1_000_000)
-    torch.cuda.synchronize()
-    build_s = time.perf_counter() - t0
-    del x_dev
-    q = torch.from_numpy(mix.queries(nq)).to(dev)
-    ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
-    dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
-    st = ix.stats()
-    scan = {}
-    for name, mode in (("plain", rq.RQ_SCAN_PLAIN), ("grouped", rq.RQ_SCAN_GROUPED),
-                       ("mma", rq.RQ_SCAN_MMA)):
-        for _ in range(2):
-            ix.search(q, nprobe, k, nrr, out_ids=ids, out_dist=dist, scan_mode=mode, stream=stream)
-        ts = []
-        for _ in range(7):
-            flush.zero_()
-            stt = {}
-            ix.search(q, nprobe, k, nrr, out_ids=ids, out_dist=dist, scan_mode=mode,
-                      stream=stream, stage_times=stt)
-            ts.append(stt["scan"])
-        scan[name] = round(sorted(ts)[len(ts) // 2], 4)
-    pid = torch.empty((nq, nprobe), dtype=torch.int32, device=dev)
-    ix.search(q, nprobe, k, nrr, out_ids=ids, out_dist=dist, dump={"probe_ids": pid},
-              stream=stream)
-    torch.cuda.synchronize()
-    lens = np.diff(ix.offsets())
-    p = pid.cpu().numpy()
-    unit = st["dim_pad"] // 8 + 8
-    unique_b = int(lens[np.unique(p)].sum()) * unit
-    pairs = int(lens[p].sum())
-    best = min(scan, key=scan.get)
-    gbs = unique_b / (scan[best] / 1e3) / 1e9
-    peak = measured_hbm_gbs()
-    ix.free()
-    return {"workload": f"skewed-shaped: N={n} D={mix.dim} (D_p {st['dim_pad']}) unit vectors, "
-                        f"Zipf list lengths, nlist={wl['nlist']}, {nq} queries, nprobe={nprobe}, "
-                        f"k={k}, n_rerank={nrr}",
-            "scan_ms": scan, "best_mode": best, "unique_index_bytes": unique_b,
-            "pairs": pairs, "pairs_per_vector": round(pairs / max(1, unique_b // unit), 2),
-            "hbm_gbs": round(gbs, 1), "peak_gbs": peak, "frac": round(gbs / peak, 4),
-            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
-            "list_len": {"min": int(lens.min()), "max": int(lens.max())},
-            "build_s": round(build_s, 2)}
-
-
-def run_serving_saturated(rq, ix, q, nprobe, k, nrr, req=250, rounds=5, slots=4):
-    """The server kept busy: every query of `rounds` passes over the query set
-    submitted at once as requests of `req` queries (host buffers in and out,
-    as for e2e); the server packs them into batches of up to 1024 and runs up
-    to `slots` batches at a time on their own streams."""
-    srv = rq.Server(ix, slots=slots, max_batch=1024)
-    warm = [srv.submit(q[lo:lo + req], nprobe, k, nrr) for lo in range(0, q.shape[0], req)]
+def run_skew_saturated(rq, ix, q, npb, kk, nrr, req=256, rounds=3, slots=4):
+    """The server kept busy: the pool submitted at once as requests of `req`
+    queries (host buffers in and out); up to `slots` batches run at a time."""
+    srv = rq.Server(ix, slots=slots, max_batch=4096)
+    warm = [srv.submit(q[lo:lo + req], int(npb[lo]), int(kk[lo]), nrr)
+            for lo in range(0, q.shape[0], req)]
     for t in warm:
         srv.wait(t)
     t0 = time.perf_counter()
-    tickets = [srv.submit(q[lo:lo + req], nprobe, k, nrr)
+    tickets = [srv.submit(q[lo:lo + req], int(npb[lo]), int(kk[lo]), nrr)
                for _ in range(rounds) for lo in range(0, q.shape[0], req)]
     for t in tickets:
         srv.wait(t)
@@ -590,127 +689,288 @@ def run_serving_saturated(rq, ix, q, nprobe, k, nrr, req=250, rounds=5, slots=4)
     srv.close()
     return {"qps": round(rounds * q.shape[0] / dt, 1), "request_size": req, "slots": slots,
             "queries": rounds * q.shape[0],
-            "form": "host buffers in and out (compare e2e); batches of up to 1024 overlap"}
+            "form": "host buffers in and out (compare e2e); batches of up to 4096 overlap"}
 
 
-def oracle_index(ix):
+# ---------------------------------------------------------------- sift1m
+def run_sift1m(rq, args, rank, world, pg, dev, flush, stream):
+    """Secondary key: the SIFT1M-shaped recipe (L2-resident index)."""
+    import torch
+
+    wl = W.WORKLOADS["sift1m"]
+    mix = wl["mix"]
+    x = mix.base(wl["n"])
+    q = mix.queries(wl["nq"])
+    x_dev = torch.from_numpy(x).to(dev)
+    q_dev = torch.from_numpy(q).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ix = rq.rq_build(x_dev, wl["nlist"], seed=0, kmeans_iters=wl["iters"])
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    nq, bs, k, nrr = wl["nq"], wl["batch"], wl["k"], wl["n_rerank"]
+    kth = exact_kth(x_dev, q_dev, k, True)
+    n_batches = nq // bs
+    batches = [q_dev[b * bs:(b + 1) * bs].contiguous() for b in range(n_batches)]
+    ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
+    dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    sweep = {}
+    nprobe = None
+    for npb in wl["nprobe"]:
+        for b in range(n_batches):
+            ix.search(batches[b], npb, k, nrr, out_ids=ids[b * bs:(b + 1) * bs],
+                      out_dist=dist[b * bs:(b + 1) * bs], use_graph=True, stream=stream)
+        torch.cuda.synchronize()
+        sweep[str(npb)] = round(recall_of(x_dev, q_dev, ids, kth, k), 4)
+        if sweep[str(npb)] >= RECALL_TARGET:
+            nprobe = npb
+            break
+    nprobe = nprobe or wl["nprobe"][-1]
+    ix.autotune(batches[0], nprobe, nrr)
+    out_i = torch.empty((bs, k), dtype=torch.int64, device=dev)
+    out_d = torch.empty((bs, k), dtype=torch.float32, device=dev)
+    order = rank_batches(n_batches, rank, world)
+
+    def timed(mode, graph, steps):
+        for i in range(3):
+            ix.search(batches[order[i % n_batches]], nprobe, k, nrr, out_ids=out_i, out_dist=out_d,
+                      scan_mode=mode, use_graph=graph, stream=stream)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        torch.cuda.synchronize()
+        for i in range(steps):
+            flush.zero_()
+            evs[i][0].record(stream)
+            ix.search(batches[order[i % n_batches]], nprobe, k, nrr, out_ids=out_i, out_dist=out_d,
+                      scan_mode=mode, use_graph=graph, stream=stream)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / 1e3
+
+    steps = max(10, args.steps)
+    t_b = timed(rq.RQ_SCAN_AUTO, True, steps)
+    t_p = timed(rq.RQ_SCAN_PLAIN, False, steps)
+    stt = {}
+    ix.search(batches[0], nprobe, k, nrr, out_ids=out_i, out_dist=out_d, stream=stream,
+              stage_times=stt)
+    res = {"workload": f"sift1m-shaped: N={wl['n']} D={mix.dim} integer-valued float32 in [0,255], "
+                       f"nlist={wl['nlist']}, batch={bs}, k={k}, n_rerank={nrr}, B_q=4",
+           "nprobe": nprobe, "recall_at_10": sweep[str(nprobe)], "recall_sweep": sweep,
+           "batched_qps": round(steps * bs / t_b, 1), "plain_qps": round(steps * bs / t_p, 1),
+           "stage_ms": {a: round(b, 4) for a, b in stt.items()}, "build_s": round(build_s, 3),
+           "l2": "flushed (256 MiB write) before each timed step; index (41 MB) fits in L2"}
+    ix.free()
+    return res
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_index_of(ix):
+    """The GPU index's arrays, as the oracle's index dict (host copies)."""
     h = ix.to_host()
     return dict(n=h["n"], dim=h["dim"], dp=h["dp"], nlist=h["nlist"], P=h["P"], cR=h["cR"],
                 offsets=h["offsets"], ids=h["ids"], codes=h["codes"],
                 r2=h["factors"][:, 0].copy(), f=h["factors"][:, 1].copy(),
-                raw=h["raw"].astype(np.float32))
+                raw=h["raw"].astype(np.float32) if h["raw"].dtype != np.float32 else h["raw"])
 
 
-def cpu_baseline(ix, q, nprobe, k, nrr, seconds):
-    """The CPU oracle's search (as it stands) on a bounded sample of queries."""
+def cpu_baseline_threads(ix, q, npb, kk, nr, seconds):
+    """The oracle's search as it stands on a bounded sample of the pool:
+    queries one at a time on one thread, then on every host core (one thread
+    per core; numpy releases the interpreter lock in its array operations).
+    The index is the GPU build's, copied to the host (its build is not part
+    of the metric)."""
+    from concurrent.futures import ThreadPoolExecutor
+
     from oracle import rabitq as R
 
-    oix = oracle_index(ix)
+    oix = oracle_index_of(ix)
+    cores = os.cpu_count() or 1
+
+    def one(i):
+        R.search(oix, q[i:i + 1], int(npb[i]), int(kk[i]), int(nr[i]))
+        return 1
+
     done = 0
     t0 = time.perf_counter()
-    while time.perf_counter() - t0 < seconds and done < q.shape[0]:
-        R.search(oix, q[done:done + 1], nprobe, k, nrr)
+    while time.perf_counter() - t0 < seconds / 3 and done < q.shape[0]:
+        one(done)
         done += 1
-    el = time.perf_counter() - t0
-    return {"value": round(done / el, 3), "unit": "queries/s", "cores": 1, "kind": "oracle",
-            "sample": f"{done} queries of the first batch, one at a time, {el:.1f} s, "
-                      f"nprobe={nprobe}, index from the same build"}
+    el1 = time.perf_counter() - t0
+    qps1 = done / el1
+    m = max(cores, int(qps1 * cores * seconds * 2 / 3))
+    idx = [(done + i) % q.shape[0] for i in range(m)]
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        got = sum(ex.map(one, idx))
+    elm = time.perf_counter() - t0
+    return {"value": round(got / elm, 3), "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "cpu": cpu_model(), "one_core": round(qps1, 3),
+            "sample": f"{done} queries on one thread ({el1:.1f} s), then {got} on {cores} "
+                      f"threads ({elm:.1f} s), pool queries with their own nprobe/k/n_rerank; "
+                      f"index from the GPU build"}
 
 
-# ---------------------------------------------------------------- reference
-def run_reference(args, rank, world, local, pg):
-    """The CPU oracle timed on the same workload: each step searches a bounded
-    sample of queries (the oracle reads the index built on the GPU; the build
-    is not part of the metric)."""
-    import torch
-
-    import paper_2605_16007_gb300 as rq
+def _cpu_worker(i):
     from oracle import rabitq as R
 
-    rq.build()
-    torch.cuda.set_device(local)
-    wl = W.WORKLOADS[WORKLOAD]
+    g = _CPU_STATE
+    R.search(g["oix"], g["q"][i:i + 1], int(g["npb"][i]), int(g["kk"][i]), int(g["nr"][i]))
+    return 1
+
+
+_CPU_STATE = {}
+
+
+def cpu_leg(args):
+    """The reference arm's work, in a process that never loads the CUDA
+    library: the oracle's own float64 build of the skewed index (not timed),
+    then warm-up + timed steps of its search, one pool query per host core
+    per step, on a fork pool of one process per core."""
+    import multiprocessing as mp
+
+    from oracle import rabitq as R
+
+    wl = W.WORKLOADS["skewed"]
     mix = wl["mix"]
     n = args.n or wl["n"]
+    cores = os.cpu_count() or 1
     x = mix.base(n)
-    q = mix.queries(wl["nq"])
-    ix = rq.rq_build(x, wl["nlist"], seed=0, kmeans_iters=wl["iters"])
-    oix = oracle_index(ix)
-    # the nprobe the batched arm's recall sweep settles on for this workload
-    # (recall@10 0.9505 at 16); --nprobe sets both arms
-    nprobe = args.nprobe or REFERENCE_NPROBE
-    k, nrr = wl["k"], wl["n_rerank"]
-    per_step = 4
-    for i in range(args.warmup):
-        R.search(oix, q[i:i + 1], nprobe, k, nrr)
+    q = mix.queries(SKEW_POOL)
+    scale, nrr = SKEW_REFERENCE_SETTING
+    npb, kk, nr = skew_params(SKEW_POOL, scale, nrr, wl["nlist"])
+    ctx = mp.get_context("fork")   # this process has no CUDA context
     t0 = time.perf_counter()
-    for s in range(args.steps):
-        lo = (s * per_step) % (q.shape[0] - per_step)
-        R.search(oix, q[lo:lo + per_step], nprobe, k, nrr)
-    el = time.perf_counter() - t0
-    value = args.steps * per_step / el
-    res = {"metric": METRIC, "value": round(value, 3), "unit": "queries/s", "n_gpus": 1,
-           "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": round(1e3 * el / args.steps, 3), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "impl": "reference",
-           "config": {"workload": f"{WORKLOAD}-shaped: N={n} D={mix.dim}, nlist={wl['nlist']}, "
-                                  f"k={k}, n_rerank={nrr}", "nprobe": nprobe,
-                      "sample": f"{per_step} queries per step"},
-           "cpu_baseline": {"value": round(value, 3), "unit": "queries/s", "cores": 1,
-                            "kind": "oracle",
-                            "sample": f"{args.steps} steps x {per_step} queries"},
-           "e2e": {"value": round(value, 3), "unit": "queries/s", "h2d_bytes_per_step": 0,
-                   "d2h_bytes_per_step": 0}}
-    return res
+    with ctx.Pool(cores) as pool:
+        oix = R.build_index(x, wl["nlist"], seed=0, iters=wl["iters"], n_train=SKEW_TRAIN,
+                            f64=True, map_fn=pool.imap)
+    build_s = time.perf_counter() - t0
+    _CPU_STATE.update(oix=oix, q=q, npb=npb, kk=kk, nr=nr)
+    with ctx.Pool(cores) as pool:
+        nxt = 0
+        for _ in range(args.warmup):
+            pool.map(_cpu_worker, range(nxt, nxt + cores))
+            nxt += cores
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pool.map(_cpu_worker, [(nxt + j) % SKEW_POOL for j in range(cores)])
+            nxt += cores
+        el = time.perf_counter() - t0
+    value = args.steps * cores / el
+    return {"value": round(value, 3), "cores": cores, "build_s": round(build_s, 1),
+            "ms_per_step": round(1e3 * el / args.steps, 3), "cpu": cpu_model(),
+            "setting": {"nprobe_scale": scale, "n_rerank": nrr}}
 
 
+def run_reference(args):
+    """The CPU oracle on the headline workload, measured by cpu_leg in a
+    child process with single-threaded BLAS (one process per core)."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-leg", "--steps", str(args.steps),
+           "--warmup", str(args.warmup)] + (["--n", str(args.n)] if args.n else [])
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True)
+    if out.returncode != 0:
+        return {"impl": "reference", "unavailable": "CPU leg failed: " +
+                (out.stderr.strip().splitlines() or ["?"])[-1][:200]}
+    leg = json.loads(out.stdout.strip().splitlines()[-1])
+    wl = W.WORKLOADS["skewed"]
+    n = args.n or wl["n"]
+    v = leg["value"]
+    return {"metric": METRIC, "value": v, "unit": "queries/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": leg["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"skewed-shaped: N={n} D=96, nlist={wl['nlist']}, per-query "
+                                   f"nprobe = {leg['setting']['nprobe_scale']} x U{{8..256}}, "
+                                   f"k in {{10,100}}, n_rerank={leg['setting']['n_rerank']}",
+                       "setting": leg["setting"],
+                       "index": "the oracle's own float64 build (k-means on 64 x nlist rows, "
+                                f"10 iterations; {leg['build_s']} s, not timed)",
+                       "sample": f"{leg['cores']} pool queries per step (one per core)"},
+            "cpu_baseline": {"value": v, "unit": "queries/s", "cores": leg["cores"],
+                             "kind": "oracle", "cpu": leg["cpu"],
+                             "sample": f"{args.steps} steps x {leg['cores']} queries"},
+            "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+# ---------------------------------------------------------------- profile
 def run_profile(args):
-    """Build, then warm-up + steps batches of each scan mode, nothing else."""
+    """Build the skewed index, then --warmup + --steps searches of one case
+    (nq, uniform nprobe, scan mode[, plain chunk]) and nothing else."""
     import torch
 
     import paper_2605_16007_gb300 as rq
 
     rq.build()
     dev = torch.device("cuda", 0)
-    wl = W.WORKLOADS[WORKLOAD]
+    wl = W.WORKLOADS["skewed"]
     n = args.n or wl["n"]
     x_dev = torch.from_numpy(wl["mix"].base(n)).to(dev)
-    q_dev = torch.from_numpy(wl["mix"].queries(wl["batch"])).to(dev)
-    ix = rq.rq_build(x_dev, wl["nlist"], seed=0, kmeans_iters=wl["iters"])
-    nprobe = args.nprobe or 16
-    k, nrr = wl["k"], wl["n_rerank"]
-    ids = torch.empty((q_dev.shape[0], k), dtype=torch.int64, device=dev)
-    dist = torch.empty((q_dev.shape[0], k), dtype=torch.float32, device=dev)
-    out = {}
-    modes = {"plain": rq.RQ_SCAN_PLAIN, "grouped": rq.RQ_SCAN_GROUPED, "mma": rq.RQ_SCAN_MMA}
-    for name in args.modes.split(","):
-        mode = modes[name]
-        for _ in range(args.warmup + args.steps):
-            st = {}
-            ix.search(q_dev, nprobe, k, nrr, out_ids=ids, out_dist=dist, scan_mode=mode,
-                      stage_times=st)
-        out[name] = {a: round(b, 4) for a, b in st.items()}
-    nc = torch.empty((q_dev.shape[0],), dtype=torch.int32, device=dev)
-    ix.search(q_dev, nprobe, k, nrr, out_ids=ids, out_dist=dist, dump={"n_candidates": nc})
-    c = nc.cpu().numpy()
-    out["candidates_per_query"] = {"mean": float(c.mean()), "p50": float(np.median(c)),
-                                   "max": int(c.max()), "min": int(c.min())}
-    print(json.dumps({"profile": out, "nprobe": nprobe}), flush=True)
+    ix = rq.rq_build(x_dev, wl["nlist"], seed=0, kmeans_iters=wl["iters"], train_size=SKEW_TRAIN)
+    del x_dev
+    parts = [int(v) for v in args.profile.split(",")]
+    nq, nprobe, mode = parts[:3]
+    chunk = parts[3] if len(parts) > 3 else 0
+    q = torch.from_numpy(wl["mix"].queries(nq)).to(dev)
+    ids = torch.empty((nq, 10), dtype=torch.int64, device=dev)
+    dist = torch.empty((nq, 10), dtype=torch.float32, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    out = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        st = {}
+        ix.search(q, nprobe, 10, 1000, out_ids=ids, out_dist=dist, scan_mode=mode,
+                  plain_chunk=chunk, stage_times=st)
+        out.append(st["scan"])
+    print(json.dumps({"profile": args.profile, "scan_ms": out[args.warmup:],
+                      "device_error": ix.device_error()}), flush=True)
+
+
+# ---------------------------------------------------------------- main
+def run_ours(args, rank, world, local, pg):
+    import torch
+
+    import paper_2605_16007_gb300 as rq
+
+    rq.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    res = run_skewed(rq, args, rank, world, local, pg, dev, flush, stream)
+    if not args.no_secondary:
+        res["secondary"] = {"sift1m": run_sift1m(rq, args, rank, world, pg, dev, flush, stream)}
+    return res
 
 
 def main():
     args = parse()
+    if args.cpu_leg:
+        print(json.dumps(cpu_leg(args)), flush=True)
+        return
     if args.profile:
         run_profile(args)
         return
     rank, world, local, pg = dist_setup(args.gpus)
     if args.impl == "reference":
-        if rank != 0:
-            return
-        res = run_reference(args, rank, world, local, pg)
-    else:
-        res = run_ours(args, rank, world, local, pg)
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        if pg is not None:
+            pg.destroy_process_group()
+        return
+    res = run_ours(args, rank, world, local, pg)
     if rank == 0:
         print(json.dumps(res), flush=True)
     if pg is not None:

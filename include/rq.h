@@ -128,12 +128,21 @@ typedef struct rq_search_opts {
   int32_t no_prune;      /* 1: keep every candidate (no bound); default 0 */
   int32_t use_graph;     /* 1: replay the launch sequence from a CUDA graph
                             cached per (stream, shape); default 0 */
-  int32_t reserved;
+  int32_t test_stall;    /* 0 in normal use. Test hook of the failure path:
+                            1 makes the pipelined scan (GROUPED or MMA) hold
+                            back its first stage, so that its bounded wait
+                            (1 ms under this hook) runs out; the search then
+                            returns RQ_ERR_TIMEOUT (synchronous calls) or
+                            leaves the code in rq_device_error. */
   rq_search_dump* dump;  /* NULL, or buffers for the intermediates */
   float* stage_ms;       /* NULL, or host array of RQ_STAGE_COUNT floats that
                             receives each stage's device time (CUDA events on
                             the search stream; the call then waits for the
                             device and does not use a graph) */
+  int32_t plain_chunk;   /* PLAIN: list vectors per thread block, 1024, 2048
+                            or 4096 (0 = 1024, or the tuned size under AUTO;
+                            D_p above 256 always uses 1024) */
+  int32_t reserved;
 } rq_search_opts;
 
 typedef struct rq_stats {
@@ -209,6 +218,15 @@ RQ_API rq_status rq_kmeans(const float* base, int64_t n, int32_t dim, int32_t nl
 RQ_API rq_status rq_philox_gaussian(uint64_t seed, uint32_t stream, int64_t count,
                              double* out);
 
+/* Device-side failures. Kernels that meet an impossible state or whose
+ * bounded wait runs out set the index's error word (rq_device_error). A
+ * search whose call waits for the device (host queries or host outputs)
+ * reads the word before it returns, clears it, and returns RQ_ERR_TIMEOUT
+ * (a bounded wait ran out) or RQ_ERR_DEVICE (any other code); its outputs
+ * are then unspecified. A search that only enqueues work (device queries and
+ * outputs) cannot see the word: its caller checks rq_device_error after
+ * synchronising. */
+
 /* rq_search -- k nearest neighbours of nq queries (Section 2.1.2 query
  * processing; Sections 3.3.1-3.3.4):
  *   1. rotate each query once: q' = P^T q (P^T (q - c) = q' - P^T c),
@@ -245,11 +263,16 @@ RQ_API rq_status rq_search_mixed(rq_index* ix, const float* queries, int64_t nq,
                           int64_t* out_ids, float* out_dist,
                           const rq_search_opts* opts, void* stream);
 
-/* rq_autotune -- time the scan modes and block sizes on `nq` sample queries
- * (host or device, nq x dim) at `nprobe`, `n_rerank`, keep the fastest for
- * RQ_SCAN_AUTO, and append the result to the text file `cache_path` (NULL:
- * no file). A later call with the same index shape and cache file reuses the
- * stored choice without timing. Synchronous. */
+/* rq_autotune -- time the scan forms on `nq` sample queries (host or device,
+ * nq x dim) at `nprobe`, `n_rerank`: the plain scan with 1024-, 2048- and
+ * 4096-vector chunks per thread block, the streaming grouped scan and (D_p =
+ * 128) the tensor-core scan. The fastest becomes the choice of RQ_SCAN_AUTO
+ * for batches of the sample's class: its size and its pair density (nq x
+ * nprobe / nlist), each on a log2 scale; a batch of a class never tuned
+ * takes the nearest tuned class. The result is appended to the text file
+ * `cache_path` (NULL: no file); a later call for the same index shape and
+ * class reuses the stored choice without timing. Every choice returns the
+ * same results. Synchronous. */
 RQ_API rq_status rq_autotune(rq_index* ix, const float* queries, int64_t nq,
                       int32_t nprobe, int32_t n_rerank, const char* cache_path);
 

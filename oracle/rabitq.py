@@ -195,13 +195,50 @@ def assign(x: np.ndarray, c: np.ndarray, chunk: int = 4096):
     return a, dist
 
 
-def update(x: np.ndarray, a: np.ndarray, nlist: int) -> np.ndarray:
+def sqdist_f64(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """||a_i - b_j||^2 for all pairs in float64 as ||a||^2 - 2 <a, b> + ||b||^2
+    (one matrix product). For float32 inputs every product is exact in
+    float64 and the result is within a few float64 ulps of ||a||^2 + ||b||^2
+    of the exact value; used where the float64 independent build needs the
+    plain distance, not the fixed float32 order."""
+    a = np.asarray(a, F64)
+    b = np.asarray(b, F64)
+    d = (a * a).sum(axis=1)[:, None] - 2.0 * (a @ b.T) + (b * b).sum(axis=1)[None, :]
+    return np.maximum(d, 0.0)
+
+
+def _nearest_f64(job):
+    """(rows, centroids) -> nearest centroid of each row and its distance."""
+    x, c = job
+    d = sqdist_f64(x, c)
+    a = np.argmin(d, axis=1)
+    return a, d[np.arange(d.shape[0]), a]
+
+
+def assign_f64(x: np.ndarray, c: np.ndarray, chunk: int = 8192, map_fn=map):
+    """Nearest centroid of each row (Section 2.1.2) by float64 distance
+    (``sqdist_f64``), ties to the lower centroid id. Returns (assignment, its
+    distance). Row chunks are independent; ``map_fn`` (default: the builtin
+    map) may spread them over worker processes."""
+    n = x.shape[0]
+    a = np.empty(n, np.int64)
+    dist = np.empty(n, F64)
+    starts = range(0, n, chunk)
+    for i, (ai, di) in zip(starts, map_fn(_nearest_f64, ((x[i:i + chunk], c) for i in starts))):
+        a[i:i + chunk] = ai
+        dist[i:i + chunk] = di
+    return a, dist
+
+
+def update(x: np.ndarray, a: np.ndarray, nlist: int, dist=None) -> np.ndarray:
     """New centroids: mean of the members, summed in float64 in ascending row
     order, divided in float64, rounded to float32. Empty clusters are then
     re-seeded in ascending id: each takes, from the currently largest cluster
     (ties: lowest id), its member farthest from that cluster's new centroid
-    (ties: lowest row), which moves to the empty cluster.
+    (ties: lowest row), which moves to the empty cluster. ``dist`` is the
+    distance used for that (default: the fixed float32 order).
     """
+    dist = seq_sqdist if dist is None else dist
     n, d = x.shape
     c = np.zeros((nlist, d), F32)
     counts = np.bincount(a, minlength=nlist)
@@ -217,7 +254,7 @@ def update(x: np.ndarray, a: np.ndarray, nlist: int) -> np.ndarray:
     for j in np.flatnonzero(counts == 0):
         donor = int(np.argmax(counts))
         mem = np.flatnonzero(a == donor)
-        dd = seq_sqdist(x[mem], c[donor:donor + 1])[:, 0]
+        dd = dist(x[mem], c[donor:donor + 1])[:, 0]
         far = mem[int(np.argmax(dd))]
         c[j] = x[far]
         a[far] = j
@@ -227,19 +264,23 @@ def update(x: np.ndarray, a: np.ndarray, nlist: int) -> np.ndarray:
 
 
 def kmeans(x: np.ndarray, nlist: int, iters: int, seed: int,
-           n_train: int = 0, return_history: bool = False):
-    """Lloyd iterations from the seeded initial rows (fixed iteration count)."""
+           n_train: int = 0, return_history: bool = False, f64: bool = False,
+           map_fn=map):
+    """Lloyd iterations from the seeded initial rows (fixed iteration count).
+    Distances in the fixed float32 order, or in float64 with ``f64`` (the
+    independent build; ``map_fn`` may spread its row chunks over workers)."""
     n = x.shape[0]
     rows = train_rows(seed, n, n_train)
     xt = x[rows]
     c = x[kmeans_init(seed, n, rows, nlist)].astype(F32)
+    nearest = (lambda xx, cc: assign_f64(xx, cc, map_fn=map_fn)) if f64 else assign
     hist = []
     for _ in range(iters):
-        a, dist = assign(xt, c)
+        a, dist = nearest(xt, c)
         hist.append(float(dist.astype(F64).sum()))
-        c = update(xt, a, nlist)
+        c = update(xt, a, nlist, sqdist_f64 if f64 else None)
     if return_history:
-        a, dist = assign(xt, c)
+        a, dist = nearest(xt, c)
         hist.append(float(dist.astype(F64).sum()))
         return c, hist
     return c
@@ -266,6 +307,13 @@ def encode(x: np.ndarray, c: np.ndarray, a: np.ndarray, P: np.ndarray):
     return pack_bits(bits), r, alpha, z
 
 
+def _encode_rows(job):
+    """(rows, their centroids, P) -> codes, r, alpha of ``encode``."""
+    x, c, P = job
+    codes, r, alpha, _ = encode(x, c, np.arange(x.shape[0]), P)
+    return codes, r, alpha
+
+
 def scan_factors(r32: np.ndarray, alpha32: np.ndarray, dp: int):
     """Per-vector float32 constants of the estimator: r^2 and
     f = r / (sqrt(D_p) * alpha), each a single float32 operation."""
@@ -277,11 +325,18 @@ def scan_factors(r32: np.ndarray, alpha32: np.ndarray, dp: int):
 
 def build_index(x: np.ndarray, nlist: int, seed: int, iters: int = 10,
                 n_train: int = 0, centroids: np.ndarray | None = None,
-                P: np.ndarray | None = None):
-    """Independent float64 index build (k-means, P, encode, list layout).
+                P: np.ndarray | None = None, f64: bool = False, map_fn=map,
+                chunk: int = 1 << 16):
+    """Index build (k-means, P, encode, list layout); P, the residual norms
+    and alpha are always float64.
 
     ``centroids`` and ``P`` may be given to rebuild an index from another
-    build's centroids and rotation (replay of the encode step).
+    build's centroids and rotation (replay of the encode step). With ``f64``
+    the k-means and list assignments use float64 distances (the independent
+    build of the benchmark's CPU baseline); otherwise the fixed float32 order
+    that the GPU build follows. The assignment and the encode work on
+    independent row chunks; ``map_fn`` (default: the builtin map) may spread
+    them over worker processes.
     """
     x = np.asarray(x, F32)
     n, d = x.shape
@@ -289,12 +344,17 @@ def build_index(x: np.ndarray, nlist: int, seed: int, iters: int = 10,
     if P is None:
         P = random_orthogonal(seed, dp)
     if centroids is None:
-        centroids = kmeans(x, nlist, iters, seed, n_train)
-    a, _ = assign(x, centroids)
+        centroids = kmeans(x, nlist, iters, seed, n_train, f64=f64, map_fn=map_fn)
+    a, _ = assign_f64(x, centroids, map_fn=map_fn) if f64 else assign(x, centroids)
     order = np.lexsort((np.arange(n), a))          # list order, then row id
     counts = np.bincount(a, minlength=nlist)
     offsets = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
-    codes, r, alpha, _ = encode(x[order], centroids, a[order], P)
+    starts = range(0, n, chunk)
+    jobs = ((x[order[i:i + chunk]], centroids[a[order[i:i + chunk]]], P) for i in starts)
+    parts = list(map_fn(_encode_rows, jobs))
+    codes = np.concatenate([p[0] for p in parts]) if parts else np.zeros((0, dp // 8), np.uint8)
+    r = np.concatenate([p[1] for p in parts]) if parts else np.zeros(0)
+    alpha = np.concatenate([p[2] for p in parts]) if parts else np.zeros(0)
     r32, al32 = r.astype(F32), alpha.astype(F32)
     r2, f = scan_factors(r32, al32, dp)
     cR = (pad(centroids.astype(F64), dp) @ P).astype(F32)

@@ -45,8 +45,9 @@ class SearchDump(C.Structure):
 
 class SearchOpts(C.Structure):
     _fields_ = [("scan_mode", C.c_int32), ("no_prune", C.c_int32),
-                ("use_graph", C.c_int32), ("reserved", C.c_int32),
-                ("dump", C.POINTER(SearchDump)), ("stage_ms", C.POINTER(C.c_float))]
+                ("use_graph", C.c_int32), ("test_stall", C.c_int32),
+                ("dump", C.POINTER(SearchDump)), ("stage_ms", C.POINTER(C.c_float)),
+                ("plain_chunk", C.c_int32), ("reserved", C.c_int32)]
 
 
 STAGES = ("rotate", "probe", "quantize", "bound", "worklist", "scan", "select", "rerank")
@@ -218,8 +219,9 @@ def rq_version() -> int:
     return lib().rq_version()
 
 
-def _opts(scan_mode, no_prune, use_graph, dump, stage_ms=None):
-    o = SearchOpts(scan_mode, int(no_prune), int(use_graph), 0, None, None)
+def _opts(scan_mode, no_prune, use_graph, dump, stage_ms=None, test_stall=False, plain_chunk=0):
+    o = SearchOpts(scan_mode, int(no_prune), int(use_graph), int(test_stall), None, None,
+                   int(plain_chunk), 0)
     if stage_ms is not None:
         o.stage_ms = stage_ms
     if dump is not None:
@@ -239,14 +241,16 @@ class Index:
     # -- search ----------------------------------------------------------
     def rq_search(self, queries, nprobe: int, k: int, n_rerank: int, out_ids=None,
                   out_dist=None, scan_mode: int = RQ_SCAN_AUTO, no_prune: bool = False,
-                  use_graph: bool = False, dump=None, stream=None, stage_times=None):
-        """stage_times: a dict that receives each stage's device time (ms)."""
+                  use_graph: bool = False, dump=None, stream=None, stage_times=None,
+                  test_stall: bool = False, plain_chunk: int = 0):
+        """stage_times: a dict that receives each stage's device time (ms).
+        test_stall: the failure-path test hook of rq_search_opts."""
         nq = _shape(queries)[0]
         if out_ids is None:
             out_ids = np.empty((nq, k), np.int64)
             out_dist = np.empty((nq, k), np.float32)
         ms = (C.c_float * len(STAGES))() if stage_times is not None else None
-        o = _opts(scan_mode, no_prune, use_graph, dump, ms)
+        o = _opts(scan_mode, no_prune, use_graph, dump, ms, test_stall, plain_chunk)
         _check(lib().rq_search(self.h, _ptr(queries), nq, nprobe, k, n_rerank,
                                _ptr(out_ids), _ptr(out_dist), C.byref(o),
                                _stream_ptr(stream)))
@@ -259,7 +263,7 @@ class Index:
     def rq_search_mixed(self, queries, nprobe, k, n_rerank, k_stride=None, out_ids=None,
                         out_dist=None, scan_mode: int = RQ_SCAN_AUTO,
                         no_prune: bool = False, use_graph: bool = False, dump=None,
-                        stream=None):
+                        stream=None, stage_times=None, plain_chunk: int = 0):
         nq = _shape(queries)[0]
         nprobe = np.ascontiguousarray(nprobe, np.int32)
         k = np.ascontiguousarray(k, np.int32)
@@ -269,10 +273,13 @@ class Index:
         if out_ids is None:
             out_ids = np.empty((nq, k_stride), np.int64)
             out_dist = np.empty((nq, k_stride), np.float32)
-        o = _opts(scan_mode, no_prune, use_graph, dump)
+        ms = (C.c_float * len(STAGES))() if stage_times is not None else None
+        o = _opts(scan_mode, no_prune, use_graph, dump, ms, False, plain_chunk)
         _check(lib().rq_search_mixed(self.h, _ptr(queries), nq, _ptr(nprobe), _ptr(k),
                                      _ptr(n_rerank), k_stride, _ptr(out_ids),
                                      _ptr(out_dist), C.byref(o), _stream_ptr(stream)))
+        if stage_times is not None:
+            stage_times.update({name: ms[i] for i, name in enumerate(STAGES)})
         return out_ids, out_dist
 
     search_mixed = rq_search_mixed

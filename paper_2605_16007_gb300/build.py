@@ -3,6 +3,12 @@
 Each ``csrc/*.cu`` file is compiled by its own nvcc process (in parallel),
 then linked with a static CUDA runtime into ``_build/librq.so``. A file is
 recompiled only when it or a header changed.
+
+With the environment variable ``RQ_CHECKS=1`` the checked build is made and
+loaded instead (``_build_checked/librq.so``, compiled with -DRQ_CHECKS=1):
+its kernels test their output and candidate-slot indexes against the
+buffers and report a bad one through the index's error word
+(``rq_device_error``) instead of accessing it.
 """
 from __future__ import annotations
 
@@ -14,7 +20,8 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-OUT_DIR = os.path.join(HERE, "_build")
+CHECKED = os.environ.get("RQ_CHECKS", "0") == "1"
+OUT_DIR = os.path.join(HERE, "_build_checked" if CHECKED else "_build")
 LIB = os.path.join(OUT_DIR, "librq.so")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
@@ -22,7 +29,7 @@ INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr",
-         "-I" + INCLUDE, "-I" + CSRC]
+         "-I" + INCLUDE, "-I" + CSRC] + (["-DRQ_CHECKS=1"] if CHECKED else [])
 
 
 def nvcc() -> str:
@@ -56,7 +63,8 @@ def _compile(src: str, extra, verbose: bool) -> str:
 
 
 def build(verbose: bool = False, extra_flags=()) -> str:
-    """Build librq.so if needed; returns its path."""
+    """Build librq.so if needed; returns its path. ``extra_flags`` force a
+    rebuild with those nvcc flags added."""
     os.makedirs(OUT_DIR, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     extra = list(extra_flags)

@@ -627,7 +627,9 @@ rq_status rq_search_mixed(rq_index* ix, const float* queries, int64_t nq, const 
 
 rq_status rq_autotune(rq_index* ix, const float* queries, int64_t nq, int32_t nprobe,
                       int32_t n_rerank, const char* cache_path) {
-  return autotune(ix, queries, nq, nprobe, n_rerank, cache_path);
+  if (nq < 1) return fail(RQ_ERR_INVALID_ARG, "nq < 1");
+  std::vector<int32_t> np(nq, nprobe);
+  return autotune(ix, queries, nq, np.data(), n_rerank, cache_path);
 }
 
 rq_status rq_get_stats(const rq_index* ix, rq_stats* out) {

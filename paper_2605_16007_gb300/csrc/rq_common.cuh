@@ -15,11 +15,28 @@ enum DeviceError : int32_t {
   kErrCandidateOverflow = 1,
   kErrBadProbe = 2,
   kErrSelectOverflow = 3,
-  kErrMmaTimeout = 4,
+  kErrMmaTimeout = 4,     // a bounded wait of the tensor-core scan ran out
+  kErrScanTimeout = 5,    // a bounded wait of the streaming scan ran out
+  kErrBadIndex = 6,       // (checked builds) an index fell outside its buffer
 };
+
 
 __device__ __forceinline__ void flag_error(int32_t* err, int32_t code) {
   if (err) atomicCAS(err, 0, code);
+}
+
+// Checked builds (-DRQ_CHECKS=1) test the indexes of the scan output and of
+// the candidate slots against their buffers; a bad one sets kErrBadIndex in
+// the error word and the access is skipped. Normal builds compile the checks
+// away.
+#ifndef RQ_CHECKS
+#define RQ_CHECKS 0
+#endif
+__device__ __forceinline__ bool index_ok(int64_t i, int64_t n, int32_t* err) {
+  if (!RQ_CHECKS) return true;
+  if (i >= 0 && i < n) return true;
+  flag_error(err, kErrBadIndex);
+  return false;
 }
 
 // ---------------------------------------------------------------------------

@@ -9,7 +9,9 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <algorithm>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 #include "rq.h"
@@ -48,11 +50,30 @@ struct SearchShape {
   int k_stride;   // output row stride
   int mode;       // resolved scan mode
   int prune;
+  int withhold;   // test hook: the pipelined scan withholds its first stage
+  int chunk;      // plain scan: list vectors per block (a multiple of 1024)
   bool operator<(const SearchShape& o) const {
-    return std::tie(nq, npmax, nsel_max, k_stride, mode, prune) <
-           std::tie(o.nq, o.npmax, o.nsel_max, o.k_stride, o.mode, o.prune);
+    return std::tie(nq, npmax, nsel_max, k_stride, mode, prune, withhold, chunk) <
+           std::tie(o.nq, o.npmax, o.nsel_max, o.k_stride, o.mode, o.prune, o.withhold,
+                    o.chunk);
   }
 };
+
+// What the autotuner chose for one class of batches.
+struct TunedChoice {
+  int mode = RQ_SCAN_GROUPED;
+  int chunk = 1024;
+};
+
+// The class of a batch for the autotuner: its size and its pair density
+// (pairs per list), each on a log2 scale, so that one choice serves the
+// batches that stress the scan alike.
+inline std::pair<int, int> tune_class(int64_t nq, int64_t sum_nprobe, int nlist) {
+  int a = 0, b = 0;
+  for (int64_t v = nq; v > 1; v >>= 1) ++a;
+  for (int64_t v = (8 * sum_nprobe) / std::max(1, nlist); v > 1; v >>= 1) ++b;
+  return {a, b};
+}
 
 // Device workspace of one search shape, carved out of one allocation.
 struct Workspace {
@@ -87,11 +108,12 @@ struct Workspace {
   // grouped scans: (query, probe) pairs bucketed by list
   int32_t* list_count = nullptr;  // nlist: pairs probing each list
   int32_t* list_pairs = nullptr;  // nlist x nq: pair ids (q * npmax + p) per list
-  int32_t* work_count = nullptr;  // work-item counter of the persistent scan
   int32_t* nchunks = nullptr;     // plain scan: nq x npmax chunk counts
   uint8_t* qdig = nullptr;        // nlist x nq x D_p: per-list buckets of FP8 query digits
   float4* qpb = nullptr;          // nlist x nq (+2): per-list buckets of {vl, delta, nq2, -Sq},
                                   // interleaved by slot couples
+  uint8_t* qrec = nullptr;        // nlist x nq pair records of the streaming scan
+                                  // (pair_rec_bytes(D_p) each)
   int64_t mwords = 0;             // mask words per query
   int64_t cap = 0;                // key slots per query (32 mwords)
 };
@@ -102,6 +124,7 @@ struct Plan {
   Workspace ws;
   cudaGraphExec_t graph = nullptr;
   int32_t* h_params = nullptr;          // pinned staging of per-query parameters
+  int32_t* h_err = nullptr;             // pinned copy of the device error word
   cudaEvent_t params_ready = nullptr;   // the last copy out of h_params has run
   uint64_t last_use = 0;
 };
@@ -134,8 +157,10 @@ struct rq_index {
   std::vector<int64_t> top_len_prefix;    // sum of the j largest list lengths
   std::vector<int64_t> top_words_prefix;  // sum of the j largest ceil(length / 32)
   int64_t max_list_len = 0;
-  // tuned choice for RQ_SCAN_AUTO
+  // tuned choices for RQ_SCAN_AUTO: per batch class (tune_class), and the
+  // latest one as the default for classes never tuned
   std::atomic<int> auto_mode{RQ_SCAN_GROUPED};
+  std::map<std::pair<int, int>, rq::TunedChoice> tuned;  // guarded by mu
   // plans (workspaces, graphs) per (stream, shape)
   std::mutex mu;
   std::map<std::pair<cudaStream_t, rq::SearchShape>, std::unique_ptr<rq::Plan>> plans;
@@ -163,7 +188,7 @@ rq_status search_run(rq_index* ix, const float* queries, int64_t nq,
                      const int32_t* n_rerank, int k_stride, int64_t* out_ids,
                      float* out_dist, const rq_search_opts* opts,
                      cudaStream_t stream);
-rq_status autotune(rq_index* ix, const float* queries, int64_t nq, int nprobe,
+rq_status autotune(rq_index* ix, const float* queries, int64_t nq, const int32_t* nprobe,
                    int n_rerank, const char* cache_path);
 void free_plans(rq_index* ix);
 

@@ -7,13 +7,7 @@
 
 namespace rq {
 
-constexpr int kGroupVectors = 256;  // vectors per grouped work item (one per thread)
-
-// Pairs per grouped work item: query planes of the group sit in shared memory.
-template <int NW4>
-struct GroupPairs {
-  static constexpr int value = (NW4 <= 8) ? 64 : 32;
-};
+constexpr int kGroupVectors = 256;  // vectors per work item of the persistent scans
 
 // With ip = sum_d bit_d q_u,d (bit-planes: ip = sum_j 2^j popc(code & plane_j))
 // and pc = popc(code):
@@ -54,9 +48,11 @@ __device__ __forceinline__ float estimate_regs(const uint4 (&code)[NW4], int pc,
 // 32-vector words; word w of probe p of query q has the fixed mask index
 // x = q * mwords + wbase[q, p] + w (bit i set: vector 32 w + i of the list
 // passed the query's bound) and 32 key slots from 32 x, where the keys of the
-// passing vectors are packed in lane order. A warp holds one word (lane i =
-// vector 32 w + i); every word of every probed list is written on every
-// search, so neither buffer is cleared.
+// passing vectors are packed in lane order. A key is (orderable estimate,
+// slot of the vector in the list layout); the finalize kernel replaces the
+// slot by the row id when it collects the candidates. A warp holds one word
+// (lane i = vector 32 w + i); every word of every probed list is written on
+// every search, so neither buffer is cleared.
 __device__ __forceinline__ void emit_word(bool pass, float d, uint32_t id, int64_t widx,
                                           uint32_t* __restrict__ mask,
                                           uint64_t* __restrict__ cand, int lane) {
@@ -111,10 +107,19 @@ __device__ __forceinline__ uint8_t e4m3_of_int(int v) {
   return (uint8_t)(((e + 7) << 3) | m);
 }
 
+// Bytes of one pair record of the streaming scan: the four bit-planes
+// (4 x D_p/8 bytes), then {vl, delta, nq2, Sq (int bits)} and {query, first
+// mask word, bound, 0}, 16 bytes each.
+__host__ __device__ constexpr int pair_rec_bytes(int dp) { return dp / 2 + 32; }
+
+// Streaming popcount scan (rq_scan_stream.cu).
+rq_status launch_scan_stream(rq_index* ix, const SearchShape& sh, Workspace& ws, cudaStream_t st,
+                             int sms, uint64_t wait_ns, int withhold);
+
 // Tensor-core scan (rq_scan_mma.cu).
 bool mma_supported(const rq_index* ix);
 rq_status launch_scan_mma(rq_index* ix, const SearchShape& sh, Workspace& ws, cudaStream_t st,
-                          int sms);
+                          int sms, int withhold);
 int next_pow2_host(int64_t v);
 
 }  // namespace rq

@@ -21,6 +21,9 @@
 // float32 estimator epilogue, so all eight warps share the epilogue.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
+#include "rq_async.cuh"
 #include "rq_common.cuh"
 #include "rq_scan.cuh"
 
@@ -33,7 +36,6 @@ constexpr int kMmaK = 128;        // D_p
 constexpr int kItemV = kGroupVectors;  // 256 vectors per work item = 2 tiles
 constexpr int kConsumers = 256;   // eight warps: expansion, MMA issue, epilogue
 constexpr int kMmaThreads = kConsumers + 32;  // plus one producer warp
-constexpr uint64_t kWaitNs = 2000000000ull;  // an mbarrier wait gives up after 2 s
 constexpr int kTmemCols = 2 * kMmaNmax;    // one accumulator per tile of the item
 
 // Shared memory of one block (offsets from a 1024-byte aligned base).
@@ -45,70 +47,17 @@ constexpr int kSmFac = kSmCode + 2 * kItemV * 16;        // 2 stages x 258 x 8 B
 constexpr int kSmQp = kSmFac + 2 * kFacBytes;            // 2 stages x 64 x 16 B
 constexpr int kSmTau = kSmQp + 2 * kMmaNmax * 16;        // 2 stages x 64 x uint32
 constexpr int kSmWrow = kSmTau + 2 * kMmaNmax * 4;       // 2 stages x 64 x int64 mask rows
-constexpr int kIdBytes = (kItemV + 4) * 4;               // +3 for alignment, rounded
-constexpr int kSmIds = kSmWrow + 2 * kMmaNmax * 8;       // 2 stages x 260 x uint32 row ids
-constexpr int kSmBar = kSmIds + 2 * kIdBytes;            // mbarriers: full[2], empty[2], mma, aux
+constexpr int kSmBar = kSmWrow + 2 * kMmaNmax * 8;       // mbarriers: full[2], empty[2], mma, aux
 constexpr int kSmMeta = kSmBar + 6 * 8;                  // 2 stages x 32-byte meta
 constexpr int kSmTmem = kSmMeta + 2 * 32;                // TMEM base address
 constexpr int kSmBytes = kSmTmem + 4;
 constexpr int kSmAlloc = kSmBytes + 1024;                // room to align the base
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx_arrive(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ uint64_t globaltimer_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Waits for the phase with the given parity; false after kWaitNs (the block
-// then stops and reports through the error word).
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  const uint64_t t0 = globaltimer_ns();
-  for (uint32_t i = 0;; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 15u) == 15u && globaltimer_ns() - t0 > kWaitNs) return false;
-  }
-}
-__device__ __forceinline__ void fence_barrier_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-// TMA bulk copy global -> shared (16-byte aligned addresses, size a multiple
-// of 16), completing on an mbarrier's transaction count.
-__device__ __forceinline__ void tma_load_1d(uint32_t dst, const void* src, uint32_t bytes,
-                                            uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
 }
 __device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
@@ -202,115 +151,146 @@ __device__ __forceinline__ uint32_t nibble_to_e4m3(uint32_t n) {
   return ((n * 0x00204081u) & 0x01010101u) * 0x38u;
 }
 
-// Work item meta of one stage: list (-1: no more items), first slot, vectors,
-// pairs, first vector within the list.
+// Work item meta of one stage: first slot, list (-1: no more items),
+// vectors, pairs, first vector within the list.
 struct Meta {
-  int l, lo, nvec, cnt, v0, pad0, pad1, pad2;
+  long long lo;
+  int l, nvec, cnt, v0, pad0, pad1;
 };
 
 __device__ __forceinline__ void named_bar_consumers() {
   asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory");
 }
 
-// Producer (the whole warp): once a stage is free, take the next item from
-// the global counter (no earlier, so that near the end no block holds items
-// that another, idle block could run) and fill the stage -- meta, the mask rows and bounds of the first group (one pair per
-// lane), then lane 0 issues the TMA copies of codes, factors, row ids, B tile
-// and parameters, all completing on the stage's `full` barrier. A stage is
-// reused once its `empty` barrier shows the consumers are done with it.
+// Producer (the whole warp). Block b of G takes the static items b, b + G,
+// b + 2G, ... (longest lists first): the warp reads 32 of them at once (one
+// per lane: item, pair count, offsets) and keeps those whose list is probed,
+// so unprobed lists cost no further load. For each kept item, once a stage is
+// free (its `empty` barrier), it writes the meta and the mask rows and bounds
+// of the first group (one pair per lane), then lane 0 issues the TMA copies of
+// codes, factors, B tile and parameters, all completing on the
+// stage's `full` barrier.
 __device__ void producer_loop(uint8_t* sm, uint32_t sbase, const int2* __restrict__ items,
-                              int n_items, int32_t* __restrict__ work_counter,
-                              const int32_t* __restrict__ list_count,
+                              int n_items, const int32_t* __restrict__ list_count,
                               const int32_t* __restrict__ list_pairs, int64_t pair_stride,
                               int npmax, const int64_t* __restrict__ offsets,
                               const uint8_t* __restrict__ codes, const float2* __restrict__ fac,
-                              const uint32_t* __restrict__ ids,
                               const uint8_t* __restrict__ qdb, const float4* __restrict__ qpb,
                               const uint32_t* __restrict__ bound,
-                              const int32_t* __restrict__ wbase, int64_t mwords, int32_t* err) {
+                              const int32_t* __restrict__ wbase, int64_t mwords, int32_t* err,
+                              uint64_t wait_ns, int withhold) {
   const int lane = threadIdx.x & 31;
   Meta* meta = reinterpret_cast<Meta*>(sm + kSmMeta);
-  for (int i = 0;; ++i) {
-    const int st = i & 1;
-    const uint32_t full = sbase + kSmBar + 8 * st;
-    const uint32_t empty = sbase + kSmBar + 16 + 8 * st;
-    if (i >= 2) {
-      int ok = 1;
-      if (lane == 0) ok = mbar_wait_bounded(empty, (uint32_t)(((i >> 1) - 1) & 1)) ? 1 : 0;
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) {
-        if (lane == 0) {
-          flag_error(err, kErrMmaTimeout);
-          meta[st].l = -1;
-          mbar_expect_tx_arrive(full, 0);
-        }
-        return;
+  const int64_t G = gridDim.x;
+  int i = 0;                       // items issued
+  int last_copy[2] = {-1, -1};     // last item whose copies went into each stage
+  bool ok = true;
+  auto claim = [&](int it) -> bool {
+    if (it < 2) return true;
+    int r = 1;
+    if (lane == 0)
+      r = mbar_wait_bounded(sbase + kSmBar + 16 + 8 * (it & 1), (uint32_t)(((it >> 1) - 1) & 1),
+                            wait_ns)
+              ? 1
+              : 0;
+    return __shfl_sync(0xffffffffu, r, 0) != 0;
+  };
+  for (int64_t base = blockIdx.x; ok && base < n_items; base += 32 * G) {
+    const int64_t idx = base + lane * G;
+    int l = 0, cnt = 0, nvec = 0, v0 = 0;
+    long long lo = 0;
+    if (idx < n_items) {
+      const int2 w = items[idx];
+      l = w.x;
+      v0 = w.y;
+      cnt = list_count[l];
+      if (cnt > 0) {
+        lo = offsets[l] + v0;
+        nvec = (int)min((long long)kItemV, (long long)offsets[l + 1] - lo);
       }
     }
-    int it = 0;
-    if (lane == 0) it = atomicAdd(work_counter, 1);
-    it = __shfl_sync(0xffffffffu, it, 0);
-    if (it >= n_items) {
+    uint32_t work = __ballot_sync(0xffffffffu, cnt > 0);
+    while (work) {
+      const int j = __ffs(work) - 1;
+      work &= work - 1;
+      const int jl = __shfl_sync(0xffffffffu, l, j);
+      const int jc = __shfl_sync(0xffffffffu, cnt, j);
+      const int jn = __shfl_sync(0xffffffffu, nvec, j);
+      const int jv0 = __shfl_sync(0xffffffffu, v0, j);
+      const long long jlo = __shfl_sync(0xffffffffu, lo, j);
+      if (!claim(i)) {
+        ok = false;
+        break;
+      }
+      const int st = i & 1;
+      const uint32_t full = sbase + kSmBar + 8 * st;
+      const int np = min(kMmaNmax, jc);
+      const int32_t* lp = list_pairs + (int64_t)jl * pair_stride;
+      uint32_t* tau = reinterpret_cast<uint32_t*>(sm + kSmTau) + st * kMmaNmax;
+      int64_t* wrow = reinterpret_cast<int64_t*>(sm + kSmWrow) + st * kMmaNmax;
+      for (int g = lane; g < np; g += 32) {
+        const int pair = lp[g];
+        const int q = pair / npmax;
+        wrow[g] = (int64_t)q * mwords + wbase[pair];
+        tau[g] = bound[q];
+      }
+      __syncwarp();
       if (lane == 0) {
-        meta[st].l = -1;
-        mbar_expect_tx_arrive(full, 0);
+        meta[st].lo = jlo;
+        meta[st].l = jl;
+        meta[st].nvec = jn;
+        meta[st].cnt = jc;
+        meta[st].v0 = jv0;
+        if (!(withhold && i == 0)) {
+          const long long lo_al = jlo & ~1ll;
+          const uint32_t fac_bytes = (uint32_t)((((jlo - lo_al) + jn) * 8 + 15) & ~15ll);
+          const uint32_t code_bytes = (uint32_t)jn * 16;
+          const uint32_t b_bytes = (uint32_t)np * kMmaK;
+          const uint32_t qp_bytes = (uint32_t)((np + 1) & ~1) * 16;
+          mbar_expect_tx_arrive(full, code_bytes + fac_bytes + b_bytes + qp_bytes);
+          tma_load_1d(sbase + kSmCode + st * kItemV * 16, codes + jlo * 16, code_bytes, full);
+          tma_load_1d(sbase + kSmFac + st * kFacBytes, fac + lo_al, fac_bytes, full);
+          tma_load_1d(sbase + kSmB + st * kMmaNmax * kMmaK,
+                      qdb + (int64_t)jl * pair_stride * kMmaK, b_bytes, full);
+          tma_load_1d(sbase + kSmQp + st * kMmaNmax * 16, qpb + (int64_t)jl * pair_stride,
+                      qp_bytes, full);
+          last_copy[st] = i;
+        }
+        // (test hook: with `withhold`, the first stage is never filled nor
+        // signalled, so the consumers' bounded wait for it runs out)
       }
-      return;
-    }
-    const int2 w = items[it];
-    const int l = w.x;
-    const int cnt = list_count[l];
-    const int64_t lo = offsets[l] + w.y;
-    const int nvec = (int)min((int64_t)kItemV, offsets[l + 1] - lo);
-    const int np = min(kMmaNmax, cnt);
-    const int32_t* lp = list_pairs + (int64_t)l * pair_stride;
-    uint32_t* tau = reinterpret_cast<uint32_t*>(sm + kSmTau) + st * kMmaNmax;
-    int64_t* wrow = reinterpret_cast<int64_t*>(sm + kSmWrow) + st * kMmaNmax;
-    for (int g = lane; g < np; g += 32) {
-      const int pair = lp[g];
-      const int q = pair / npmax;
-      wrow[g] = (int64_t)q * mwords + wbase[pair];
-      tau[g] = bound[q];
-    }
-    __syncwarp();
-    if (lane == 0) {
-      meta[st].l = l;
-      meta[st].lo = (int)lo;
-      meta[st].nvec = nvec;
-      meta[st].cnt = cnt;
-      meta[st].v0 = w.y;
-      if (cnt == 0) {
-        mbar_expect_tx_arrive(full, 0);
-      } else {
-        const int64_t lo_al = lo & ~(int64_t)1;
-        const uint32_t fac_bytes = (uint32_t)((((lo - lo_al) + nvec) * 8 + 15) & ~15);
-        const int64_t lo_al4 = lo & ~(int64_t)3;
-        const uint32_t id_bytes = (uint32_t)((((lo - lo_al4) + nvec) * 4 + 15) & ~15);
-        const uint32_t code_bytes = (uint32_t)nvec * 16;
-        const uint32_t b_bytes = (uint32_t)np * kMmaK;
-        const uint32_t qp_bytes = (uint32_t)((np + 1) & ~1) * 16;
-        mbar_expect_tx_arrive(full, code_bytes + fac_bytes + id_bytes + b_bytes + qp_bytes);
-        tma_load_1d(sbase + kSmCode + st * kItemV * 16, codes + lo * 16, code_bytes, full);
-        tma_load_1d(sbase + kSmFac + st * kFacBytes, fac + lo_al, fac_bytes, full);
-        tma_load_1d(sbase + kSmIds + st * kIdBytes, ids + lo_al4, id_bytes, full);
-        tma_load_1d(sbase + kSmB + st * kMmaNmax * kMmaK, qdb + (int64_t)l * pair_stride * kMmaK,
-                    b_bytes, full);
-        tma_load_1d(sbase + kSmQp + st * kMmaNmax * 16, qpb + (int64_t)l * pair_stride, qp_bytes,
-                    full);
-      }
+      __syncwarp();
+      ++i;
     }
   }
+  if (ok && claim(i)) {
+    if (lane == 0) {
+      meta[i & 1].l = -1;
+      mbar_expect_tx_arrive(sbase + kSmBar + 8 * (i & 1), 0);
+    }
+  } else {
+    ok = false;
+  }
+  if (lane == 0 && !ok) {
+    flag_error(err, kErrMmaTimeout);
+    // After a wait ran out the consumers may have left: the copies still in
+    // flight land before the block returns.
+    for (int s = 0; s < 2; ++s)
+      if (last_copy[s] >= 0)
+        mbar_wait_bounded(sbase + kSmBar + 8 * s, (uint32_t)((last_copy[s] >> 1) & 1), wait_ns);
+  }
+  __syncwarp();
 }
 
 __global__ void __launch_bounds__(kMmaThreads, 3)
-scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict__ work_counter,
+scan_mma_kernel(const int2* __restrict__ items, int n_items,
                 const int32_t* __restrict__ list_count, const int32_t* __restrict__ list_pairs,
                 int64_t pair_stride, const float4* __restrict__ qpb,
                 const uint8_t* __restrict__ qdb, int npmax, const int64_t* __restrict__ offsets,
                 const uint8_t* __restrict__ codes, const float2* __restrict__ fac,
-                const uint32_t* __restrict__ ids, const uint32_t* __restrict__ bound,
+                const uint32_t* __restrict__ bound,
                 const int32_t* __restrict__ wbase, int64_t mwords, uint32_t* __restrict__ mask,
-                uint64_t* __restrict__ cand, int32_t* err) {
+                uint64_t* __restrict__ cand, int32_t* err, uint64_t wait_ns, int withhold) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ volatile int s_ok[4];  // results of the polled waits
   const uint32_t raw_addr = smem_u32(smem_raw);
@@ -336,8 +316,8 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
   const uint32_t taddr = *s_tmem;
 
   if (warp == kConsumers / 32) {
-    producer_loop(sm, sbase, items, n_items, work_counter, list_count, list_pairs, pair_stride,
-                    npmax, offsets, codes, fac, ids, qdb, qpb, bound, wbase, mwords, err);
+    producer_loop(sm, sbase, items, n_items, list_count, list_pairs, pair_stride, npmax, offsets,
+                  codes, fac, qdb, qpb, bound, wbase, mwords, err, wait_ns, withhold);
   } else {
     uint32_t ph_mma = 0, ph_aux = 0;
     bool abort = false;
@@ -347,7 +327,7 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
       const uint32_t empty = sbase + kSmBar + 16 + 8 * st;
       // One thread polls each mbarrier; the others wait at the named
       // barrier, which orders the observed data for them, without issuing.
-      if (tid == 0) s_ok[0] = mbar_wait_bounded(full, (uint32_t)((i >> 1) & 1)) ? 1 : 0;
+      if (tid == 0) s_ok[0] = mbar_wait_bounded(full, (uint32_t)((i >> 1) & 1), wait_ns) ? 1 : 0;
       named_bar_consumers();
       if (!s_ok[0]) abort = true;
       const Meta m = meta[st];
@@ -358,8 +338,6 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
       const float4* qp_s = reinterpret_cast<const float4*>(sm + kSmQp + st * kMmaNmax * 16);
       uint32_t* s_tau = reinterpret_cast<uint32_t*>(sm + kSmTau) + st * kMmaNmax;
       int64_t* s_wrow = reinterpret_cast<int64_t*>(sm + kSmWrow) + st * kMmaNmax;
-      const uint32_t* ids_s = reinterpret_cast<const uint32_t*>(sm + kSmIds + st * kIdBytes) +
-                              (m.lo & 3);
       const int32_t* lp = list_pairs + (int64_t)m.l * pair_stride;
       const uint64_t bdesc = sdesc_sw128(sbase + kSmB + st * kMmaNmax * kMmaK);
       for (int g0 = 0; g0 < m.cnt && !abort; g0 += kMmaNmax) {
@@ -383,7 +361,7 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
             s_wrow[g] = (int64_t)q * mwords + wbase[pair];
             s_tau[g] = bound[q];
           }
-          if (tid == 0) s_ok[2] = mbar_wait_bounded(bar_aux, ph_aux) ? 1 : 0;
+          if (tid == 0) s_ok[2] = mbar_wait_bounded(bar_aux, ph_aux, wait_ns) ? 1 : 0;
           ph_aux ^= 1u;
           named_bar_consumers();
           if (!s_ok[2]) abort = true;
@@ -421,7 +399,7 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
           mma_commit(bar_mma);
         }
         if (abort) break;
-        if (tid == 0) s_ok[1] = mbar_wait_bounded(bar_mma, ph_mma) ? 1 : 0;
+        if (tid == 0) s_ok[1] = mbar_wait_bounded(bar_mma, ph_mma, wait_ns) ? 1 : 0;
         ph_mma ^= 1u;
         named_bar_consumers();
         if (!s_ok[1]) {
@@ -485,9 +463,8 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
                   if (valid && g + 1 < np && orderable(dd.y) <= tt.y) passbits |= 2u << (2 * h);
                 }
               }
-              const uint32_t id = passbits ? ids_s[v] : 0u;
-              emit_chunk<8>(passbits, d, s_wrow + c1, np - c1, word, warp * 32 < m.nvec, id, mask,
-                            cand, lane);
+              emit_chunk<8>(passbits, d, s_wrow + c1, np - c1, word, warp * 32 < m.nvec,
+                            (uint32_t)(m.lo + v), mask, cand, lane);
             }
           }
         }
@@ -503,7 +480,7 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
     if (abort && tid == 0) flag_error(err, kErrMmaTimeout);
     if (abort) {
       // An MMA may still be in flight: give it a bounded time to land.
-      mbar_wait_bounded(bar_mma, ph_mma);
+      mbar_wait_bounded(bar_mma, ph_mma, wait_ns);
     }
   }
   tc_fence_before();
@@ -517,15 +494,16 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict
 bool mma_supported(const rq_index* ix) { return ix->dp == kMmaK; }
 
 rq_status launch_scan_mma(rq_index* ix, const SearchShape& sh, Workspace& ws, cudaStream_t st,
-                          int sms) {
+                          int sms, int withhold) {
   if (ix->dp != kMmaK) return fail(RQ_ERR_NOT_IMPLEMENTED, "tensor-core scan built for D_p = 128");
   RQ_TRY(allow_dynamic_smem((const void*)scan_mma_kernel, kSmAlloc));
   // Three blocks per SM (registers; ~69 KB of shared memory each); their
   // TMEM (128 columns each) stays within the SM's 512 columns.
-  scan_mma_kernel<<<(unsigned)(sms * 3), kMmaThreads, kSmAlloc, st>>>(
-      ix->items, ix->n_items, ws.work_count, ws.list_count, ws.list_pairs, sh.nq, ws.qpb, ws.qdig,
-      sh.npmax, ix->offsets, ix->codes, ix->fac, ix->ids, ws.bound, ws.wbase, ws.mwords, ws.mask,
-      ws.cand, ix->d_err);
+  const unsigned grid = (unsigned)std::max(1, std::min(sms * 3, ix->n_items));
+  scan_mma_kernel<<<grid, kMmaThreads, kSmAlloc, st>>>(
+      ix->items, ix->n_items, ws.list_count, ws.list_pairs, sh.nq, ws.qpb, ws.qdig, sh.npmax,
+      ix->offsets, ix->codes, ix->fac, ws.bound, ws.wbase, ws.mwords, ws.mask, ws.cand,
+      ix->d_err, withhold ? kTestWaitLimitNs : kWaitLimitNs, withhold);
   RQ_CUDA(cudaGetLastError());
   return RQ_OK;
 }

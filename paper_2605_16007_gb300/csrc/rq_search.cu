@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "rq_async.cuh"
 #include "rq_common.cuh"
 #include "rq_internal.h"
 #include "rq_pairdist.cuh"
@@ -159,7 +160,8 @@ __device__ __forceinline__ void quantize_pair(int64_t pair, int64_t q, int c, in
                                               int32_t* __restrict__ list_count,
                                               int32_t* __restrict__ list_pairs,
                                               uint8_t* __restrict__ qdb,
-                                              float4* __restrict__ qpb) {
+                                              float4* __restrict__ qpb,
+                                              uint8_t* __restrict__ qrec, uint64_t* slot_out) {
   constexpr int PER = 4 * NW4;  // values per lane (dp / 32)
   // Grouped scans: the pair takes the next slot of its list's bucket (room
   // for every query of the batch).
@@ -168,6 +170,12 @@ __device__ __forceinline__ void quantize_pair(int64_t pair, int64_t q, int c, in
     if (lane == 0) slot = atomicAdd(&list_count[c], 1);
     slot = __shfl_sync(0xffffffffu, slot, 0);
   }
+  // Streaming scan: the pair's record in its list's bucket (planes, then
+  // {vl, delta, nq2, Sq}; query, mask word and bound are added once the
+  // bound is known).
+  uint32_t* rec = qrec ? reinterpret_cast<uint32_t*>(qrec + ((int64_t)c * nq + slot) * pair_rec_bytes(dp))
+                       : nullptr;
+  if (lane == 0 && slot_out) *slot_out = ((uint64_t)(uint32_t)slot << 32) | (uint32_t)c;
   float r[PER];
   float vl = __int_as_float(0x7f800000), vr = -vl, acc = 0.0f;
 #pragma unroll
@@ -207,14 +215,18 @@ __device__ __forceinline__ void quantize_pair(int64_t pair, int64_t q, int c, in
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const uint32_t w = __ballot_sync(0xffffffffu, (qu >> j) & 1);
-      if (lane == 0) pl[j * W + i] = w;
+      if (lane == 0) {
+        pl[j * W + i] = w;
+        if (rec) rec[j * W + i] = w;
+      }
     }
   }
   sq = warp_sum_int(sq);
   if (lane == 0) {
     const float4 qp = make_float4(vl, delta, nq2, __int_as_float(sq));
     qparams[pair] = qp;
-    if (list_count) {
+    if (rec) *reinterpret_cast<float4*>(rec + 4 * W) = qp;
+    if (list_pairs) {
       list_pairs[(int64_t)c * nq + slot] = (int32_t)pair;
       if (qpb) {
         // The tensor-core scan's copy, interleaved by slot couples for its
@@ -231,25 +243,25 @@ __device__ __forceinline__ void quantize_pair(int64_t pair, int64_t q, int c, in
 }
 
 // ---------------------------------------------------------------------------
-// Plain scan: one block per (query, probed list, chunk of kPlainChunk
+// Plain scan: one block per (query, probed list, chunk of `chunk`
 // vectors) -- the query-level schedule of Section 3.3.1, with long lists cut
 // into chunks so that they do not leave one block running alone. A thread
 // loads the codes of up to eight 128-vector steps before estimating them,
-// then the row ids of its passing vectors of all the steps at once (so that
-// no step's survivor write waits alone on its id load); each warp writes the
-// survivor mask word and the keys of its 32 vectors (emit_word).
+// then writes, per warp, the survivor mask word and the keys of its 32
+// vectors (emit_word). Keys carry the vector's slot; the finalize kernel maps
+// the slots of the candidates it collects to row ids.
 // ---------------------------------------------------------------------------
-constexpr int kPlainChunk = 1024;  // vectors of one list per block of the plain scan
+constexpr int kPlainChunk = 1024;  // default vectors of one list per block of the plain scan
 
-template <int NW4>
+template <int NW4, int CHUNK>
 __global__ void __launch_bounds__(128, NW4 == 1 ? 8 : 4)  // 8 blocks/SM: 3% faster at D_p 128
 scan_plain_kernel(const int32_t* __restrict__ nchunks, const int32_t* __restrict__ probe_ids,
                   int npmax, const float4* __restrict__ qparams,
                   const uint32_t* __restrict__ planes, const int64_t* __restrict__ offsets,
                   const uint8_t* __restrict__ codes, const float2* __restrict__ fac,
-                  const uint32_t* __restrict__ ids, int dp, const uint32_t* __restrict__ bound,
+                  int dp, const uint32_t* __restrict__ bound,
                   const int32_t* __restrict__ wbase, int64_t mwords, uint32_t* __restrict__ mask,
-                  uint64_t* __restrict__ cand) {
+                  uint64_t* __restrict__ cand, int64_t mask_words, int32_t* err) {
   constexpr int W = 4 * NW4;
   constexpr int RB = NW4 >= 8 ? 1 : 8 / NW4;  // 128-vector steps with their loads in flight
   __shared__ __align__(16) uint32_t s_pl[4 * W];
@@ -260,8 +272,8 @@ scan_plain_kernel(const int32_t* __restrict__ nchunks, const int32_t* __restrict
   const int64_t q = pair / npmax;
   const int c = probe_ids[pair];
   const int64_t lo = offsets[c], hi = offsets[c + 1];
-  const int64_t start = lo + (int64_t)blockIdx.y * kPlainChunk;
-  const int64_t end = min(hi, start + kPlainChunk);
+  const int64_t start = lo + (int64_t)blockIdx.y * CHUNK;
+  const int64_t end = min(hi, start + CHUNK);
   for (int i = threadIdx.x; i < 4 * W; i += blockDim.x) s_pl[i] = planes[pair * 4 * W + i];
   __syncthreads();
   const float4 qp = qparams[pair];
@@ -297,111 +309,13 @@ scan_plain_kernel(const int32_t* __restrict__ nchunks, const int32_t* __restrict
         if (orderable(dv[r]) <= tau) passm |= 1u << r;
       }
     }
-    uint32_t idv[RB];
-#pragma unroll
-    for (int r = 0; r < RB; ++r)
-      idv[r] = (passm >> r) & 1u ? __ldg(ids + b0 + 128 * r + threadIdx.x) : 0u;
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
       const int64_t s0 = b0 + 128 * r;
       if (s0 + warp * 32 >= end) break;  // warp-uniform: this word is past the chunk's end
-      emit_word((passm >> r) & 1u, dv[r], idv[r], wrow + (s0 - lo) / 32 + warp, mask, cand, lane);
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Grouped scan (Section 3.3.1 block-level schedule, with the queries that
-// probe one list served together): work items are the index's static
-// (list, first vector) blocks of kGroupVectors vectors, longest lists first,
-// taken from a global counter by persistent blocks so that work crosses
-// query boundaries and stays balanced over skewed list lengths. A thread
-// holds one vector's code in registers and runs the estimator for every
-// (query, list) pair that probes the list, GP pairs at a time with their
-// bit-planes staged in shared memory.
-template <int NW4>
-__global__ void __launch_bounds__(kGroupVectors)
-scan_grouped_kernel(const int2* __restrict__ items, int n_items, int32_t* __restrict__ work_counter,
-                    const int32_t* __restrict__ list_count, const int32_t* __restrict__ list_pairs,
-                    int64_t pair_stride, const float4* __restrict__ qparams,
-                    const uint32_t* __restrict__ planes, int npmax,
-                    const int64_t* __restrict__ offsets, const uint8_t* __restrict__ codes,
-                    const float2* __restrict__ fac, const uint32_t* __restrict__ ids, int dp,
-                    const uint32_t* __restrict__ bound, const int32_t* __restrict__ wbase,
-                    int64_t mwords, uint32_t* __restrict__ mask, uint64_t* __restrict__ cand) {
-  constexpr int W = 4 * NW4;
-  constexpr int GP = GroupPairs<NW4>::value;
-  __shared__ __align__(16) uint32_t s_pl[GP][4 * W];
-  __shared__ float4 s_qp[GP];
-  __shared__ uint32_t s_tau[GP];
-  __shared__ int64_t s_wrow[GP];
-  __shared__ int s_item;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(work_counter, 1);
-    __syncthreads();
-    const int it = s_item;
-    if (it >= n_items) break;
-    const int2 w = items[it];
-    const int l = w.x;
-    const int cnt = list_count[l];
-    if (cnt == 0) {
-      __syncthreads();
-      continue;
-    }
-    const int64_t lo = offsets[l] + w.y;
-    const int64_t hi = min(offsets[l + 1], lo + kGroupVectors);
-    const int64_t s = lo + threadIdx.x;
-    const bool valid = s < hi;
-    const bool word_valid = lo + warp * 32 < hi;
-    const int64_t word = w.y / 32 + warp;
-    uint4 code[NW4];
-    float2 f = make_float2(0.0f, 0.0f);
-    int pc = 0;
-    if (valid) {
-      const uint4* cp = reinterpret_cast<const uint4*>(codes + s * (dp / 8));
-#pragma unroll
-      for (int i = 0; i < NW4; ++i) {
-        code[i] = __ldg(cp + i);
-        pc += __popc(code[i].x) + __popc(code[i].y) + __popc(code[i].z) + __popc(code[i].w);
-      }
-      f = fac[s];
-    } else {
-#pragma unroll
-      for (int i = 0; i < NW4; ++i) code[i] = make_uint4(0, 0, 0, 0);
-    }
-    const int32_t* lp = list_pairs + (int64_t)l * pair_stride;
-    for (int g0 = 0; g0 < cnt; g0 += GP) {
-      const int np = min(GP, cnt - g0);
-      for (int i = threadIdx.x; i < np * 4 * W; i += blockDim.x) {
-        const int g = i / (4 * W), k = i % (4 * W);
-        s_pl[g][k] = planes[(int64_t)lp[g0 + g] * 4 * W + k];
-      }
-      for (int g = threadIdx.x; g < np; g += blockDim.x) {
-        const int pair = lp[g0 + g];
-        const int q = pair / npmax;
-        s_qp[g] = qparams[pair];
-        s_wrow[g] = (int64_t)q * mwords + wbase[pair];
-        s_tau[g] = bound[q];
-      }
-      __syncthreads();
-      for (int g0c = 0; g0c < np; g0c += 16) {
-        float d[16];
-        uint32_t passbits = 0;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int g = g0c + j;
-          d[j] = 0.0f;
-          if (valid && g < np) {
-            d[j] = estimate_regs<NW4>(code, pc, f, s_pl[g], s_qp[g], dp);
-            if (orderable(d[j]) <= s_tau[g]) passbits |= 1u << j;
-          }
-        }
-        const uint32_t id = passbits ? ids[s] : 0u;
-        emit_chunk<16>(passbits, d, s_wrow + g0c, np - g0c, word, word_valid, id, mask, cand,
-                       lane);
-      }
-      __syncthreads();
+      const int64_t widx = wrow + (s0 - lo) / 32 + warp;
+      if (!index_ok(widx, mask_words, err)) continue;
+      emit_word((passm >> r) & 1u, dv[r], (uint32_t)(s0 + threadIdx.x), widx, mask, cand, lane);
     }
   }
 }
@@ -708,10 +622,20 @@ struct FinalizeLayout {
 // survivor masks into shared memory (or compacted in place when there are
 // more than S), warp 0 selects (radix passes), all 128 threads gather and
 // re-rank, warp 0 selects the final k.
+// Survivor keys leave the scans as (estimate, slot); the row id of the slot
+// replaces it as the candidates are collected, so that every selection ranks
+// by (estimate, row id).
+__device__ __forceinline__ uint64_t slot_to_id(uint64_t key, const uint32_t* __restrict__ ids,
+                                               int64_t n_slots, int32_t* err) {
+  const uint32_t slot = (uint32_t)key;
+  return (key & 0xFFFFFFFF00000000ull) | (index_ok(slot, n_slots, err) ? __ldg(ids + slot) : 0u);
+}
+
 template <typename RawT>
 __global__ void __launch_bounds__(128)
 finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ wtotal,
-                int64_t mwords, uint64_t* __restrict__ cand, int32_t* __restrict__ counts,
+                int64_t mwords, uint64_t* __restrict__ cand, const uint32_t* __restrict__ ids,
+                int64_t n_slots, int32_t* err, int32_t* __restrict__ counts,
                 const int32_t* __restrict__ nsel, const int32_t* __restrict__ kq,
                 const int32_t* __restrict__ rerank_on, int nsel_max, uint64_t* __restrict__ sel,
                 const RawT* __restrict__ raw, const float* __restrict__ q, int dim, int k_stride,
@@ -773,7 +697,7 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
         const int n = __popc(mw[r]);
         const uint64_t* kw = krow + (int64_t)(tid + 128 * r) * 32;
 #pragma unroll 4
-        for (int b = 0; b < n; ++b) s_stage[pos + b] = kw[b];
+        for (int b = 0; b < n; ++b) s_stage[pos + b] = slot_to_id(kw[b], ids, n_slots, err);
         pos += n;
       }
     } else {
@@ -781,7 +705,7 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
         const int n = __popc(mrow[i]);
         const uint64_t* kw = krow + (int64_t)i * 32;
 #pragma unroll 4
-        for (int b = 0; b < n; ++b) s_stage[pos + b] = kw[b];
+        for (int b = 0; b < n; ++b) s_stage[pos + b] = slot_to_id(kw[b], ids, n_slots, err);
         pos += n;
       }
     }
@@ -805,7 +729,7 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
       if (tid < 64 && pc) {
         const int at = ps - pc + (warp == 1 ? s_scan[0] : 0);
         const uint64_t* kw = krow + (int64_t)(c0 + tid) * 32;
-        for (int b = 0; b < pc; ++b) s_stage[at + b] = kw[b];
+        for (int b = 0; b < pc; ++b) s_stage[at + b] = slot_to_id(kw[b], ids, n_slots, err);
       }
       __syncthreads();
       for (int i = tid; i < tot; i += blockDim.x) krow[run + i] = s_stage[i];
@@ -1111,10 +1035,12 @@ struct PrepArgs {
   int32_t* list_pairs;
   uint8_t* qdb;
   float4* qpb;
+  uint8_t* qrec;      // streaming scan: per-list pair records (null otherwise)
   const uint8_t* codes;
   const float2* fac;
   uint32_t* bound;
-  int32_t* nchunks;   // plain scan: kPlainChunk chunks of each probe (null otherwise)
+  int32_t* nchunks;   // plain scan: `chunk`-vector chunks of each probe (null otherwise)
+  int chunk;
   int32_t* err;
 };
 
@@ -1141,7 +1067,7 @@ __global__ void __launch_bounds__(128, NW4 >= 4 ? 4 : 8) prep_kernel(PrepArgs a)
       int nc = 0;
       if (p < npq && p < got) {
         const uint32_t l = (uint32_t)dst[p];
-        nc = (int)((a.offsets[l + 1] - a.offsets[l] + kPlainChunk - 1) / kPlainChunk);
+        nc = (int)((a.offsets[l + 1] - a.offsets[l] + a.chunk - 1) / a.chunk);
       }
       a.nchunks[row * a.npmax + p] = nc;
     }
@@ -1150,9 +1076,14 @@ __global__ void __launch_bounds__(128, NW4 >= 4 ? 4 : 8) prep_kernel(PrepArgs a)
     if (tid == 0) flag_error(a.err, kErrBadProbe);
     return;
   }
+  // (dst[p] keeps the list id in its low word; the quantisation puts the
+  // pair's bucket slot in the high word, which held the distance: every
+  // reader of the distances above is done after this barrier)
+  __syncthreads();
   for (int p = warp; p < npq; p += 4)
     quantize_pair<NW4>(row * a.npmax + p, row, (int)(uint32_t)dst[p], lane, a.qrot, a.nq, a.cR,
-                       a.dp, a.qparams, a.planes, a.list_count, a.list_pairs, a.qdb, a.qpb);
+                       a.dp, a.qparams, a.planes, a.list_count, a.list_pairs, a.qdb, a.qpb,
+                       a.qrec, &dst[p]);
   // The block's own writes of planes and parameters are visible to it
   // after the barrier.
   __syncthreads();
@@ -1163,6 +1094,16 @@ __global__ void __launch_bounds__(128, NW4 >= 4 ? 4 : 8) prep_kernel(PrepArgs a)
                            a.codes, a.fac, a.dp, reinterpret_cast<uint32_t*>(region), hist,
                            small, ctl);
   if (tid == 0) a.bound[row] = tau;
+  if (a.qrec) {
+    // the rest of each pair record: query, first mask word, bound
+    const int rb = pair_rec_bytes(a.dp);
+    for (int p = tid; p < npq; p += blockDim.x) {
+      const uint64_t e = dst[p];
+      const int64_t c = (uint32_t)e, slot = (uint32_t)(e >> 32);
+      int4* m = reinterpret_cast<int4*>(a.qrec + (c * a.nq + slot) * rb + a.dp / 2 + 16);
+      *m = make_int4((int)row, a.wbase[row * a.npmax + p], (int)tau, 0);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1215,12 +1156,12 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
   L.take(&ws.out_d, nq * sh.k_stride);
   if (sh.mode != RQ_SCAN_PLAIN) {
     L.take(&ws.list_count, ix->nlist);
-    L.take(&ws.list_pairs, (int64_t)ix->nlist * nq);
-    L.take(&ws.work_count, 4);
   } else {
     L.take(&ws.nchunks, nq * np);
   }
+  if (sh.mode == RQ_SCAN_GROUPED) L.take(&ws.qrec, (int64_t)ix->nlist * nq * pair_rec_bytes(ix->dp));
   if (sh.mode == RQ_SCAN_MMA) {
+    L.take(&ws.list_pairs, (int64_t)ix->nlist * nq);
     L.take(&ws.qdig, (int64_t)ix->nlist * nq * ix->dp);
     L.take(&ws.qpb, (int64_t)ix->nlist * nq + 2);  // + a couple read past the last bucket
   }
@@ -1256,12 +1197,12 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
   rebase(ws.out_d, b);
   if (sh.mode != RQ_SCAN_PLAIN) {
     rebase(ws.list_count, b);
-    rebase(ws.list_pairs, b);
-    rebase(ws.work_count, b);
   } else {
     rebase(ws.nchunks, b);
   }
+  if (sh.mode == RQ_SCAN_GROUPED) rebase(ws.qrec, b);
   if (sh.mode == RQ_SCAN_MMA) {
+    rebase(ws.list_pairs, b);
     rebase(ws.qdig, b);
     rebase(ws.qpb, b);
   }
@@ -1308,13 +1249,15 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
     a.qparams = ws.qparams;
     a.planes = ws.planes;
     a.list_count = grouped ? ws.list_count : nullptr;
-    a.list_pairs = ws.list_pairs;
+    a.list_pairs = sh.mode == RQ_SCAN_MMA ? ws.list_pairs : nullptr;
     a.qdb = sh.mode == RQ_SCAN_MMA ? ws.qdig : nullptr;
     a.qpb = sh.mode == RQ_SCAN_MMA ? ws.qpb : nullptr;
+    a.qrec = sh.mode == RQ_SCAN_GROUPED ? ws.qrec : nullptr;
     a.codes = ix->codes;
     a.fac = ix->fac;
     a.bound = ws.bound;
     a.nchunks = grouped ? nullptr : ws.nchunks;
+    a.chunk = sh.chunk;
     a.err = ix->d_err;
     const size_t stage =
         certified ? ((std::max<size_t>((size_t)ix->nlist * 8, (size_t)kProbeRowStage * dp * 4) +
@@ -1331,21 +1274,22 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
   if (sh.mode == RQ_SCAN_PLAIN) {
     tm.mark(RQ_STAGE_SCAN, st);
     const unsigned chunks =
-        (unsigned)std::max<int64_t>(1, (ix->max_list_len + kPlainChunk - 1) / kPlainChunk);
-    scan_plain_kernel<NW4><<<dim3((unsigned)pairs, chunks), 128, 0, st>>>(
+        (unsigned)std::max<int64_t>(1, (ix->max_list_len + sh.chunk - 1) / sh.chunk);
+    auto kern = scan_plain_kernel<NW4, 1024>;
+    if (NW4 <= 2 && sh.chunk == 2048) kern = scan_plain_kernel<NW4, (NW4 <= 2 ? 2048 : 1024)>;
+    if (NW4 <= 2 && sh.chunk == 4096) kern = scan_plain_kernel<NW4, (NW4 <= 2 ? 4096 : 1024)>;
+    kern<<<dim3((unsigned)pairs, chunks), 128, 0, st>>>(
         ws.nchunks, ws.probe_ids, np, ws.qparams, ws.planes, ix->offsets, ix->codes, ix->fac,
-        ix->ids, dp, ws.bound, ws.wbase, ws.mwords, ws.mask, ws.cand);
+        dp, ws.bound, ws.wbase, ws.mwords, ws.mask, ws.cand, nq * ws.mwords, ix->d_err);
   } else {
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
     tm.mark(RQ_STAGE_SCAN, st);
     if (sh.mode == RQ_SCAN_MMA) {
-      RQ_TRY(launch_scan_mma(ix, sh, ws, st, sms));
+      RQ_TRY(launch_scan_mma(ix, sh, ws, st, sms, sh.withhold));
     } else {
-      scan_grouped_kernel<NW4><<<(unsigned)(sms * 8), kGroupVectors, 0, st>>>(
-          ix->items, ix->n_items, ws.work_count, ws.list_count, ws.list_pairs, nq, ws.qparams,
-          ws.planes, np, ix->offsets, ix->codes, ix->fac, ix->ids, dp, ws.bound, ws.wbase,
-          ws.mwords, ws.mask, ws.cand);
+      RQ_TRY(launch_scan_stream(ix, sh, ws, st, sms, sh.withhold ? kTestWaitLimitNs : kWaitLimitNs,
+                                sh.withhold));
     }
   }
   return RQ_OK;
@@ -1360,7 +1304,7 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
   const bool grouped = sh.mode != RQ_SCAN_PLAIN;
   rotate_kernel8<<<dim3(blocks_for(nq, 8), dp / 64), 256, 0, st>>>(
       ws.q, nq, ix->dim, ix->P32, dp, ws.qrot, grouped ? ws.list_count : nullptr,
-      grouped ? ix->nlist : 0, grouped ? ws.work_count : nullptr, grouped ? 4 : 0);
+      grouped ? ix->nlist : 0, nullptr, 0);
   // 2. centroid ranking: approximate (filter of the certified selection)
   // where certified_probe holds, else exact
   tm.mark(RQ_STAGE_PROBE, st);
@@ -1400,12 +1344,12 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
     RQ_TRY(allow_dynamic_smem((const void*)finalize_kernel<float>, 200 * 1024));
     if (ix->raw_dtype == RQ_U8)
       finalize_kernel<uint8_t><<<(unsigned)nq, 128, smem, st>>>(
-          ws.mask, ws.wtotal, ws.mwords, ws.cand, ws.counts, ws.nsel, ws.kq, ws.rerank_on,
+          ws.mask, ws.wtotal, ws.mwords, ws.cand, ix->ids, ix->n, ix->d_err, ws.counts, ws.nsel, ws.kq, ws.rerank_on,
           sh.nsel_max, ws.sel, static_cast<const uint8_t*>(ix->raw), ws.q, ix->dim, sh.k_stride, lay,
           ws.out_ids, ws.out_d);
     else
       finalize_kernel<float><<<(unsigned)nq, 128, smem, st>>>(
-          ws.mask, ws.wtotal, ws.mwords, ws.cand, ws.counts, ws.nsel, ws.kq, ws.rerank_on,
+          ws.mask, ws.wtotal, ws.mwords, ws.cand, ix->ids, ix->n, ix->d_err, ws.counts, ws.nsel, ws.kq, ws.rerank_on,
           sh.nsel_max, ws.sel, static_cast<const float*>(ix->raw), ws.q, ix->dim, sh.k_stride, lay,
           ws.out_ids, ws.out_d);
   }
@@ -1453,11 +1397,12 @@ rq_status get_plan(rq_index* ix, cudaStream_t st, const SearchShape& sh, Plan** 
   p->shape = sh;
   p->stream = st;
   RQ_TRY(alloc_workspace(ix, sh, st, p->ws));
-  if (cudaMallocHost(&p->h_params, sizeof(int32_t) * (4 * sh.nq + 1)) != cudaSuccess) {
+  if (cudaMallocHost(&p->h_params, sizeof(int32_t) * (4 * sh.nq + 2)) != cudaSuccess) {
     cudaGetLastError();
     destroy_plan(p.get());
     return fail(RQ_ERR_OOM, "pinned parameter buffer");
   }
+  p->h_err = p->h_params + 4 * sh.nq + 1;
   RQ_CUDA(cudaEventCreateWithFlags(&p->params_ready, cudaEventDisableTiming));
   p->last_use = ++ix->plan_clock;
   *out = p.get();
@@ -1482,28 +1427,57 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Time each scan mode on the sample batch (warm-up run, then the best of three
-// CUDA-event timings) and keep the fastest for RQ_SCAN_AUTO. The choice is
-// stored per (n, dim, nlist, nq, nprobe, n_rerank) in a text cache file.
-rq_status autotune(rq_index* ix, const float* queries, int64_t nq, int nprobe, int n_rerank,
-                   const char* cache_path) {
-  if (!ix || !queries || nq < 1) return fail(RQ_ERR_INVALID_ARG, "bad autotune arguments");
+// The tuned choice for a batch of the given class: the exact class when it
+// was tuned, else the nearest tuned class (batch size and pair density on
+// their log2 scales), else the latest tuned mode with the default chunk.
+TunedChoice tuned_for(rq_index* ix, std::pair<int, int> cls) {
+  std::lock_guard<std::mutex> lk(ix->mu);
+  TunedChoice best;
+  best.mode = ix->auto_mode.load();
+  int best_d = 1 << 30;
+  for (const auto& kv : ix->tuned) {
+    const int d = std::abs(kv.first.first - cls.first) + std::abs(kv.first.second - cls.second);
+    if (d < best_d) {
+      best_d = d;
+      best = kv.second;
+    }
+  }
+  return best;
+}
+
+// Time the scan forms on the sample batch -- the plain scan at each chunk
+// size, the streaming scan and (D_p = 128) the tensor-core scan; a warm-up
+// run, then the best of three CUDA-event timings each -- and keep the
+// fastest for batches of the sample's class (tune_class). Choices are kept
+// per (n, dim, nlist, class) in a text cache file, one line each.
+rq_status autotune(rq_index* ix, const float* queries, int64_t nq, const int32_t* nprobe,
+                   int n_rerank, const char* cache_path) {
+  if (!ix || !queries || !nprobe || nq < 1) return fail(RQ_ERR_INVALID_ARG, "bad autotune arguments");
+  int64_t sum_np = 0;
+  for (int64_t i = 0; i < nq; ++i) sum_np += nprobe[i];
+  const std::pair<int, int> cls = tune_class(nq, sum_np, ix->nlist);
   char key[160];
-  snprintf(key, sizeof(key), "n=%lld dim=%d nlist=%d nq=%lld nprobe=%d n_rerank=%d",
-           (long long)ix->n, ix->dim, ix->nlist, (long long)nq, nprobe, n_rerank);
+  snprintf(key, sizeof(key), "n=%lld dim=%d nlist=%d nq_class=%d density_class=%d",
+           (long long)ix->n, ix->dim, ix->nlist, cls.first, cls.second);
   if (cache_path) {
     if (FILE* f = fopen(cache_path, "r")) {
-      char line[256];
-      int found = -1;
+      char line[512];
+      int found = -1, chunk = kPlainChunk;
       while (fgets(line, sizeof(line), f)) {
         const size_t kl = strlen(key);
         if (strncmp(line, key, kl) == 0 && line[kl] == ' ') {
-          int m = 0;
-          if (sscanf(line + kl, " mode=%d", &m) == 1) found = m;
+          int m = 0, c = 0;
+          if (sscanf(line + kl, " mode=%d chunk=%d", &m, &c) == 2) {
+            found = m;
+            chunk = c;
+          }
         }
       }
       fclose(f);
-      if (found >= RQ_SCAN_PLAIN && found <= RQ_SCAN_MMA) {
+      if (found >= RQ_SCAN_PLAIN && found <= RQ_SCAN_MMA && chunk >= kPlainChunk &&
+          chunk % kPlainChunk == 0) {
+        std::lock_guard<std::mutex> lk(ix->mu);
+        ix->tuned[cls] = TunedChoice{found, chunk};
         ix->auto_mode.store(found);
         return RQ_OK;
       }
@@ -1548,42 +1522,46 @@ rq_status autotune(rq_index* ix, const float* queries, int64_t nq, int nprobe, i
   RQ_CUDA(cudaStreamCreateWithFlags(&sc.st, cudaStreamNonBlocking));
   RQ_CUDA(cudaEventCreate(&sc.e0));
   RQ_CUDA(cudaEventCreate(&sc.e1));
-  cudaStream_t st = sc.st;
-  cudaEvent_t e0 = sc.e0, e1 = sc.e1;
-  int64_t* d_ids = sc.d_ids;
-  float* d_d = sc.d_d;
-  float* d_q = sc.d_q;
-  std::vector<int32_t> a(nq, nprobe), b(nq, k), c(nq, n_rerank);
-  int best_mode = RQ_SCAN_GROUPED;
+  std::vector<int32_t> kk(nq, k), nr(nq, n_rerank);
+  TunedChoice best;
   float best_ms = 1e30f;
   std::string report;
-  rq_status s = RQ_OK;
-  for (int mode = RQ_SCAN_PLAIN; mode <= RQ_SCAN_MMA && s == RQ_OK; ++mode) {
-    if (mode == RQ_SCAN_MMA && !mma_supported(ix)) continue;
+  const TunedChoice forms[] = {{RQ_SCAN_PLAIN, 1024}, {RQ_SCAN_PLAIN, 2048}, {RQ_SCAN_PLAIN, 4096},
+                               {RQ_SCAN_GROUPED, 1024}, {RQ_SCAN_MMA, 1024}};
+  for (const TunedChoice& fm : forms) {
+    if (fm.mode == RQ_SCAN_MMA && !mma_supported(ix)) continue;
+    if (fm.mode == RQ_SCAN_PLAIN && fm.chunk > kPlainChunk && ix->max_list_len <= fm.chunk / 2)
+      continue;  // no list is long enough for this chunk to differ
     rq_search_opts o{};
-    o.scan_mode = mode;
+    o.scan_mode = fm.mode;
     o.use_graph = 1;
-    float best = 1e30f;
-    for (int rep = 0; rep < 4 && s == RQ_OK; ++rep) {
-      cudaEventRecord(e0, st);
-      s = search_run(ix, d_q, nq, a.data(), b.data(), c.data(), k, d_ids, d_d, &o, st);
-      cudaEventRecord(e1, st);
-      cudaEventSynchronize(e1);
+    o.plain_chunk = fm.chunk;
+    float ms_best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      RQ_CUDA(cudaEventRecord(sc.e0, sc.st));
+      RQ_TRY(search_run(ix, sc.d_q, nq, nprobe, kk.data(), nr.data(), k, sc.d_ids, sc.d_d, &o,
+                        sc.st));
+      RQ_CUDA(cudaEventRecord(sc.e1, sc.st));
+      RQ_CUDA(cudaEventSynchronize(sc.e1));
       float ms = 0.0f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (rep > 0) best = std::min(best, ms);
+      RQ_CUDA(cudaEventElapsedTime(&ms, sc.e0, sc.e1));
+      if (rep > 0) ms_best = std::min(ms_best, ms);
     }
-    report += " mode" + std::to_string(mode) + "_ms=" + std::to_string(best);
-    if (best < best_ms) {
-      best_ms = best;
-      best_mode = mode;
+    report += " mode" + std::to_string(fm.mode) + "_chunk" + std::to_string(fm.chunk) +
+              "_ms=" + std::to_string(ms_best);
+    if (ms_best < best_ms) {
+      best_ms = ms_best;
+      best = fm;
     }
   }
-  if (s != RQ_OK) return s;
-  ix->auto_mode.store(best_mode);
+  {
+    std::lock_guard<std::mutex> lk(ix->mu);
+    ix->tuned[cls] = best;
+  }
+  ix->auto_mode.store(best.mode);
   if (cache_path) {
     if (FILE* f = fopen(cache_path, "a")) {
-      fprintf(f, "%s mode=%d%s\n", key, best_mode, report.c_str());
+      fprintf(f, "%s mode=%d chunk=%d%s\n", key, best.mode, best.chunk, report.c_str());
       fclose(f);
     }
   }
@@ -1626,9 +1604,20 @@ rq_status search_run(rq_index* ix, const float* queries, int64_t nq, const int32
   }
   if (k_stride < kmax) return fail(RQ_ERR_INVALID_ARG, "k_stride below the largest k");
   int mode = opts ? opts->scan_mode : RQ_SCAN_AUTO;
-  if (mode == RQ_SCAN_AUTO) mode = ix->auto_mode.load();
+  int chunk = (opts && opts->plain_chunk > 0) ? opts->plain_chunk : kPlainChunk;
+  if (mode == RQ_SCAN_AUTO) {
+    int64_t sum_np = 0;
+    for (int64_t i = 0; i < nq; ++i) sum_np += h_np[i];
+    const TunedChoice t = tuned_for(ix, tune_class(nq, sum_np, ix->nlist));
+    mode = t.mode;
+    if (!(opts && opts->plain_chunk > 0)) chunk = t.chunk;
+  }
   if (mode < RQ_SCAN_PLAIN || mode > RQ_SCAN_MMA)
     return fail(RQ_ERR_INVALID_ARG, "unknown scan mode");
+  // only the plain scan has chunks; codes wider than 256 bits use 1024
+  if (mode != RQ_SCAN_PLAIN || ix->dp > 256) chunk = kPlainChunk;
+  if (chunk != 1024 && chunk != 2048 && chunk != 4096)
+    return fail(RQ_ERR_INVALID_ARG, "plain_chunk must be 1024, 2048 or 4096");
   if (mode == RQ_SCAN_MMA && !mma_supported(ix)) mode = RQ_SCAN_GROUPED;
   const bool no_prune = opts && opts->no_prune;
   h_rr[nq] = no_prune ? 1 : 0;
@@ -1659,7 +1648,8 @@ rq_status search_run(rq_index* ix, const float* queries, int64_t nq, const int32
   }
   const bool ids_dev = is_device_ptr(out_ids), d_dev = is_device_ptr(out_dist);
 
-  SearchShape sh{nq, npmax, nsel_max, k_stride, mode, no_prune ? 1 : 0};
+  const int withhold = (opts && opts->test_stall && mode != RQ_SCAN_PLAIN) ? 1 : 0;
+  SearchShape sh{nq, npmax, nsel_max, k_stride, mode, no_prune ? 1 : 0, withhold, chunk};
   cudaStream_t run_st = st;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   if (use_graph && st == nullptr) {
@@ -1734,7 +1724,21 @@ rq_status search_run(rq_index* ix, const float* queries, int64_t nq, const int32
   }
   // Host outputs (or host queries read by a pending copy) need the stream
   // to finish before the call returns; device-only calls stay asynchronous.
-  if (!ids_dev || !d_dev || !q_dev) RQ_CUDA(cudaStreamSynchronize(st));
+  // A call that waits also reads the device error word (one 4-byte copy).
+  const bool waits = !ids_dev || !d_dev || !q_dev;
+  if (waits) {
+    RQ_CUDA(cudaMemcpyAsync(plan->h_err, ix->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    RQ_CUDA(cudaStreamSynchronize(st));
+    const int32_t code = *plan->h_err;
+    if (code != 0) {
+      RQ_CUDA(cudaMemsetAsync(ix->d_err, 0, sizeof(int32_t), st));
+      RQ_CUDA(cudaStreamSynchronize(st));
+      if (code == kErrMmaTimeout || code == kErrScanTimeout)
+        return fail(RQ_ERR_TIMEOUT, "a bounded wait of the scan ran out (device code " +
+                                        std::to_string(code) + ")");
+      return fail(RQ_ERR_DEVICE, "a kernel flagged device error " + std::to_string(code));
+    }
+  }
   if (stage_ms) {
     RQ_CUDA(cudaEventSynchronize(tm.ev[RQ_STAGE_COUNT]));
     for (int i = 0; i < RQ_STAGE_COUNT; ++i) {

@@ -338,3 +338,62 @@ def test_integer_valued_base_kept_as_bytes_is_lossless(rq):
     # a base that is not integer-valued keeps its float copy
     t = rq.rq_build(W.mixture("tiny").base(3000), 16, seed=0, kmeans_iters=2)
     assert t.stats()["raw_bytes"] == 3000 * 128 * 4
+
+
+# ---------------------------------------------------------------- failure paths
+@pytest.mark.parametrize("mode", [2, 3])
+def test_scan_wait_runs_out_and_is_reported(tiny, mode):
+    """The pipelined scans bound every mbarrier wait. The test hook makes the
+    producer hold back its first stage (nothing ever signals it), so the
+    consumers' wait (1 ms under the hook) runs out: the kernel flags the
+    error word and returns, a synchronous search reports RQ_ERR_TIMEOUT and
+    clears the word, an asynchronous one leaves the code for
+    rq_device_error, and the context stays usable."""
+    _, q, ix, _ = tiny
+    rq = lib()
+    ref = ix.search(q, 8, 10, 100, scan_mode=mode)
+    with pytest.raises(rq.RQError) as e:
+        ix.search(q, 8, 10, 100, scan_mode=mode, test_stall=True)
+    assert e.value.status == rq.RQ_ERR_TIMEOUT
+    assert ix.device_error() == 0            # the synchronous call cleared it
+    qd = torch.from_numpy(q).cuda()
+    oi = torch.empty((q.shape[0], 10), dtype=torch.int64, device="cuda")
+    od = torch.empty((q.shape[0], 10), dtype=torch.float32, device="cuda")
+    ix.search(qd, 8, 10, 100, out_ids=oi, out_dist=od, scan_mode=mode, test_stall=True)
+    torch.cuda.synchronize()
+    assert ix.device_error() == (4 if mode == 3 else 5)
+    assert ix.device_error() == 0            # read and cleared
+    for _ in range(2):                       # the context and the index still work
+        got = ix.search(q, 8, 10, 100, scan_mode=mode)
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+
+
+def test_plain_chunks_and_tuned_choices_are_identical(rq, tmp_path):
+    """Every form the autotuner can pick (the plain scan at 1024, 2048 and
+    4096 vectors per block, the streaming and tensor-core scans) returns the
+    same results, bit for bit, on lists longer than a chunk; the tuned choice
+    is stored per batch class in the cache file and read back from it."""
+    mix = W.mixture("tiny")
+    x = mix.base(30000)
+    q = mix.queries(40)
+    ix = rq.rq_build(x, 8, seed=5, kmeans_iters=3)
+    assert ix.stats()["max_list"] > 4096
+    ref = ix.search(q, 3, 10, 200, scan_mode=1)
+    for kw in (dict(scan_mode=1, plain_chunk=2048), dict(scan_mode=1, plain_chunk=4096),
+               dict(scan_mode=1, plain_chunk=4096, use_graph=True), dict(scan_mode=2),
+               dict(scan_mode=3)):
+        got = ix.search(q, 3, 10, 200, **kw)
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), kw
+    with pytest.raises(rq.RQError):
+        ix.search(q, 3, 10, 200, scan_mode=1, plain_chunk=1500)
+    cache = str(tmp_path / "tune.txt")
+    ix.autotune(q, 3, 200, cache_path=cache)
+    lines = open(cache).read().splitlines()
+    assert len(lines) == 1 and "nq_class=" in lines[0] and " mode=" in lines[0]
+    got = ix.search(q, 3, 10, 200)                       # AUTO: the tuned choice
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    ix2 = rq.rq_build(x, 8, seed=5, kmeans_iters=3)
+    ix2.autotune(q, 3, 200, cache_path=cache)            # read from the cache file
+    assert len(open(cache).read().splitlines()) == 1
+    got = ix2.search(q, 3, 10, 200)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])

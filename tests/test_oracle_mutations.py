@@ -74,6 +74,12 @@ CASES = {
                                             [P.test_rotation_is_signed_qr_of_gaussian]),
     "random_orthogonal: transposed": (R, "random_orthogonal", "return q * s[None, :]", "return (q * s[None, :]).T",
                                       [P.test_rotation_is_signed_qr_of_gaussian]),
+    "_encode_rows: every row against the first centroid": (
+        R, "_encode_rows", "np.arange(x.shape[0])", "np.zeros(x.shape[0], np.int64)",
+        [P.test_build_layout_and_chunked_encode]),
+    "build_index: lists in descending row order": (
+        R, "build_index", "np.lexsort((np.arange(n), a))", "np.lexsort((-np.arange(n), a))",
+        [P.test_build_layout_and_chunked_encode]),
     "encode: P instead of P^T": (R, "encode", "z = pad(u, dp) @ P", "z = pad(u, dp) @ P.T",
                                  [P.test_alpha_identity_and_codes]),
     "encode: sign(0) -> 0 bit": (R, "encode", "bits = z >= 0", "bits = z > 0",
@@ -99,6 +105,11 @@ CASES = {
     "update: reseed from the nearest member": (R, "update", "far = mem[int(np.argmax(dd))]",
                                                "far = mem[int(np.argmin(dd))]",
                                                [P.test_update_is_mean_and_reseeds_empty]),
+    "sqdist_f64: sign of the cross term": (R, "sqdist_f64", "- 2.0 * (a @ b.T)", "+ 2.0 * (a @ b.T)",
+                                           [P.test_float64_assignment_is_nearest_exactly]),
+    "assign_f64: ties to the higher id": (R, "_nearest_f64", "a = np.argmin(d, axis=1)",
+                                          "a = d.shape[1] - 1 - np.argmin(d[:, ::-1], axis=1)",
+                                          [P.test_float64_assignment_is_nearest_exactly]),
     "kmeans_init: largest keys": (R, "kmeans_init", "rows[np.argsort(keys)[:nlist]]",
                                   "rows[np.argsort(keys)[::-1][:nlist]]", [P.test_kmeans_init_is_smallest_keys]),
     "train_rows: largest keys": (R, "train_rows", "np.argsort(keys)[:n_train]",

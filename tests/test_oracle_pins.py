@@ -167,6 +167,28 @@ def test_train_rows_are_smallest_keys():
     assert list(R.train_rows(seed, n, n_train)) != other
 
 
+def test_float64_assignment_is_nearest_exactly():
+    """The float64 assignment of the independent build: on integer-valued
+    rows (every float64 operation exact) it is the brute-force nearest
+    centroid by exact squared distance, ties (duplicate centroids) to the
+    lower id; on real-valued rows its distances are within float64 rounding
+    of the exact ones."""
+    rng = np.random.default_rng(19)
+    x = rng.integers(0, 256, (300, 16)).astype(F32)
+    c = rng.integers(0, 256, (24, 16)).astype(F32)
+    c[20:] = c[3:7]                        # duplicates: ties go to 3..6
+    d = R.sqdist_f64(x, c)
+    ex = np.array([[sum((int(a) - int(b)) ** 2 for a, b in zip(xi, cj)) for cj in c] for xi in x])
+    assert np.array_equal(d, ex.astype(F64))
+    a, dist = R.assign_f64(x, c, chunk=64)
+    ref = [min(range(24), key=lambda j: (ex[i, j], j)) for i in range(300)]
+    assert list(a) == ref and np.array_equal(dist, ex[np.arange(300), ref].astype(F64))
+    xr = rng.standard_normal((50, 96)).astype(F32)
+    cr = rng.standard_normal((30, 96)).astype(F32)
+    exr = ((xr.astype(F64)[:, None] - cr.astype(F64)[None]) ** 2).sum(-1)
+    assert np.allclose(R.sqdist_f64(xr, cr), exr, rtol=1e-13, atol=1e-12)
+
+
 def test_update_is_mean_and_reseeds_empty():
     # 1-D example worked by hand: centroids 0, 0 (duplicate), 10.
     x = np.array([[-1.0], [1.0], [2.0], [9.0], [11.0], [30.0]], F32)
@@ -218,6 +240,31 @@ def test_alpha_identity_and_codes():
     assert np.all((alpha > 0) & (alpha <= 1 + 1e-12))
     # sign convention: bit = [z >= 0]
     assert np.array_equal(bits.astype(bool), z >= 0)
+
+
+def test_build_layout_and_chunked_encode():
+    """build_index lays the rows out list by list (ascending row id inside a
+    list) and encodes each against its own list's centroid: its codes and
+    factors equal Eqs. 1-3 applied to every row directly, whatever the
+    chunking of the rows and whether the chunks are mapped by a pool."""
+    mix = W.mixture("tiny")
+    x = mix.base(1500)
+    P = R.random_orthogonal(4, 128)
+    c = R.kmeans(x, 12, 2, seed=4)
+    ref = R.build_index(x, 12, seed=4, centroids=c, P=P, chunk=1 << 20)
+    for chunk in (1, 97, 512):
+        got = R.build_index(x, 12, seed=4, centroids=c, P=P, chunk=chunk)
+        for key in ("ids", "offsets", "codes", "r", "alpha", "r2", "f"):
+            assert np.array_equal(got[key], ref[key]), (chunk, key)
+    a, _ = R.assign(x, c)
+    order = ref["ids"]
+    assert np.all(np.diff(a[order]) >= 0)
+    for l in range(12):
+        rows = order[ref["offsets"][l]:ref["offsets"][l + 1]]
+        assert np.all(a[rows] == l) and np.all(np.diff(rows) > 0)
+    codes, r, alpha, _ = R.encode(x[order], c, a[order], P)
+    assert np.array_equal(ref["codes"], codes)
+    assert np.array_equal(ref["r"], r.astype(F32)) and np.array_equal(ref["alpha"], alpha.astype(F32))
 
 
 def test_alpha_mean_and_zero_residual():

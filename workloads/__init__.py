@@ -28,6 +28,9 @@ recipe stands in for one of them):
 from __future__ import annotations
 
 import dataclasses
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 
 # Streams of the seed tuple: which random draw a chunk belongs to.
@@ -96,14 +99,27 @@ class Mixture:
 
     def rows(self, n: int, stream_seed: int, start_chunk: int = 0,
              labels: bool = False):
+        """n rows, chunk by chunk; chunks are independent, so they are drawn
+        by a thread pool (the result does not depend on the thread count)."""
         means, std = self.means(), self.dim_std()
         cdf = np.cumsum(self.weights())
         out = np.empty((n, self.dim), np.float32)
         lab = np.empty(n, np.int32)
-        for i, r0 in enumerate(range(0, n, CHUNK_ROWS)):
+
+        def fill(job):
+            i, r0 = job
             r = min(CHUNK_ROWS, n - r0)
             out[r0:r0 + r], lab[r0:r0 + r] = self.chunk(
                 stream_seed, start_chunk + i, r, means, std, cdf)
+
+        jobs = list(enumerate(range(0, n, CHUNK_ROWS)))
+        if len(jobs) <= 1:
+            for j in jobs:
+                fill(j)
+        else:
+            workers = max(1, min(16, os.cpu_count() or 1, len(jobs)))
+            with ThreadPoolExecutor(workers) as ex:
+                list(ex.map(fill, jobs))
         return (out, lab) if labels else out
 
     def base(self, n: int, labels: bool = False):
