@@ -339,12 +339,12 @@ def run_skewed(rq, args, rank, world, local, pg, dev, flush, stream):
     ids_pool = torch.empty((SKEW_POOL, kmax), dtype=torch.int64, device=dev)
     d_pool = torch.empty((SKEW_POOL, kmax), dtype=torch.float32, device=dev)
 
-    def run_pool(npb, kk, nr, mode=rq.RQ_SCAN_AUTO, graph=True):
+    def run_pool(npb, kk, nr, mode=rq.RQ_SCAN_AUTO, graph=True, est=rq.RQ_EST_BQ4):
         for b0 in range(0, SKEW_POOL, 1024):
             sl = slice(b0, b0 + 1024)
             ix.search_mixed(q_dev[sl], npb[sl], kk[sl], nr[sl], k_stride=kmax,
                             out_ids=ids_pool[sl], out_dist=d_pool[sl], scan_mode=mode,
-                            use_graph=graph, stream=stream)
+                            use_graph=graph, stream=stream, estimator=est)
         torch.cuda.synchronize()
         return recall_of(x_dev, q_dev, ids_pool, kth, 10)
 
@@ -398,18 +398,19 @@ def run_skewed(rq, args, rank, world, local, pg, dev, flush, stream):
                                 d=torch.empty((b, kmax), dtype=torch.float32, device=dev))
         return batches[key]
 
-    def step(key, mode, graph):
+    def step(key, mode, graph, est=rq.RQ_EST_BQ4):
         bt = batch_of(key)
         ix.search_mixed(bt["q"], bt["npb"], bt["kk"], bt["nr"], k_stride=kmax, out_ids=bt["ids"],
-                        out_dist=bt["d"], scan_mode=mode, use_graph=graph, stream=stream)
+                        out_dist=bt["d"], scan_mode=mode, use_graph=graph, stream=stream,
+                        estimator=est)
 
-    def timed(mode, graph, steps, warmup):
+    def timed(mode, graph, steps, warmup, est=rq.RQ_EST_BQ4):
         # every batch shape once (workspaces, graphs), then the warm-up steps
         for key in skew_schedule(len(SKEW_BATCHES)):
-            step(key, mode, graph)
+            step(key, mode, graph, est)
         sched = skew_schedule(warmup + steps, start=rank * len(SKEW_BATCHES))
         for key in sched[:warmup]:
-            step(key, mode, graph)
+            step(key, mode, graph, est)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(steps)]
         torch.cuda.synchronize()
@@ -418,7 +419,7 @@ def run_skewed(rq, args, rank, world, local, pg, dev, flush, stream):
         for i, key in enumerate(sched[warmup:]):
             flush.zero_()
             evs[i][0].record(stream)
-            step(key, mode, graph)
+            step(key, mode, graph, est)
             evs[i][1].record(stream)
         torch.cuda.synchronize()
         barrier(pg)
@@ -435,6 +436,15 @@ def run_skewed(rq, args, rank, world, local, pg, dev, flush, stream):
     # -- plain form
     t_plain, nq_plain, _ = timed(rq.RQ_SCAN_PLAIN, False, len(SKEW_BATCHES), 2)
     plain_qps = sum_over_ranks(pg, nq_plain) / max_over_ranks(pg, t_plain)
+    # -- the paper's FastScan estimator (full-precision query) at the same
+    # setting: recall and batched QPS (query-level schedule)
+    lut_recall = round(run_pool(npb, kk, nr, est=rq.RQ_EST_LUT), 4)
+    t_lut, nq_lut, _ = timed(rq.RQ_SCAN_PLAIN, True, len(SKEW_BATCHES), 2, rq.RQ_EST_LUT)
+    estimator_lut = {"recall_at_10": lut_recall,
+                     "value": round(sum_over_ranks(pg, nq_lut) / max_over_ranks(pg, t_lut), 1),
+                     "unit": "queries/s",
+                     "form": "FastScan float32 tables (Section 3.3.2), query-level scan, graph; "
+                             "same setting, schedule and re-rank as value"}
     # -- e2e through the C ABI with host buffers
     e2e = run_skew_e2e(rq, ix, q, npb, kk, nr, kmax, args, rank, pg, flush)
     # -- per batch size: stage times of the tuned form and of each scan form,
@@ -504,6 +514,7 @@ def run_skewed(rq, args, rank, world, local, pg, dev, flush, stream):
         "plain": {"value": round(plain_qps, 1), "unit": "queries/s",
                   "ms_per_step": round(1e3 * t_plain / len(SKEW_BATCHES), 4)},
         "serving": serving,
+        "estimator_lut": estimator_lut,
         "e2e": e2e,
         "roofline": roofline,
         "scan_by_batch": scan_table,

@@ -80,6 +80,16 @@ typedef enum rq_scan_mode {
   RQ_SCAN_MMA = 3
 } rq_scan_mode;
 
+/* The estimator of the code scan.
+ *  BQ4: the query residual quantised to B_q = 4 bits, the inner product of
+ *       Eq. 4 evaluated exactly as an integer by AND + popcount over four
+ *       bit-planes (or a tensor-core product), Section 3.3.2.
+ *  LUT: the paper's FastScan form: the full-precision residual, float32
+ *       tables of 256 entries per 8 dimensions gathered by code byte
+ *       (Section 3.3.2); runs on the query-level (PLAIN) schedule; D_p <= 256.
+ * The exact re-rank and everything else are the same for both. */
+typedef enum rq_estimator { RQ_EST_BQ4 = 0, RQ_EST_LUT = 1 } rq_estimator;
+
 typedef struct rq_build_opts {
   int32_t kmeans_iters; /* Lloyd iterations (default 10; 0 keeps the
                            initial rows as centroids) */
@@ -142,7 +152,7 @@ typedef struct rq_search_opts {
   int32_t plain_chunk;   /* PLAIN: list vectors per thread block, 1024, 2048
                             or 4096 (0 = 1024, or the tuned size under AUTO;
                             D_p above 256 always uses 1024) */
-  int32_t reserved;
+  int32_t estimator;     /* rq_estimator (default BQ4) */
 } rq_search_opts;
 
 typedef struct rq_stats {
@@ -322,6 +332,14 @@ RQ_API rq_status rq_device_error(rq_index* ix, int32_t* code);
 RQ_API rq_status rq_probe_static(const rq_index* ix, const float* queries, int64_t nq,
                                  int32_t nprobe, int32_t* out_ids, float* out_dist,
                                  void* stream);
+
+/* rq_test_fail_allocations -- test hook of the failure paths: the after-th
+ * next device allocation this library makes (0 = the very next) fails as if
+ * the device were out of memory, and the ones after it succeed again; a
+ * negative value disarms the hook. The call that meets the failure returns
+ * RQ_ERR_OOM and releases what it had allocated. Process-wide; not for use
+ * while other threads call into the library. */
+RQ_API void rq_test_fail_allocations(int64_t after);
 
 RQ_API const char* rq_status_str(rq_status s);
 RQ_API const char* rq_last_error(void);

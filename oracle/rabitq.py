@@ -46,7 +46,9 @@ F64 = np.float64
 BQ = 4                    # query bits (B_q)
 QMAX = (1 << BQ) - 1      # 15
 LANES = 32                # width of the fixed lane-sum order
-BOUND_CANDIDATES = 1024   # candidates that set a query's first bound
+BOUND_MIN = 1024          # the first bound sees at least this many candidates,
+BOUND_FACTOR = 16         # and 16 n_sel of them,
+BOUND_MAX = 32768         # but no more than this (or n_sel, when larger)
 U64_MAX = np.uint64(0xFFFFFFFFFFFFFFFF)
 U32_MAX = 0xFFFFFFFF
 
@@ -437,31 +439,87 @@ def estimate(codes, r2, f, quant: dict, dp: int, qi=None) -> np.ndarray:
     return (d2 + F32(0)).astype(F32)
 
 
-def list_candidates(index: dict, qrot_i: np.ndarray, probe_ids: np.ndarray):
+def lut_tables(res: np.ndarray) -> np.ndarray:
+    """FastScan tables of one rotated residual (Section 3.3.2, the paper's
+    estimator: the query is not quantised). For group g of eight dimensions
+    and byte value v, T[g, v] is the float32 sum of res[8 g + i] over the set
+    bits i of v, added in increasing i from 0. res: (D_p,) -> (D_p/8, 256).
+    """
+    res = np.asarray(res, F32)
+    groups = res.shape[-1] // 8
+    out = np.zeros((groups, 256), F32)
+    for v in range(256):
+        acc = np.zeros(groups, F32)
+        for i in range(8):
+            if (v >> i) & 1:
+                acc = acc + res[i::8]       # res[8 g + i] for every group g
+        out[:, v] = acc
+    return out
+
+
+def estimate_lut(codes, r2, f, res) -> np.ndarray:
+    """Estimated squared distance (Eqs. 4-5) with the full-precision rotated
+    residual, in the FastScan form (float32): s = sum over groups g, in
+    increasing g, of T[g, code byte g] (so s = sum_d bit_d res_d);
+    t = 2 s - S, S = sum_d res_d in the 32-lane order (so t = sum_d b_d res_d,
+    b_d = 2 bit_d - 1); d2 = (nq2 + r^2) - 2 (f t), nq2 = ||res||^2 in the
+    32-lane order; then + 0."""
+    res = np.asarray(res, F32)
+    T = lut_tables(res)
+    codes = np.asarray(codes, np.uint8)
+    s = np.zeros(codes.shape[0], F32)
+    for g in range(T.shape[0]):
+        s = s + T[g][codes[:, g]]
+    t = F32(2) * s - lane_sum(res)
+    nq2 = lane_sum(res * res)
+    d2 = (nq2 + np.asarray(r2, F32)) - F32(2) * (np.asarray(f, F32) * t)
+    return (d2 + F32(0)).astype(F32)
+
+
+def list_candidates(index: dict, qrot_i: np.ndarray, probe_ids: np.ndarray,
+                    estimator: str = "bq4"):
     """Estimated distances of every vector in the probed lists of one query,
-    in probe order and list order. Returns (d2, ids, quantisations)."""
+    in probe order and list order. Returns (d2, ids, quantisations); with
+    ``estimator="lut"`` the unquantised FastScan form is used and the
+    quantisations list holds the residuals."""
     off = index["offsets"]
     ds, ids, qs = [], [], []
     for c in probe_ids:
         lo, hi = int(off[c]), int(off[c + 1])
-        q = quantize((qrot_i - index["cR"][c])[None, :])
-        qs.append(q)
-        ds.append(estimate(index["codes"][lo:hi], index["r2"][lo:hi],
-                           index["f"][lo:hi], q, index["dp"], qi=0))
+        res = (qrot_i - index["cR"][c])
+        if estimator == "lut":
+            qs.append(res)
+            ds.append(estimate_lut(index["codes"][lo:hi], index["r2"][lo:hi],
+                                   index["f"][lo:hi], res))
+        else:
+            q = quantize(res[None, :])
+            qs.append(q)
+            ds.append(estimate(index["codes"][lo:hi], index["r2"][lo:hi],
+                               index["f"][lo:hi], q, index["dp"], qi=0))
         ids.append(index["ids"][lo:hi])
     if not ds:
         return np.zeros(0, F32), np.zeros(0, np.int64), qs
     return np.concatenate(ds), np.concatenate(ids), qs
 
 
-def first_bound(d2: np.ndarray, n_sel: int, cap: int = BOUND_CANDIDATES):
+def bound_window(n_sel: int) -> int:
+    """How many candidates, in probe order, set a query's first bound:
+    max(1024, n_sel, min(16 n_sel, 32768))."""
+    return max(BOUND_MIN, n_sel, min(BOUND_FACTOR * n_sel, BOUND_MAX))
+
+
+def first_bound(d2: np.ndarray, n_sel: int, window: int | None = None):
     """Upper bound for pruning (Section 3.3.3): the n_sel-th smallest
-    orderable distance among the first max(cap, n_sel) candidates in probe
-    order; no bound (all ones) when the query has fewer than n_sel candidates.
+    orderable distance among the first ``bound_window(n_sel)`` candidates in
+    probe order (lists by ascending centroid distance, so the prefix holds
+    the most promising candidates); no bound (all ones) when the query has
+    fewer than n_sel candidates. The n_sel-th smallest of any prefix is at or
+    above the n_sel-th smallest of all candidates, so nothing the selection
+    keeps is pruned; a longer prefix gives a tighter bound.
     """
     if d2.size < n_sel or n_sel == 0:
         return U32_MAX
-    m = min(d2.size, max(cap, n_sel))
+    m = min(d2.size, bound_window(n_sel) if window is None else window)
     return int(np.sort(orderable(d2[:m]))[n_sel - 1])
 
 
@@ -521,11 +579,12 @@ def rerank(raw: np.ndarray, q: np.ndarray, cand_ids: np.ndarray, k: int):
 
 
 def search(index: dict, q: np.ndarray, nprobe, k, n_rerank, qrot=None,
-           prune: bool = True, return_stages: bool = False):
+           prune: bool = True, return_stages: bool = False, estimator: str = "bq4"):
     """Full search of a batch. ``nprobe``, ``k``, ``n_rerank`` are scalars or
     per-query arrays. ``qrot`` replaces the float64 rotation (replay of a
     rotation computed elsewhere). n_rerank = 0 returns the top k by the
-    estimate, without re-rank.
+    estimate, without re-rank. ``estimator``: "bq4" (4-bit query, bit-plane
+    popcounts) or "lut" (full-precision query, FastScan tables).
     """
     q = np.asarray(q, F32)
     nq = q.shape[0]
@@ -539,7 +598,7 @@ def search(index: dict, q: np.ndarray, nprobe, k, n_rerank, qrot=None,
     dist = np.full((nq, kmax), np.inf, F32)
     stages = []
     for i in range(nq):
-        d2, cid, qs = list_candidates(index, qrot[i], pid[i, :npb[i]])
+        d2, cid, qs = list_candidates(index, qrot[i], pid[i, :npb[i]], estimator)
         n_sel = int(nrr[i]) if nrr[i] > 0 else int(kk[i])
         sel = select_candidates(d2, cid, n_sel, prune)
         if nrr[i] > 0:

@@ -23,6 +23,7 @@ RQ_OK, RQ_ERR_INVALID_ARG, RQ_ERR_OOM, RQ_ERR_CUDA, RQ_ERR_TIMEOUT = 0, 1, 2, 3,
 RQ_ERR_BUSY, RQ_ERR_IO, RQ_ERR_NOT_IMPLEMENTED, RQ_ERR_DEVICE = 5, 6, 7, 8
 RQ_F32, RQ_U8 = 0, 1
 RQ_SCAN_AUTO, RQ_SCAN_PLAIN, RQ_SCAN_GROUPED, RQ_SCAN_MMA = 0, 1, 2, 3
+RQ_EST_BQ4, RQ_EST_LUT = 0, 1
 
 
 class RQError(RuntimeError):
@@ -47,7 +48,7 @@ class SearchOpts(C.Structure):
     _fields_ = [("scan_mode", C.c_int32), ("no_prune", C.c_int32),
                 ("use_graph", C.c_int32), ("test_stall", C.c_int32),
                 ("dump", C.POINTER(SearchDump)), ("stage_ms", C.POINTER(C.c_float)),
-                ("plain_chunk", C.c_int32), ("reserved", C.c_int32)]
+                ("plain_chunk", C.c_int32), ("estimator", C.c_int32)]
 
 
 STAGES = ("rotate", "probe", "quantize", "bound", "worklist", "scan", "select", "rerank")
@@ -113,6 +114,7 @@ _SIGS = {
     "rq_server_destroy": (None, [C.c_void_p]),
     "rq_probe_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
                                   C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rq_test_fail_allocations": (None, [C.c_int64]),
 }
 
 
@@ -219,9 +221,16 @@ def rq_version() -> int:
     return lib().rq_version()
 
 
-def _opts(scan_mode, no_prune, use_graph, dump, stage_ms=None, test_stall=False, plain_chunk=0):
+def rq_test_fail_allocations(after: int):
+    """Test hook: the after-th next device allocation of the library fails
+    (-1 disarms); see include/rq.h."""
+    lib().rq_test_fail_allocations(after)
+
+
+def _opts(scan_mode, no_prune, use_graph, dump, stage_ms=None, test_stall=False, plain_chunk=0,
+          estimator=RQ_EST_BQ4):
     o = SearchOpts(scan_mode, int(no_prune), int(use_graph), int(test_stall), None, None,
-                   int(plain_chunk), 0)
+                   int(plain_chunk), int(estimator))
     if stage_ms is not None:
         o.stage_ms = stage_ms
     if dump is not None:
@@ -242,7 +251,7 @@ class Index:
     def rq_search(self, queries, nprobe: int, k: int, n_rerank: int, out_ids=None,
                   out_dist=None, scan_mode: int = RQ_SCAN_AUTO, no_prune: bool = False,
                   use_graph: bool = False, dump=None, stream=None, stage_times=None,
-                  test_stall: bool = False, plain_chunk: int = 0):
+                  test_stall: bool = False, plain_chunk: int = 0, estimator: int = RQ_EST_BQ4):
         """stage_times: a dict that receives each stage's device time (ms).
         test_stall: the failure-path test hook of rq_search_opts."""
         nq = _shape(queries)[0]
@@ -250,7 +259,7 @@ class Index:
             out_ids = np.empty((nq, k), np.int64)
             out_dist = np.empty((nq, k), np.float32)
         ms = (C.c_float * len(STAGES))() if stage_times is not None else None
-        o = _opts(scan_mode, no_prune, use_graph, dump, ms, test_stall, plain_chunk)
+        o = _opts(scan_mode, no_prune, use_graph, dump, ms, test_stall, plain_chunk, estimator)
         _check(lib().rq_search(self.h, _ptr(queries), nq, nprobe, k, n_rerank,
                                _ptr(out_ids), _ptr(out_dist), C.byref(o),
                                _stream_ptr(stream)))
@@ -263,7 +272,8 @@ class Index:
     def rq_search_mixed(self, queries, nprobe, k, n_rerank, k_stride=None, out_ids=None,
                         out_dist=None, scan_mode: int = RQ_SCAN_AUTO,
                         no_prune: bool = False, use_graph: bool = False, dump=None,
-                        stream=None, stage_times=None, plain_chunk: int = 0):
+                        stream=None, stage_times=None, plain_chunk: int = 0,
+                        estimator: int = RQ_EST_BQ4):
         nq = _shape(queries)[0]
         nprobe = np.ascontiguousarray(nprobe, np.int32)
         k = np.ascontiguousarray(k, np.int32)
@@ -274,7 +284,7 @@ class Index:
             out_ids = np.empty((nq, k_stride), np.int64)
             out_dist = np.empty((nq, k_stride), np.float32)
         ms = (C.c_float * len(STAGES))() if stage_times is not None else None
-        o = _opts(scan_mode, no_prune, use_graph, dump, ms, False, plain_chunk)
+        o = _opts(scan_mode, no_prune, use_graph, dump, ms, False, plain_chunk, estimator)
         _check(lib().rq_search_mixed(self.h, _ptr(queries), nq, _ptr(nprobe), _ptr(k),
                                      _ptr(n_rerank), k_stride, _ptr(out_ids),
                                      _ptr(out_dist), C.byref(o), _stream_ptr(stream)))

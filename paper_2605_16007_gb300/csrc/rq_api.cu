@@ -2,6 +2,7 @@
 // export/import, and the continuous-batching server.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -36,6 +37,18 @@ rq_status cuda_fail(cudaError_t e, const char* what, const char* file, int line)
   set_error(std::string(what) + ": " + cudaGetErrorString(e) + " (" + (base ? base + 1 : file) +
             ":" + std::to_string(line) + ")");
   return (e == cudaErrorMemoryAllocation) ? RQ_ERR_OOM : RQ_ERR_CUDA;
+}
+
+// The allocation-failure hook: the countdown-th next device allocation
+// fails (0 = the next one); -1 = none.
+static std::atomic<int64_t> g_fail_countdown{-1};
+
+bool alloc_should_fail() {
+  int64_t c = g_fail_countdown.load();
+  while (c >= 0) {
+    if (g_fail_countdown.compare_exchange_weak(c, c - 1)) return c == 0;
+  }
+  return false;
 }
 
 rq_status allow_dynamic_smem(const void* func, int bytes) {
@@ -78,7 +91,7 @@ __global__ void u8_to_f32_kernel(const uint8_t* a, float* b, int64_t n) {
 
 rq_status check_finite_device(const float* d, int64_t n, const char* what) {
   int32_t* cnt = nullptr;
-  RQ_CUDA(cudaMalloc(&cnt, sizeof(int32_t)));
+  RQ_CUDA(dev_alloc(&cnt, sizeof(int32_t)));
   cudaMemset(cnt, 0, sizeof(int32_t));
   count_nonfinite_kernel<<<(unsigned)std::max<int64_t>(1, (n + 255) / 256), 256>>>(d, n, cnt);
   int32_t h = 0;
@@ -106,7 +119,7 @@ rq_status upload_base(const void* base, rq_dtype dt, int64_t n, int dim, void** 
                       float** d_f32, bool* f32_is_temp) {
   const size_t elt = (dt == RQ_U8) ? 1 : 4;
   const size_t bytes = elt * (size_t)n * dim;
-  RQ_CUDA(cudaMalloc(d_raw, bytes));
+  RQ_CUDA(dev_alloc(d_raw, bytes));
   cudaError_t e = cudaMemcpy(*d_raw, base, bytes, cudaMemcpyDefault);
   if (e != cudaSuccess) {
     cudaFree(*d_raw);
@@ -123,7 +136,7 @@ rq_status upload_base(const void* base, rq_dtype dt, int64_t n, int dim, void** 
     }
     return s;
   }
-  e = cudaMalloc(d_f32, sizeof(float) * (size_t)n * dim);
+  e = dev_alloc(d_f32, sizeof(float) * (size_t)n * dim);
   if (e != cudaSuccess) {
     cudaFree(*d_raw);
     *d_raw = nullptr;
@@ -155,7 +168,7 @@ rq_status compress_raw(rq_index* ix) {
   if (ix->raw_dtype != RQ_F32) return RQ_OK;
   const int64_t count = ix->n * ix->dim;
   int32_t* cnt = nullptr;
-  RQ_CUDA(cudaMalloc(&cnt, sizeof(int32_t)));
+  RQ_CUDA(dev_alloc(&cnt, sizeof(int32_t)));
   cudaMemset(cnt, 0, sizeof(int32_t));
   const unsigned blocks = (unsigned)std::max<int64_t>(1, (count + 255) / 256);
   count_non_byte_kernel<<<blocks, 256>>>(static_cast<const float*>(ix->raw), count, cnt);
@@ -165,7 +178,7 @@ rq_status compress_raw(rq_index* ix) {
   if (e != cudaSuccess) return cuda_fail(e, "raw check", __FILE__, __LINE__);
   if (h != 0) return RQ_OK;
   uint8_t* r8 = nullptr;
-  if (cudaMalloc(&r8, (size_t)count + 16) != cudaSuccess) {
+  if (dev_alloc(&r8, (size_t)count + 16) != cudaSuccess) {
     cudaGetLastError();
     return RQ_OK;  // keep the float copy
   }
@@ -195,8 +208,8 @@ rq_status build_common(const void* base, rq_dtype dt, int64_t n, int32_t dim, in
   rq_status s = RQ_OK;
   if (cent) {
     const int dp = dim_pad(dim);
-    if (cudaMalloc(&cent_tmp, sizeof(float) * nlist * dim) != cudaSuccess ||
-        cudaMalloc(&P_tmp, sizeof(double) * dp * dp) != cudaSuccess) {
+    if (dev_alloc(&cent_tmp, sizeof(float) * nlist * dim) != cudaSuccess ||
+        dev_alloc(&P_tmp, sizeof(double) * dp * dp) != cudaSuccess) {
       cudaGetLastError();
       s = fail(RQ_ERR_OOM, "given centroids / rotation");
     } else {
@@ -343,13 +356,9 @@ int pow2_at_least(int v) {
 
 // Device bytes a batch shape needs (the search workspace) -- the admission
 // cost of a batch.
-size_t batch_bytes(const rq_index* ix, int64_t nq, int npmax, int nsel, int kst) {
-  const int64_t mwords = ix->top_words_prefix[std::min<int64_t>(npmax, ix->nlist)];
-  size_t b = 0;
-  b += (size_t)nq * (ix->dim + ix->dp) * 4 + (size_t)nq * ix->nlist * 8;
-  b += (size_t)nq * npmax * (4 + 4 + 16 + 16 * (ix->dp / 32) + 4 + 4);
-  b += (size_t)nq * mwords * (4 + 32 * 8) + (size_t)nq * nsel * 8 + (size_t)nq * kst * 12;
-  return b + (1 << 20);
+size_t batch_bytes(const rq_index* ix, int64_t nq, int npmax, int nsel, int kst, int mode) {
+  return search_workspace_bytes(ix, nq, npmax, nsel, kst, mode) + (size_t)nq * kst * 12 +
+         (size_t)nq * ix->dim * 4 + (1 << 20);
 }
 
 rq_status slot_reserve(Slot& sl, int64_t nq_elems, int64_t out_elems) {
@@ -357,7 +366,7 @@ rq_status slot_reserve(Slot& sl, int64_t nq_elems, int64_t out_elems) {
     if (sl.h_q) cudaFreeHost(sl.h_q);
     if (sl.d_q) cudaFree(sl.d_q);
     RQ_CUDA(cudaMallocHost(&sl.h_q, sizeof(float) * nq_elems));
-    RQ_CUDA(cudaMalloc(&sl.d_q, sizeof(float) * nq_elems));
+    RQ_CUDA(dev_alloc(&sl.d_q, sizeof(float) * nq_elems));
     sl.cap_q = nq_elems;
   }
   if (out_elems > sl.cap_out) {
@@ -367,8 +376,8 @@ rq_status slot_reserve(Slot& sl, int64_t nq_elems, int64_t out_elems) {
     if (sl.d_d) cudaFree(sl.d_d);
     RQ_CUDA(cudaMallocHost(&sl.h_ids, sizeof(int64_t) * out_elems));
     RQ_CUDA(cudaMallocHost(&sl.h_d, sizeof(float) * out_elems));
-    RQ_CUDA(cudaMalloc(&sl.d_ids, sizeof(int64_t) * out_elems));
-    RQ_CUDA(cudaMalloc(&sl.d_d, sizeof(float) * out_elems));
+    RQ_CUDA(dev_alloc(&sl.d_ids, sizeof(int64_t) * out_elems));
+    RQ_CUDA(dev_alloc(&sl.d_d, sizeof(float) * out_elems));
     sl.cap_out = out_elems;
   }
   return RQ_OK;
@@ -471,7 +480,7 @@ void server_loop(rq_server* s) {
         const int64_t b2 = std::max(64, pow2_at_least((int)nq2 + 1));
         const int npb = std::min(pow2_at_least(np2), std::min(s->ix->nlist, kMaxSelect));
         const int nsb = std::min(pow2_at_least(ns2), kMaxSelect);
-        const size_t need = batch_bytes(s->ix, b2, npb, nsb, pow2_at_least(k2));
+        const size_t need = batch_bytes(s->ix, b2, npb, nsb, pow2_at_least(k2), RQ_SCAN_MMA);
         if (!take.empty() && s->mem_in_use + need > budget) break;
         if (take.empty() && s->mem_in_use > 0 && s->mem_in_use + need > budget) break;
         take.push_back(r);
@@ -488,7 +497,7 @@ void server_loop(rq_server* s) {
         const int npb = std::min(pow2_at_least(npm), std::min(s->ix->nlist, kMaxSelect));
         const int nsb = std::min(pow2_at_least(nsm), kMaxSelect);
         const int kb = std::min(pow2_at_least(km), nsb);
-        sl.mem = batch_bytes(s->ix, sl.bucket, npb, nsb, kb);
+        sl.mem = batch_bytes(s->ix, sl.bucket, npb, nsb, kb, RQ_SCAN_MMA);
         s->mem_in_use += sl.mem;
         sl.busy = true;
         lk.unlock();
@@ -547,6 +556,8 @@ const char* rq_status_str(rq_status s) {
 
 const char* rq_last_error(void) { return t_error.c_str(); }
 
+void rq_test_fail_allocations(int64_t after) { g_fail_countdown.store(after < 0 ? -1 : after); }
+
 int32_t rq_version(void) { return 10000; }
 
 rq_status rq_build(const void* base, rq_dtype dtype, int64_t n, int32_t dim, int32_t nlist,
@@ -578,7 +589,7 @@ rq_status rq_kmeans(const float* base, int64_t n, int32_t dim, int32_t nlist, ui
   bool temp = false;
   RQ_TRY(upload_base(base, RQ_F32, n, dim, &d_raw, &d_f32, &temp));
   float* d_c = nullptr;
-  cudaError_t e = cudaMalloc(&d_c, sizeof(float) * nlist * dim);
+  cudaError_t e = dev_alloc(&d_c, sizeof(float) * nlist * dim);
   if (e != cudaSuccess) {
     cudaFree(d_raw);
     return cuda_fail(e, "centroid buffer", __FILE__, __LINE__);
@@ -597,7 +608,7 @@ rq_status rq_philox_gaussian(uint64_t seed, uint32_t stream, int64_t count, doub
   if (!out || count < 0) return fail(RQ_ERR_INVALID_ARG, "bad output or count");
   if (count == 0) return RQ_OK;
   double* d = nullptr;
-  RQ_CUDA(cudaMalloc(&d, sizeof(double) * count));
+  RQ_CUDA(dev_alloc(&d, sizeof(double) * count));
   rq_status s = philox_gaussian_device(seed, stream, count, d);
   if (s == RQ_OK) {
     cudaError_t e = cudaMemcpy(out, d, sizeof(double) * count, cudaMemcpyDefault);
@@ -737,7 +748,7 @@ rq_status rq_import(const char* path, rq_index** out) {
       break;
     }
     // 16 bytes of tail room: bulk copies read whole 16-byte units.
-    if (cudaMalloc(a.dev, a.bytes + 16) != cudaSuccess) {
+    if (dev_alloc(a.dev, a.bytes + 16) != cudaSuccess) {
       cudaGetLastError();
       *a.dev = nullptr;
       s = fail(RQ_ERR_OOM, "index arrays");
@@ -751,8 +762,8 @@ rq_status rq_import(const char* path, rq_index** out) {
   fclose(f);
   if (s == RQ_OK) {
     const int64_t nn = (int64_t)h.dp * h.dp;
-    if (cudaMalloc(&ix->P32, sizeof(float) * nn) != cudaSuccess ||
-        cudaMalloc(&ix->d_err, sizeof(int32_t)) != cudaSuccess) {
+    if (dev_alloc(&ix->P32, sizeof(float) * nn) != cudaSuccess ||
+        dev_alloc(&ix->d_err, sizeof(int32_t)) != cudaSuccess) {
       cudaGetLastError();
       s = fail(RQ_ERR_OOM, "index arrays");
     } else {

@@ -33,7 +33,7 @@ struct DevBuf {
   }
   rq_status alloc(size_t count) {
     n = count;
-    cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+    cudaError_t e = dev_alloc(&p, std::max<size_t>(count, 1) * sizeof(T));
     if (e != cudaSuccess) {
       p = nullptr;
       cudaGetLastError();
@@ -781,7 +781,7 @@ rq_status finish_index_host_side(rq_index* ix) {
   if (ix->items) cudaFree(ix->items);
   ix->items = nullptr;
   ix->n_items = (int)items.size();
-  RQ_CUDA(cudaMalloc(&ix->items, sizeof(int2) * std::max<size_t>(items.size(), 1)));
+  RQ_CUDA(dev_alloc(&ix->items, sizeof(int2) * std::max<size_t>(items.size(), 1)));
   RQ_CUDA(cudaMemcpy(ix->items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
   return RQ_OK;
 }

@@ -20,7 +20,12 @@ namespace rq {
 
 constexpr int kMaxDim = 2048;
 constexpr int kMaxSelect = 4096;      // largest n_rerank / k / nprobe
-constexpr int kBoundCandidates = 1024;  // candidates that set the first bound
+// How many candidates, in probe order, set a query's first pruning bound:
+// max(1024, n_sel, min(16 n_sel, 32768)).
+__host__ __device__ inline int bound_window(int n_sel) {
+  const int w = 16 * n_sel < 32768 ? 16 * n_sel : 32768;
+  return n_sel > w ? n_sel : (w > 1024 ? w : 1024);
+}
 constexpr int kMaxNlist = 1 << 20;
 
 // Error bookkeeping: the first error message of the calling thread.
@@ -52,10 +57,11 @@ struct SearchShape {
   int prune;
   int withhold;   // test hook: the pipelined scan withholds its first stage
   int chunk;      // plain scan: list vectors per block (a multiple of 1024)
+  int lut;        // 1: FastScan estimator (full-precision query, float32 tables)
   bool operator<(const SearchShape& o) const {
-    return std::tie(nq, npmax, nsel_max, k_stride, mode, prune, withhold, chunk) <
+    return std::tie(nq, npmax, nsel_max, k_stride, mode, prune, withhold, chunk, lut) <
            std::tie(o.nq, o.npmax, o.nsel_max, o.k_stride, o.mode, o.prune, o.withhold,
-                    o.chunk);
+                    o.chunk, o.lut);
   }
 };
 
@@ -99,6 +105,7 @@ struct Workspace {
   int32_t* wtotal = nullptr;    // nq: mask words of the query's probes
   uint64_t* cand = nullptr;     // nq x cap, cap = 32 mwords
   uint64_t* sel = nullptr;      // nq x nsel_max
+  uint32_t* bkeys = nullptr;    // nq x bound_window(nsel_max): first-bound estimates
   int32_t* nprobe = nullptr;    // nq
   int32_t* kq = nullptr;        // nq
   int32_t* nsel = nullptr;      // nq
@@ -191,9 +198,23 @@ rq_status search_run(rq_index* ix, const float* queries, int64_t nq,
 rq_status autotune(rq_index* ix, const float* queries, int64_t nq, const int32_t* nprobe,
                    int n_rerank, const char* cache_path);
 void free_plans(rq_index* ix);
+size_t search_workspace_bytes(const rq_index* ix, int64_t nq, int npmax, int nsel_max,
+                              int k_stride, int mode);
 
 // Memory residence
 bool is_device_ptr(const void* p);
+
+// Every device allocation of the library goes through dev_alloc, so that the
+// test hook rq_test_fail_allocations can make a chosen one fail.
+bool alloc_should_fail();
+template <typename T>
+inline cudaError_t dev_alloc(T** p, size_t bytes) {
+  if (alloc_should_fail()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
 
 // Lets kernel `func` take up to `bytes` of dynamic shared memory on the
 // current device. The opt-in above 48 KB is a per-device attribute, so it is

@@ -321,6 +321,183 @@ scan_plain_kernel(const int32_t* __restrict__ nchunks, const int32_t* __restrict
 }
 
 // ---------------------------------------------------------------------------
+// FastScan estimator (Section 3.3.2, the paper's form: the query is not
+// quantised). For a rotated residual r, table entry T[g][v] is the float32
+// sum of r[8 g + i] over the set bits i of byte v, added in increasing i from
+// 0; a code's s is the sum over groups g, in increasing g, of T[g][code byte
+// g]; t = 2 s - S (S = sum_d r_d in the 32-lane order) = sum_d b_d r_d, and
+// d2 = (nq2 + r_x^2) - 2 (f t), then + 0 -- every operation rounded once.
+// ---------------------------------------------------------------------------
+
+// Builds the D_p/8 x 256 tables from r (shared memory, D_p floats) with the
+// whole block: level h fills the entries whose highest set bit is h from the
+// entry without that bit, so each entry adds its bits in increasing order.
+__device__ inline void build_lut(const float* r, float* T, int groups) {
+  for (int g = threadIdx.x; g < groups; g += blockDim.x) T[g * 256] = 0.0f;
+  __syncthreads();
+  for (int h = 0; h < 8; ++h) {
+    const int span = 1 << h;
+    for (int i = threadIdx.x; i < groups * span; i += blockDim.x) {
+      const int g = i >> h, v = span + (i & (span - 1));
+      T[g * 256 + v] = __fadd_rn(T[g * 256 + v - span], r[8 * g + h]);
+    }
+    __syncthreads();
+  }
+}
+
+template <int NW4>
+__device__ __forceinline__ float estimate_lut_regs(const uint4 (&code)[NW4], const float* T,
+                                                   float2 fac, float nq2, float S) {
+  float sum = 0.0f;
+#pragma unroll
+  for (int w = 0; w < NW4; ++w) {
+    const uint32_t word[4] = {code[w].x, code[w].y, code[w].z, code[w].w};
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int g = 16 * w + j;
+      const float e = T[g * 256 + ((word[j >> 2] >> (8 * (j & 3))) & 255u)];
+      sum = (g == 0) ? e : __fadd_rn(sum, e);
+    }
+  }
+  const float t = __fsub_rn(__fmul_rn(2.0f, sum), S);
+  const float d = __fsub_rn(__fadd_rn(nq2, fac.x), __fmul_rn(2.0f, __fmul_rn(fac.y, t)));
+  return __fadd_rn(d, 0.0f);
+}
+
+// The residual r = q' - P^T c of one (query, probed list) pair into shared
+// memory (D_p floats), by the whole block.
+__device__ __forceinline__ void residual_to_smem(const float* __restrict__ qrot, int64_t q,
+                                                 const float* __restrict__ cR, int c, int dp,
+                                                 float* r) {
+  for (int d = threadIdx.x; d < dp; d += blockDim.x)
+    r[d] = __fsub_rn(qrot[q * dp + d], cR[(int64_t)c * dp + d]);
+}
+
+// Plain (query-level) scan with the FastScan estimator: one block per
+// (query, probed list, chunk of 1024 list vectors); the block builds its
+// pair's tables in shared memory, then each thread estimates its vectors
+// (the codes of its 128-vector steps loaded before they are estimated) and
+// each warp writes the survivor mask word and keys of its 32 vectors.
+template <int NW4>
+__global__ void __launch_bounds__(128)
+scan_lut_kernel(const int32_t* __restrict__ nchunks, const int32_t* __restrict__ probe_ids,
+                int npmax, const float4* __restrict__ qparams, const float* __restrict__ qrot,
+                const float* __restrict__ cR, const int64_t* __restrict__ offsets,
+                const uint8_t* __restrict__ codes, const float2* __restrict__ fac, int dp,
+                const uint32_t* __restrict__ bound, const int32_t* __restrict__ wbase,
+                int64_t mwords, uint32_t* __restrict__ mask, uint64_t* __restrict__ cand,
+                int64_t mask_words, int32_t* err) {
+  constexpr int RB = NW4 >= 2 ? 4 : 8;
+  extern __shared__ __align__(16) float s_lut[];  // D_p/8 x 256 table, then D_p residual
+  float* s_r = s_lut + 32 * dp;
+  const int64_t pair = blockIdx.x;
+  if ((int)blockIdx.y >= nchunks[pair]) return;
+  const int64_t q = pair / npmax;
+  const int c = probe_ids[pair];
+  const int64_t lo = offsets[c], hi = offsets[c + 1];
+  const int64_t start = lo + (int64_t)blockIdx.y * 1024;
+  const int64_t end = min(hi, start + 1024);
+  residual_to_smem(qrot, q, cR, c, dp, s_r);
+  __syncthreads();
+  build_lut(s_r, s_lut, dp / 8);
+  const float4 qp = qparams[pair];
+  const uint32_t tau = bound[q];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t wrow = q * mwords + wbase[pair];
+  for (int64_t b0 = start; b0 < end; b0 += 128 * RB) {
+    uint4 code[RB][NW4];
+    float2 fv[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const int64_t sl = b0 + 128 * r + threadIdx.x;
+      if (sl < end) {
+        const uint4* cp = reinterpret_cast<const uint4*>(codes + sl * (dp / 8));
+#pragma unroll
+        for (int w = 0; w < NW4; ++w) code[r][w] = __ldg(cp + w);
+        fv[r] = __ldg(fac + sl);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const int64_t s0 = b0 + 128 * r;
+      if (s0 + warp * 32 >= end) break;  // warp-uniform: this word is past the chunk's end
+      const int64_t sl = s0 + threadIdx.x;
+      float d = 0.0f;
+      bool pass = false;
+      if (sl < end) {
+        d = estimate_lut_regs<NW4>(code[r], s_lut, fv[r], qp.z, qp.w);
+        pass = orderable(d) <= tau;
+      }
+      const int64_t widx = wrow + (s0 - lo) / 32 + warp;
+      if (!index_ok(widx, mask_words, err)) continue;
+      emit_word(pass, d, (uint32_t)sl, widx, mask, cand, lane);
+    }
+  }
+}
+
+// The FastScan quantities of one pair (a warp): nq2 = ||r||^2 and S = sum_d
+// r_d, both in the 32-lane order, stored as {0, 0, nq2, S}.
+template <int NW4>
+__device__ __forceinline__ void lut_pair(int64_t pair, int64_t q, int c, int lane,
+                                         const float* __restrict__ qrot,
+                                         const float* __restrict__ cR, int dp,
+                                         float4* __restrict__ qparams) {
+  float acc2 = 0.0f, acc1 = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 4 * NW4; ++i) {
+    const int d = lane + 32 * i;
+    const float r = __fsub_rn(qrot[q * dp + d], cR[(int64_t)c * dp + d]);
+    acc2 = __fadd_rn(acc2, __fmul_rn(r, r));
+    acc1 = __fadd_rn(acc1, r);
+  }
+  const float nq2 = lane_tree_sum(acc2);
+  const float S = lane_tree_sum(acc1);
+  if (lane == 0) qparams[pair] = make_float4(0.0f, 0.0f, nq2, S);
+}
+
+// First bound with the FastScan estimator (the same candidates and rank as
+// bound_block): per probe the block builds the pair's tables in `lut`
+// (D_p/8 x 256 floats, then D_p residual floats) and estimates the list's
+// first vectors.
+template <int NW4>
+__device__ inline uint32_t bound_block_lut(int64_t qi, int npmax, int npq, int n_sel,
+                                           const uint64_t* lists,
+                                           const float4* __restrict__ qparams,
+                                           const float* __restrict__ qrot,
+                                           const float* __restrict__ cR,
+                                           const int64_t* __restrict__ offsets,
+                                           const uint8_t* __restrict__ codes,
+                                           const float2* __restrict__ fac, int dp,
+                                           uint32_t* s_bkeys, float* lut, int* hist,
+                                           uint64_t* small, int* ctl) {
+  const int tid = threadIdx.x;
+  const int cap1 = bound_window(n_sel);
+  float* r = lut + 32 * dp;
+  int taken = 0;
+  for (int p = 0; p < npq && taken < cap1; ++p) {
+    const int64_t pair = qi * npmax + p;
+    const uint32_t c = (uint32_t)lists[p];
+    const int64_t lo = offsets[c];
+    const int m = (int)min(offsets[c + 1] - lo, (int64_t)(cap1 - taken));
+    __syncthreads();
+    residual_to_smem(qrot, qi, cR, (int)c, dp, r);
+    __syncthreads();
+    build_lut(r, lut, dp / 8);
+    const float4 qp = qparams[pair];
+    for (int i = tid; i < m; i += blockDim.x) {
+      uint4 code[NW4];
+      const uint4* cp = reinterpret_cast<const uint4*>(codes + (lo + i) * (dp / 8));
+#pragma unroll
+      for (int w = 0; w < NW4; ++w) code[w] = __ldg(cp + w);
+      s_bkeys[taken + i] = orderable(estimate_lut_regs<NW4>(code, lut, __ldg(fac + lo + i), qp.z, qp.w));
+    }
+    taken += m;
+  }
+  __syncthreads();
+  return taken >= n_sel ? block_kth_u32(s_bkeys, taken, n_sel, hist, small, ctl) : kU32Max;
+}
+
+// ---------------------------------------------------------------------------
 // Rotation q' = P^T q (float32 FMA): 8 queries x 64 output columns per
 // block, K in chunks of 128 staged in shared memory with every load of a
 // chunk in flight at once (16-byte loads when the rows allow). The first
@@ -612,7 +789,7 @@ __device__ __forceinline__ float exact_dist_lanes(const RawT* __restrict__ x,
 // Per-warp shared memory of the finalize kernel: selection (P keys), top-k
 // (PK keys), histogram (256 ints), bucket (32 keys), query row (dim floats).
 struct FinalizeLayout {
-  int P, PK, S, dim;  // S: candidate keys staged per query (>= 2048: 64 mask words)
+  int P, PK, S, dim;  // S: candidate keys staged per query (>= 4096: 128 mask words)
   __host__ __device__ int bytes() const {
     return (P + PK + S) * 8 + 256 * 4 + 32 * 8 + ((dim * 4 + 15) & ~15);
   }
@@ -643,7 +820,7 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ int s_ctl[8];
   __shared__ int s_part[4];
-  __shared__ int s_scan[2];
+  __shared__ int s_scan[4];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t row = blockIdx.x;
   uint64_t* s_sel = reinterpret_cast<uint64_t*>(smem);
@@ -710,12 +887,12 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
       }
     }
   } else {
-    // Many: compact the keys to the front of the query's key slots, 64 mask
-    // words (at most S = 2048 keys) at a time through shared memory. The
+    // Many: compact the keys to the front of the query's key slots, 128 mask
+    // words (at most 4096 keys <= S) at a time through shared memory. The
     // keys written never reach the slots of words not yet staged.
     int64_t run = 0;
-    for (int c0 = 0; c0 < T; c0 += 64) {
-      const uint32_t w = (tid < 64 && c0 + tid < T) ? mrow[c0 + tid] : 0u;
+    for (int c0 = 0; c0 < T; c0 += 128) {
+      const uint32_t w = (c0 + tid < T) ? mrow[c0 + tid] : 0u;
       const int pc = __popc(w);
       int ps = pc;
 #pragma unroll
@@ -723,11 +900,12 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
         const int t = __shfl_up_sync(0xffffffffu, ps, o);
         if (lane >= o) ps += t;
       }
-      if (warp < 2 && lane == 31) s_scan[warp] = ps;
+      if (lane == 31) s_scan[warp] = ps;
       __syncthreads();
-      const int tot = s_scan[0] + s_scan[1];
-      if (tid < 64 && pc) {
-        const int at = ps - pc + (warp == 1 ? s_scan[0] : 0);
+      const int tot = s_scan[0] + s_scan[1] + s_scan[2] + s_scan[3];
+      if (pc) {
+        int at = ps - pc;
+        for (int w2 = 0; w2 < warp; ++w2) at += s_scan[w2];
         const uint64_t* kw = krow + (int64_t)(c0 + tid) * 32;
         for (int b = 0; b < pc; ++b) s_stage[at + b] = slot_to_id(kw[b], ids, n_slots, err);
       }
@@ -964,7 +1142,7 @@ __device__ inline uint32_t bound_block(int64_t qi, int npmax, int npq, int n_sel
   constexpr int RB = NW4 >= 4 ? 1 : 4 / NW4;  // codes in flight per thread
   __shared__ __align__(16) uint32_t s_pl[4 * W];
   const int tid = threadIdx.x;
-  const int cap1 = max(kBoundCandidates, n_sel);
+  const int cap1 = bound_window(n_sel);
   int taken = 0;
   for (int p = 0; p < npq && taken < cap1; ++p) {
     const int64_t pair = qi * npmax + p;
@@ -1041,6 +1219,10 @@ struct PrepArgs {
   uint32_t* bound;
   int32_t* nchunks;   // plain scan: `chunk`-vector chunks of each probe (null otherwise)
   int chunk;
+  int lut;            // 1: FastScan estimator (residual sums; tables for the bound)
+  uint32_t* bkeys;    // per query: the first bound's candidate estimates (global scratch)
+  int64_t bkeys_stride;
+  int lut_offset;     // byte offset of the table region in dynamic shared memory
   int32_t* err;
 };
 
@@ -1055,6 +1237,8 @@ __global__ void __launch_bounds__(128, NW4 >= 4 ? 4 : 8) prep_kernel(PrepArgs a)
   const int P = max(2, next_pow2(a.npmax));  // keeps `region` 16-byte aligned
   uint64_t* dst = reinterpret_cast<uint64_t*>(smem);
   uint64_t* region = dst + P;
+  // FastScan tables of the bound (after the region, whose size the host gives)
+  float* lut_region = reinterpret_cast<float*>(smem + a.lut_offset);
   const int npq = min(a.nprobe[row], a.npmax);
   const int got =
       a.g ? probe_select_certified(a.g, a.cn, a.qrot, a.cR, a.nlist, a.npmax, a.dp, row, dst,
@@ -1080,19 +1264,30 @@ __global__ void __launch_bounds__(128, NW4 >= 4 ? 4 : 8) prep_kernel(PrepArgs a)
   // pair's bucket slot in the high word, which held the distance: every
   // reader of the distances above is done after this barrier)
   __syncthreads();
-  for (int p = warp; p < npq; p += 4)
-    quantize_pair<NW4>(row * a.npmax + p, row, (int)(uint32_t)dst[p], lane, a.qrot, a.nq, a.cR,
-                       a.dp, a.qparams, a.planes, a.list_count, a.list_pairs, a.qdb, a.qpb,
-                       a.qrec, &dst[p]);
+  for (int p = warp; p < npq; p += 4) {
+    if (a.lut)
+      lut_pair<NW4>(row * a.npmax + p, row, (int)(uint32_t)dst[p], lane, a.qrot, a.cR, a.dp,
+                    a.qparams);
+    else
+      quantize_pair<NW4>(row * a.npmax + p, row, (int)(uint32_t)dst[p], lane, a.qrot, a.nq,
+                         a.cR, a.dp, a.qparams, a.planes, a.list_count, a.list_pairs, a.qdb,
+                         a.qpb, a.qrec, &dst[p]);
+  }
   // The block's own writes of planes and parameters are visible to it
   // after the barrier.
   __syncthreads();
   const int n_sel = a.nsel[row];
   uint32_t tau = kU32Max;
-  if (!*a.no_prune && n_sel > 0)
-    tau = bound_block<NW4>(row, a.npmax, npq, n_sel, dst, a.qparams, a.planes, a.offsets,
-                           a.codes, a.fac, a.dp, reinterpret_cast<uint32_t*>(region), hist,
-                           small, ctl);
+  if (!*a.no_prune && n_sel > 0) {
+    uint32_t* bk = a.bkeys + row * a.bkeys_stride;
+    if (a.lut)
+      tau = bound_block_lut<NW4>(row, a.npmax, npq, n_sel, dst, a.qparams, a.qrot, a.cR,
+                                 a.offsets, a.codes, a.fac, a.dp, bk, lut_region, hist, small,
+                                 ctl);
+    else
+      tau = bound_block<NW4>(row, a.npmax, npq, n_sel, dst, a.qparams, a.planes, a.offsets,
+                             a.codes, a.fac, a.dp, bk, hist, small, ctl);
+  }
   if (tid == 0) a.bound[row] = tau;
   if (a.qrec) {
     // the rest of each pair record: query, first mask word, bound
@@ -1127,7 +1322,12 @@ void rebase(T*& p, char* base) {
   p = reinterpret_cast<T*>(base + reinterpret_cast<size_t>(p));
 }
 
-rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, Workspace& ws) {
+// Above this many bytes a batch's workspace is split into sub-batches.
+constexpr size_t kWorkspaceBudget = size_t(8) << 30;
+
+// Lays out the workspace of a search shape: every field as an offset from
+// the base, the total in ws.bytes.
+void layout_workspace(const rq_index* ix, const SearchShape& sh, Workspace& ws) {
   const int64_t nq = sh.nq, np = sh.npmax;
   const int W = ix->dp / 32;
   ws.mwords = std::max<int64_t>(1, ix->top_words_prefix[std::min(np, (int64_t)ix->nlist)]);
@@ -1148,6 +1348,7 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
   L.take(&ws.wtotal, nq);
   L.take(&ws.cand, nq * ws.cap);
   L.take(&ws.sel, nq * sh.nsel_max);
+  L.take(&ws.bkeys, nq * bound_window(sh.nsel_max));
   // the per-query parameters in one region (one copy from the pinned staging
   // buffer, which has the same layout): nprobe, k, selection size, re-rank
   // flag (+1: the no-prune flag)
@@ -1166,8 +1367,36 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
     L.take(&ws.qpb, (int64_t)ix->nlist * nq + 2);  // + a couple read past the last bucket
   }
   ws.bytes = L.off;
+}
+
+size_t workspace_bytes(const rq_index* ix, const SearchShape& sh) {
+  Workspace ws;
+  layout_workspace(ix, sh, ws);
+  return ws.bytes;
+}
+
+}  // namespace
+
+// Device bytes one search of this shape holds: its workspace, or that of the
+// sub-batches it is split into.
+size_t search_workspace_bytes(const rq_index* ix, int64_t nq, int npmax, int nsel_max,
+                              int k_stride, int mode) {
+  SearchShape sh{nq, npmax, nsel_max, k_stride, mode, 0, 0, kPlainChunk, 0};
+  size_t b = workspace_bytes(ix, sh);
+  while (sh.nq > 1 && b > kWorkspaceBudget) {
+    sh.nq = (sh.nq + 1) / 2;
+    b = workspace_bytes(ix, sh);
+  }
+  return b;
+}
+
+namespace {
+
+rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, Workspace& ws) {
+  const int64_t nq = sh.nq;
+  layout_workspace(ix, sh, ws);
   (void)st;
-  cudaError_t e = cudaMalloc(&ws.base, ws.bytes);
+  cudaError_t e = dev_alloc(&ws.base, ws.bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     ws.base = nullptr;
@@ -1189,6 +1418,7 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
   rebase(ws.wtotal, b);
   rebase(ws.cand, b);
   rebase(ws.sel, b);
+  rebase(ws.bkeys, b);
   rebase(ws.nprobe, b);
   ws.kq = ws.nprobe + nq;
   ws.nsel = ws.nprobe + 2 * nq;
@@ -1258,20 +1488,34 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
     a.bound = ws.bound;
     a.nchunks = grouped ? nullptr : ws.nchunks;
     a.chunk = sh.chunk;
+    a.lut = sh.lut;
+    a.bkeys = ws.bkeys;
+    a.bkeys_stride = bound_window(sh.nsel_max);
     a.err = ix->d_err;
+    // the probe selection's shared region: the certified form's keys, rows,
+    // candidates and query; the exact form stages the nlist keys when they fit
     const size_t stage =
         certified ? ((std::max<size_t>((size_t)ix->nlist * 8, (size_t)kProbeRowStage * dp * 4) +
                       15) & ~(size_t)15) + kProbeCandCap * 4 + (size_t)dp * 4
-                  : 0;
-    const int kpw = std::max(kBoundCandidates, sh.nsel_max);
-    const size_t smem =
-        (size_t)std::max(2, next_pow2_host(np)) * 8 + std::max<size_t>(stage, (size_t)kpw * 4);
+                  : (ix->nlist <= kProbeStageKeys ? (size_t)ix->nlist * 8 : 0);
+    size_t smem = (size_t)std::max(2, next_pow2_host(np)) * 8 + std::max<size_t>(stage, 64);
+    smem = (smem + 15) & ~(size_t)15;
+    a.lut_offset = (int)smem;
+    if (sh.lut) smem += (size_t)(32 * dp + dp) * sizeof(float);
     RQ_TRY(allow_dynamic_smem((const void*)prep_kernel<NW4>, 200 * 1024));
     prep_kernel<NW4><<<(unsigned)nq, 128, smem, st>>>(a);
   }
   tm.mark(RQ_STAGE_BOUND, st);
   tm.mark(RQ_STAGE_WORKLIST, st);
-  if (sh.mode == RQ_SCAN_PLAIN) {
+  if (sh.lut) {
+    tm.mark(RQ_STAGE_SCAN, st);
+    const unsigned chunks = (unsigned)std::max<int64_t>(1, (ix->max_list_len + 1023) / 1024);
+    const size_t lsm = (size_t)(32 * dp + dp) * sizeof(float);
+    scan_lut_kernel<NW4 <= 2 ? NW4 : 1><<<dim3((unsigned)pairs, chunks), 128, lsm, st>>>(
+        ws.nchunks, ws.probe_ids, np, ws.qparams, ws.qrot, ix->cR, ix->offsets, ix->codes,
+        ix->fac, dp, ws.bound, ws.wbase, ws.mwords, ws.mask, ws.cand, nq * ws.mwords,
+        ix->d_err);
+  } else if (sh.mode == RQ_SCAN_PLAIN) {
     tm.mark(RQ_STAGE_SCAN, st);
     const unsigned chunks =
         (unsigned)std::max<int64_t>(1, (ix->max_list_len + sh.chunk - 1) / sh.chunk);
@@ -1337,7 +1581,7 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
   // 5-6. candidate selection and exact re-rank
   tm.mark(RQ_STAGE_SELECT, st);
   {
-    const FinalizeLayout lay{next_pow2_host(sh.nsel_max), next_pow2_host(sh.k_stride), 2048,
+    const FinalizeLayout lay{next_pow2_host(sh.nsel_max), next_pow2_host(sh.k_stride), 4096,
                              ix->dim};
     const size_t smem = lay.bytes();
     RQ_TRY(allow_dynamic_smem((const void*)finalize_kernel<uint8_t>, 200 * 1024));
@@ -1515,9 +1759,9 @@ rq_status autotune(rq_index* ix, const float* queries, int64_t nq, const int32_t
     }
   } sc;
   sc.ix = ix;
-  RQ_CUDA(cudaMalloc(&sc.d_ids, sizeof(int64_t) * nq * k));
-  RQ_CUDA(cudaMalloc(&sc.d_d, sizeof(float) * nq * k));
-  RQ_CUDA(cudaMalloc(&sc.d_q, sizeof(float) * nq * ix->dim));
+  RQ_CUDA(dev_alloc(&sc.d_ids, sizeof(int64_t) * nq * k));
+  RQ_CUDA(dev_alloc(&sc.d_d, sizeof(float) * nq * k));
+  RQ_CUDA(dev_alloc(&sc.d_q, sizeof(float) * nq * ix->dim));
   RQ_CUDA(cudaMemcpy(sc.d_q, queries, sizeof(float) * nq * ix->dim, cudaMemcpyDefault));
   RQ_CUDA(cudaStreamCreateWithFlags(&sc.st, cudaStreamNonBlocking));
   RQ_CUDA(cudaEventCreate(&sc.e0));
@@ -1574,53 +1818,16 @@ void free_plans(rq_index* ix) {
   ix->plans.clear();
 }
 
-rq_status search_run(rq_index* ix, const float* queries, int64_t nq, const int32_t* nprobe,
-                     const int32_t* k, const int32_t* n_rerank, int k_stride, int64_t* out_ids,
-                     float* out_dist, const rq_search_opts* opts, cudaStream_t st) {
-  if (!ix) return fail(RQ_ERR_INVALID_ARG, "index is NULL");
-  if (nq < 0) return fail(RQ_ERR_INVALID_ARG, "nq < 0");
-  if (nq == 0) return RQ_OK;
-  if (!queries || !out_ids || !out_dist || !nprobe || !k || !n_rerank)
-    return fail(RQ_ERR_INVALID_ARG, "NULL pointer argument");
-  if (nq > (int64_t)1 << 24) return fail(RQ_ERR_INVALID_ARG, "nq above 2^24 in one call");
-  const int pmax_allowed = std::min(ix->nlist, kMaxSelect);
-  std::vector<int32_t> h_np(nq), h_k(nq), h_ns(nq), h_rr(nq + 1);
-  int npmax = 0, nsel_max = 0, kmax = 0;
-  for (int64_t i = 0; i < nq; ++i) {
-    const int a = nprobe[i], b = k[i], c = n_rerank[i];
-    if (a < 1 || a > pmax_allowed)
-      return fail(RQ_ERR_INVALID_ARG, "nprobe " + std::to_string(a) + " outside [1, " +
-                                          std::to_string(pmax_allowed) + "]");
-    if (b < 1 || b > kMaxSelect) return fail(RQ_ERR_INVALID_ARG, "k outside [1, 4096]");
-    if (c != 0 && (c < b || c > kMaxSelect))
-      return fail(RQ_ERR_INVALID_ARG, "n_rerank must be 0 or in [k, 4096]");
-    h_np[i] = a;
-    h_k[i] = b;
-    h_ns[i] = c > 0 ? c : b;
-    h_rr[i] = c > 0 ? 1 : 0;
-    npmax = std::max(npmax, a);
-    nsel_max = std::max(nsel_max, h_ns[i]);
-    kmax = std::max(kmax, b);
-  }
-  if (k_stride < kmax) return fail(RQ_ERR_INVALID_ARG, "k_stride below the largest k");
-  int mode = opts ? opts->scan_mode : RQ_SCAN_AUTO;
-  int chunk = (opts && opts->plain_chunk > 0) ? opts->plain_chunk : kPlainChunk;
-  if (mode == RQ_SCAN_AUTO) {
-    int64_t sum_np = 0;
-    for (int64_t i = 0; i < nq; ++i) sum_np += h_np[i];
-    const TunedChoice t = tuned_for(ix, tune_class(nq, sum_np, ix->nlist));
-    mode = t.mode;
-    if (!(opts && opts->plain_chunk > 0)) chunk = t.chunk;
-  }
-  if (mode < RQ_SCAN_PLAIN || mode > RQ_SCAN_MMA)
-    return fail(RQ_ERR_INVALID_ARG, "unknown scan mode");
-  // only the plain scan has chunks; codes wider than 256 bits use 1024
-  if (mode != RQ_SCAN_PLAIN || ix->dp > 256) chunk = kPlainChunk;
-  if (chunk != 1024 && chunk != 2048 && chunk != 4096)
-    return fail(RQ_ERR_INVALID_ARG, "plain_chunk must be 1024, 2048 or 4096");
-  if (mode == RQ_SCAN_MMA && !mma_supported(ix)) mode = RQ_SCAN_GROUPED;
-  const bool no_prune = opts && opts->no_prune;
-  h_rr[nq] = no_prune ? 1 : 0;
+// One launch sequence for a batch whose per-query parameters are already
+// checked: h_np, h_k, h_ns (selection sizes) and h_rr (re-rank flags, then
+// the no-prune flag at [nq]), searched as shape `sh` (sh.npmax and
+// sh.nsel_max may exceed this batch's own, so that a split batch keeps the
+// strides of its parent).
+rq_status search_part(rq_index* ix, const float* queries, int64_t nq, const int32_t* h_np,
+                      const int32_t* h_k, const int32_t* h_ns, const int32_t* h_rr, int k_stride,
+                      int64_t* out_ids, float* out_dist, const rq_search_opts* opts,
+                      cudaStream_t st, SearchShape sh) {
+  const int npmax = sh.npmax, nsel_max = sh.nsel_max;
   float* stage_ms = opts ? opts->stage_ms : nullptr;
   const bool use_graph = opts && opts->use_graph && !stage_ms;
   const rq_search_dump* dump = opts ? opts->dump : nullptr;
@@ -1648,8 +1855,6 @@ rq_status search_run(rq_index* ix, const float* queries, int64_t nq, const int32
   }
   const bool ids_dev = is_device_ptr(out_ids), d_dev = is_device_ptr(out_dist);
 
-  const int withhold = (opts && opts->test_stall && mode != RQ_SCAN_PLAIN) ? 1 : 0;
-  SearchShape sh{nq, npmax, nsel_max, k_stride, mode, no_prune ? 1 : 0, withhold, chunk};
   cudaStream_t run_st = st;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   if (use_graph && st == nullptr) {
@@ -1669,10 +1874,10 @@ rq_status search_run(rq_index* ix, const float* queries, int64_t nq, const int32
   // call's copy out of it must have run before it is overwritten.
   RQ_CUDA(cudaEventSynchronize(plan->params_ready));
   int32_t* hp = plan->h_params;
-  std::memcpy(hp, h_np.data(), sizeof(int32_t) * nq);
-  std::memcpy(hp + nq, h_k.data(), sizeof(int32_t) * nq);
-  std::memcpy(hp + 2 * nq, h_ns.data(), sizeof(int32_t) * nq);
-  std::memcpy(hp + 3 * nq, h_rr.data(), sizeof(int32_t) * (nq + 1));
+  std::memcpy(hp, h_np, sizeof(int32_t) * nq);
+  std::memcpy(hp + nq, h_k, sizeof(int32_t) * nq);
+  std::memcpy(hp + 2 * nq, h_ns, sizeof(int32_t) * nq);
+  std::memcpy(hp + 3 * nq, h_rr, sizeof(int32_t) * (nq + 1));
   RQ_CUDA(cudaMemcpyAsync(ws.nprobe, hp, sizeof(int32_t) * (4 * nq + 1), cudaMemcpyHostToDevice,
                           run_st));
   RQ_CUDA(cudaEventRecord(plan->params_ready, run_st));
@@ -1746,6 +1951,111 @@ rq_status search_run(rq_index* ix, const float* queries, int64_t nq, const int32
       RQ_CUDA(cudaEventElapsedTime(&ms, tm.ev[i], tm.ev[i + 1]));
       stage_ms[i] = ms;
     }
+  }
+  return RQ_OK;
+}
+
+
+rq_status search_run(rq_index* ix, const float* queries, int64_t nq, const int32_t* nprobe,
+                     const int32_t* k, const int32_t* n_rerank, int k_stride, int64_t* out_ids,
+                     float* out_dist, const rq_search_opts* opts, cudaStream_t st) {
+  if (!ix) return fail(RQ_ERR_INVALID_ARG, "index is NULL");
+  if (nq < 0) return fail(RQ_ERR_INVALID_ARG, "nq < 0");
+  if (nq == 0) return RQ_OK;
+  if (!queries || !out_ids || !out_dist || !nprobe || !k || !n_rerank)
+    return fail(RQ_ERR_INVALID_ARG, "NULL pointer argument");
+  if (nq > (int64_t)1 << 24) return fail(RQ_ERR_INVALID_ARG, "nq above 2^24 in one call");
+  const int pmax_allowed = std::min(ix->nlist, kMaxSelect);
+  std::vector<int32_t> h_np(nq), h_k(nq), h_ns(nq), h_rr(nq + 1);
+  int npmax = 0, nsel_max = 0, kmax = 0;
+  for (int64_t i = 0; i < nq; ++i) {
+    const int a = nprobe[i], b = k[i], c = n_rerank[i];
+    if (a < 1 || a > pmax_allowed)
+      return fail(RQ_ERR_INVALID_ARG, "nprobe " + std::to_string(a) + " outside [1, " +
+                                          std::to_string(pmax_allowed) + "]");
+    if (b < 1 || b > kMaxSelect) return fail(RQ_ERR_INVALID_ARG, "k outside [1, 4096]");
+    if (c != 0 && (c < b || c > kMaxSelect))
+      return fail(RQ_ERR_INVALID_ARG, "n_rerank must be 0 or in [k, 4096]");
+    h_np[i] = a;
+    h_k[i] = b;
+    h_ns[i] = c > 0 ? c : b;
+    h_rr[i] = c > 0 ? 1 : 0;
+    npmax = std::max(npmax, a);
+    nsel_max = std::max(nsel_max, h_ns[i]);
+    kmax = std::max(kmax, b);
+  }
+  if (k_stride < kmax) return fail(RQ_ERR_INVALID_ARG, "k_stride below the largest k");
+  int mode = opts ? opts->scan_mode : RQ_SCAN_AUTO;
+  int chunk = (opts && opts->plain_chunk > 0) ? opts->plain_chunk : kPlainChunk;
+  if (mode == RQ_SCAN_AUTO) {
+    int64_t sum_np = 0;
+    for (int64_t i = 0; i < nq; ++i) sum_np += h_np[i];
+    const TunedChoice t = tuned_for(ix, tune_class(nq, sum_np, ix->nlist));
+    mode = t.mode;
+    if (!(opts && opts->plain_chunk > 0)) chunk = t.chunk;
+  }
+  if (mode < RQ_SCAN_PLAIN || mode > RQ_SCAN_MMA)
+    return fail(RQ_ERR_INVALID_ARG, "unknown scan mode");
+  // only the plain scan has chunks; codes wider than 256 bits use 1024
+  if (mode != RQ_SCAN_PLAIN || ix->dp > 256) chunk = kPlainChunk;
+  if (chunk != 1024 && chunk != 2048 && chunk != 4096)
+    return fail(RQ_ERR_INVALID_ARG, "plain_chunk must be 1024, 2048 or 4096");
+  if (mode == RQ_SCAN_MMA && !mma_supported(ix)) mode = RQ_SCAN_GROUPED;
+  const int estimator = opts ? opts->estimator : RQ_EST_BQ4;
+  if (estimator != RQ_EST_BQ4 && estimator != RQ_EST_LUT)
+    return fail(RQ_ERR_INVALID_ARG, "unknown estimator");
+  if (estimator == RQ_EST_LUT) {
+    if (ix->dp > 256)
+      return fail(RQ_ERR_NOT_IMPLEMENTED, "the FastScan estimator is built for D_p <= 256");
+    mode = RQ_SCAN_PLAIN;  // its scan runs on the query-level schedule
+    chunk = kPlainChunk;
+  }
+  const bool no_prune = opts && opts->no_prune;
+  h_rr[nq] = no_prune ? 1 : 0;
+  const int withhold = (opts && opts->test_stall && mode != RQ_SCAN_PLAIN) ? 1 : 0;
+  SearchShape sh{nq, npmax, nsel_max, k_stride, mode, no_prune ? 1 : 0, withhold, chunk,
+                 estimator == RQ_EST_LUT ? 1 : 0};
+  // A batch whose workspace would pass the budget runs as consecutive
+  // sub-batches of one workspace (the survivor slots grow with the pairs
+  // scanned); results and dump rows land where the whole batch puts them.
+  int64_t sub = nq;
+  while (sub > 1) {
+    SearchShape t = sh;
+    t.nq = sub;
+    if (workspace_bytes(ix, t) <= kWorkspaceBudget) break;
+    sub = (sub + 1) / 2;
+  }
+  if (sub == nq) return search_part(ix, queries, nq, h_np.data(), h_k.data(), h_ns.data(),
+                                    h_rr.data(), k_stride, out_ids, out_dist, opts, st, sh);
+  float part_ms[RQ_STAGE_COUNT];
+  if (opts && opts->stage_ms)
+    for (int i = 0; i < RQ_STAGE_COUNT; ++i) opts->stage_ms[i] = 0.0f;
+  for (int64_t i0 = 0; i0 < nq; i0 += sub) {
+    const int64_t n1 = std::min(sub, nq - i0);
+    rq_search_opts po = opts ? *opts : rq_search_opts{};
+    rq_search_dump pd{};
+    if (opts && opts->dump) {
+      const rq_search_dump& d = *opts->dump;
+      const int64_t cb = ix->dp / 8;
+      pd.qrot = d.qrot ? d.qrot + i0 * ix->dp : nullptr;
+      pd.probe_ids = d.probe_ids ? d.probe_ids + i0 * npmax : nullptr;
+      pd.probe_dist = d.probe_dist ? d.probe_dist + i0 * npmax : nullptr;
+      pd.qparams = d.qparams ? d.qparams + i0 * npmax * 4 : nullptr;
+      pd.planes = d.planes ? d.planes + i0 * npmax * 4 * cb : nullptr;
+      pd.bound = d.bound ? d.bound + i0 : nullptr;
+      pd.selected = d.selected ? d.selected + i0 * nsel_max : nullptr;
+      pd.n_candidates = d.n_candidates ? d.n_candidates + i0 : nullptr;
+      po.dump = &pd;
+    }
+    if (opts && opts->stage_ms) po.stage_ms = part_ms;
+    std::vector<int32_t> rr(h_rr.begin() + i0, h_rr.begin() + i0 + n1);
+    rr.push_back(h_rr[nq]);
+    SearchShape t = sh;
+    t.nq = n1;
+    RQ_TRY(search_part(ix, queries + i0 * ix->dim, n1, h_np.data() + i0, h_k.data() + i0, h_ns.data() + i0, rr.data(),
+                       k_stride, out_ids + i0 * k_stride, out_dist + i0 * k_stride, &po, st, t));
+    if (opts && opts->stage_ms)
+      for (int i = 0; i < RQ_STAGE_COUNT; ++i) opts->stage_ms[i] += part_ms[i];
   }
   return RQ_OK;
 }

@@ -72,9 +72,11 @@ def search_dump(ix, q, nprobe, k, n_rerank, mixed=False, **kw):
 
 
 def replay_and_compare(hix: dict, q: np.ndarray, dump: dict, prune: bool = True,
-                       check_probe: bool = True):
+                       check_probe: bool = True, estimator: str = "bq4"):
     """Recompute every stage in the oracle from the GPU's inputs to it and
-    require bit-equality. Returns counts of compared items."""
+    require bit-equality. Returns counts of compared items. With
+    estimator="lut" the per-pair quantities are nq2 and the residual sum
+    (no planes)."""
     nq = q.shape[0]
     npmax = dump["probe_ids"].shape[1]
     stats = dict(pairs=0, candidates=0)
@@ -86,9 +88,15 @@ def replay_and_compare(hix: dict, q: np.ndarray, dump: dict, prune: bool = True,
     for i in range(nq):
         np_i = int(dump["npb"][i])
         pids = dump["probe_ids"][i, :np_i].astype(np.int64)
-        d2, cid, qs = R.list_candidates(hix, dump["qrot"][i], pids)
+        d2, cid, qs = R.list_candidates(hix, dump["qrot"][i], pids, estimator)
         for p, qz in enumerate(qs):
             gp = dump["qparams"][i, p]
+            if estimator == "lut":
+                res = np.asarray(qz, np.float32)
+                assert gp[2:3].view(np.uint32)[0] == R.lane_sum(res * res).view(np.uint32), (i, p, "nq2")
+                assert gp[3:4].view(np.uint32)[0] == R.lane_sum(res).view(np.uint32), (i, p, "sum")
+                stats["pairs"] += 1
+                continue
             assert gp[0] == qz["vl"][0] and gp[1] == qz["delta"][0], (i, p, "vl/delta")
             assert gp[2].view(np.uint32) == qz["nq2"][0].view(np.uint32), (i, p, "nq2")
             assert gp[3:4].view(np.int32)[0] == qz["sq"][0], (i, p, "Sq")
@@ -100,6 +108,7 @@ def replay_and_compare(hix: dict, q: np.ndarray, dump: dict, prune: bool = True,
         npass = int(np.count_nonzero(R.orderable(d2) <= np.uint64(tau)))
         assert int(dump["n_candidates"][i]) == npass, (i, "candidates passing the bound")
         sel = R.select_candidates(d2, cid, n_sel, prune)
+        stats.setdefault("estimates", []).append(d2)
         gsel = np.sort(dump["selected"][i, :n_sel])   # a set when re-ranked
         assert np.array_equal(gsel[:sel.size], sel), (i, "selected keys")
         assert np.all(gsel[sel.size:] == U64_MAX), (i, "selection padding")

@@ -397,3 +397,52 @@ def test_plain_chunks_and_tuned_choices_are_identical(rq, tmp_path):
     assert len(open(cache).read().splitlines()) == 1
     got = ix2.search(q, 3, 10, 200)
     assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+
+
+# ---------------------------------------------------------------- FastScan estimator
+@pytest.mark.parametrize("prune", [True, False])
+def test_fastscan_estimator_replays_bit_exact(tiny, prune):
+    """The paper's FastScan form (full-precision residual, float32 tables per
+    8 dimensions): per-pair sums, bound, survivors, selection and results
+    replayed in the oracle from the GPU's rotated queries, bit for bit."""
+    _, q, ix, h = tiny
+    rq = lib()
+    dump = search_dump(ix, q, 8, 10, 100, estimator=rq.RQ_EST_LUT, no_prune=not prune)
+    st = replay_and_compare(h, q, dump, prune=prune, estimator="lut")
+    assert st["pairs"] == q.shape[0] * 8
+    # the two estimators differ (the 4-bit query is an approximation of it)
+    d4 = search_dump(ix, q, 8, 10, 100)
+    assert not np.array_equal(d4["selected"], dump["selected"])
+
+
+def test_fastscan_estimator_mixed_padded_and_unranked(rq):
+    """FastScan with mixed per-query nprobe / k / n_rerank (including top-k
+    by the estimate), at D_p 256, and refused above 256."""
+    mix = W.mixture("tiny", dim=200)
+    x = mix.base(4000)
+    q = mix.queries(30)
+    ix = rq.rq_build(x, 24, seed=6, kmeans_iters=3)
+    h = host_index(ix)
+    npb, kk = W.per_query_params(30, 8, (1, 24), (1, 10, 20))
+    nr = np.where(np.arange(30) % 4 == 0, 0, np.maximum(kk, 60)).astype(np.int32)
+    dump = search_dump(ix, q, npb, kk, nr, mixed=True, estimator=rq.RQ_EST_LUT)
+    replay_and_compare(h, q, dump, estimator="lut")
+    hd = W.mixture("highdim")
+    ixh = rq.rq_build(hd.base(2000), 8, seed=1, kmeans_iters=2)
+    with pytest.raises(rq.RQError) as e:
+        ixh.search(hd.queries(2), 2, 10, 50, estimator=rq.RQ_EST_LUT)
+    assert e.value.status == rq.RQ_ERR_NOT_IMPLEMENTED
+
+
+def test_exact_probe_path_wide_codes_many_lists(rq):
+    """D_p above 128 takes the exact centroid ranking, whose selection stages
+    all nlist keys in shared memory: 800 lists (6.4 KB of keys) at D_p 256,
+    replayed bit for bit in every mode that D_p supports."""
+    mix = W.mixture("tiny", dim=200)
+    x = mix.base(20000)
+    q = mix.queries(10)
+    ix = rq.rq_build(x, 800, seed=9, kmeans_iters=2)
+    h = host_index(ix)
+    for mode in (1, 2):
+        dump = search_dump(ix, q, 12, 10, 100, scan_mode=mode)
+        replay_and_compare(h, q, dump)

@@ -69,6 +69,38 @@ def test_skewed_full_size_modes_agree_and_replay(skewed):
     h = host_index(ix)
     stats = replay_and_compare(h, q[rows], sub)
     assert stats["pairs"] == int(npb[rows].sum())
+    # the FastScan estimator on the same batch, sampled replay
+    lut = search_dump(ix, q, npb, kk, nr, mixed=True, estimator=rq.RQ_EST_LUT)
+    sub = {key: (v[rows] if isinstance(v, np.ndarray) and v.shape[:1] == (nq,) else v)
+           for key, v in lut.items()}
+    replay_and_compare(h, q[rows], sub, estimator="lut")
     # the plain scan's chunking is exercised: probed lists longer than a chunk
     lens = np.diff(h["offsets"])
     assert lens[base["probe_ids"][rows][base["probe_ids"][rows] >= 0]].max() > 4 * 1024
+
+
+def test_skewed_large_batch_split_equals_small_batches(skewed):
+    """A batch whose survivor slots would pass the workspace budget (2048
+    queries at nprobe 512 on the skewed index: tens of GB) runs as
+    sub-batches of one workspace; its results and dumped intermediates equal
+    those of the same queries searched in small batches, in every mode."""
+    rq, ix = skewed
+    wl = W.WORKLOADS["skewed"]
+    nq = 2048
+    q = wl["mix"].queries(nq)
+    qd = torch.from_numpy(q).cuda()
+    ref_i = torch.empty((nq, 10), dtype=torch.int64, device="cuda")
+    ref_d = torch.empty((nq, 10), dtype=torch.float32, device="cuda")
+    for b0 in range(0, nq, 128):
+        ix.search(qd[b0:b0 + 128], 512, 10, 200, out_ids=ref_i[b0:b0 + 128],
+                  out_dist=ref_d[b0:b0 + 128], scan_mode=3)
+    torch.cuda.synchronize()
+    for mode in (3, 2):
+        oi = torch.empty((nq, 10), dtype=torch.int64, device="cuda")
+        od = torch.empty((nq, 10), dtype=torch.float32, device="cuda")
+        bound = torch.empty((nq,), dtype=torch.int32, device="cuda")
+        ix.search(qd, 512, 10, 200, out_ids=oi, out_dist=od, scan_mode=mode,
+                  dump={"bound": bound})
+        torch.cuda.synchronize()
+        assert torch.equal(oi, ref_i) and torch.equal(od, ref_d), mode
+    assert ix.device_error() == 0

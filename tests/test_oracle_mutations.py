@@ -62,6 +62,16 @@ CASES = {
     "ip_planes: plane weight j + 1": (R, "ip_planes", "(1 << j)", "(j + 1)",
                                       [P.test_integer_estimator_forms_agree_exactly] + EST),
     "scan_factors: sqrt(D_p) dropped": (R, "scan_factors", "r32 / (sq * alpha32)", "r32 / alpha32", EST),
+    # FastScan form (unquantised query)
+    "lut_tables: most significant bit first": (R, "lut_tables", "acc = acc + res[i::8]",
+                                               "acc = acc + res[7 - i::8]",
+                                               [P.test_lut_tables_by_brute_force_order]),
+    "estimate_lut: s instead of 2 s": (R, "estimate_lut", "t = F32(2) * s - lane_sum(res)",
+                                       "t = s - lane_sum(res)",
+                                       [P.test_lut_estimator_is_eq4_with_full_precision_query]),
+    "estimate_lut: sum of the residual dropped": (R, "estimate_lut", "t = F32(2) * s - lane_sum(res)",
+                                                  "t = F32(2) * s",
+                                                  [P.test_lut_estimator_is_eq4_with_full_precision_query]),
     # query quantisation
     "quantize: rounds down": (R, "quantize", "* inv[..., None] + F32(0.5)", "* inv[..., None]",
                               [P.test_quantize_error_bound_and_degenerate] + EST),
@@ -138,6 +148,11 @@ CASES = {
                                         [P.test_prune_is_lossless_including_ties]),
     "first_bound: one rank early": (R, "first_bound", "[n_sel - 1])", "[max(0, n_sel - 2)])",
                                     [P.test_prune_is_lossless_including_ties]),
+    "bound_window: no 16 n_sel term": (R, "bound_window", "min(BOUND_FACTOR * n_sel, BOUND_MAX)",
+                                       "BOUND_MIN", [P.test_first_bound_window_and_tightness]),
+    "first_bound: window one short": (R, "first_bound", "bound_window(n_sel) if window is None else window",
+                                      "bound_window(n_sel) - 1 if window is None else window",
+                                      [P.test_first_bound_window_and_tightness]),
     "select_running_bound: bound is the held minimum": (R, "select_running_bound", "top = max(held)",
                                                         "top = min(held)",
                                                   [P.test_running_bound_form_equals_first_bound_form]),
@@ -146,8 +161,8 @@ CASES = {
                                                 [P.test_running_bound_form_equals_first_bound_form]),
     "rerank: absolute instead of squared": (R, "rerank", "d = lane_sum(diff * diff)", "d = lane_sum(np.abs(diff))",
                                             [P.test_rerank_matches_fp64_and_pads]),
-    "list_candidates: residual sign": (R, "list_candidates", 'quantize((qrot_i - index["cR"][c])[None, :])',
-                                       'quantize((index["cR"][c] - qrot_i)[None, :])',
+    "list_candidates: residual sign": (R, "list_candidates", 'res = (qrot_i - index["cR"][c])',
+                                       'res = (index["cR"][c] - qrot_i)',
                                        [P.test_recall_target_on_tiny_workload]),
     "search: selects k instead of n_rerank": (R, "search", "n_sel = int(nrr[i]) if nrr[i] > 0 else int(kk[i])",
                                               "n_sel = int(kk[i])", [P.test_search_limit_is_exact_knn]),

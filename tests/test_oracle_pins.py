@@ -391,6 +391,76 @@ def test_eq5_with_exact_inner_product_is_exact_distance():
     assert np.allclose(d2, ((x - q) ** 2).sum(axis=1), rtol=1e-12)
 
 
+def test_lut_tables_by_brute_force_order():
+    """Each FastScan entry is the float32 sum of the residual entries of the
+    entry's set bits, added in increasing bit order from 0 (checked one entry
+    at a time), LSB-first like the codes."""
+    rng = np.random.default_rng(41)
+    res = (rng.standard_normal(128) * np.float32(1e3)).astype(F32)
+    res[::7] *= np.float32(1e-6)                     # mixed magnitudes: order matters
+    T = R.lut_tables(res)
+    assert T.shape == (16, 256)
+    for g in (0, 5, 15):
+        for v in range(256):
+            acc = np.float32(0)
+            for i in range(8):
+                if (v >> i) & 1:
+                    acc = np.float32(acc + res[8 * g + i])
+            assert T[g, v] == acc, (g, v)
+    # the byte of a code addresses its own group: one set bit picks one entry
+    code = np.zeros((1, 16), np.uint8)
+    code[0, 3] = 1 << 5
+    assert R.lut_tables(res)[3, code[0, 3]] == res[8 * 3 + 5]
+
+
+def test_lut_estimator_is_eq4_with_full_precision_query():
+    """The FastScan form evaluates Eq. 4 with the unquantised residual: on
+    integer-valued residuals (every float32 sum exact) t = sum_d b_d res_d
+    exactly and d2 equals the t-form evaluated in float64 then rounded by the
+    same float32 steps; on real residuals t is within the float32 rounding of
+    the float64 dot product; and the 4-bit quantised estimate differs from it
+    by at most D_p delta / 2 in t (the per-dimension quantisation error)."""
+    rng = np.random.default_rng(43)
+    dp = 128
+    codes = rng.integers(0, 256, (300, dp // 8)).astype(np.uint8)
+    bits = R.unpack_bits(codes, dp).astype(np.int64)
+    b = 2 * bits - 1
+    r2 = rng.uniform(0.5, 2.0, 300).astype(F32)
+    f = rng.uniform(0.01, 0.2, 300).astype(F32)
+    res_i = rng.integers(-20, 21, dp).astype(F32)
+    d = R.estimate_lut(codes, r2, f, res_i)
+    t = (b * res_i.astype(np.int64)).sum(axis=1)
+    nq2 = np.float32((res_i.astype(np.int64) ** 2).sum())
+    ref = (nq2 + r2) - np.float32(2) * (f * t.astype(F32))
+    assert np.array_equal(d, (ref + np.float32(0)).astype(F32))
+    res = rng.standard_normal(dp).astype(F32)
+    T = R.lut_tables(res)
+    s = np.zeros(300, F32)
+    for g in range(dp // 8):
+        s = s + T[g][codes[:, g]]
+    t32 = np.float32(2) * s - R.lane_sum(res)
+    t64 = (b * res.astype(F64)).sum(axis=1)
+    assert np.all(np.abs(t32 - t64) <= 3 * dp * 2.0 ** -24 * np.abs(res).sum())
+    qz = R.quantize(res[None, :])
+    ip = R.ip_planes(codes, qz["planes"][0])
+    pc = R.popcount8(codes)
+    tq = qz["delta"][0] * (2 * ip - qz["sq"][0]).astype(F64) + qz["vl"][0] * (2 * pc - dp)
+    assert np.all(np.abs(tq - t64) <= dp * qz["delta"][0] / 2 + 1e-4)
+
+
+def test_lut_search_limit_is_exact_knn(tiny):
+    """With every list probed and every candidate re-ranked the FastScan
+    search is the exact kNN; with the tiny workload's settings its recall is
+    at least the 4-bit form's."""
+    x, q, ix = tiny
+    ti, td = R.exact_knn(x, q, 10)
+    ids, dist = R.search(ix, q, 32, 10, x.shape[0], estimator="lut")
+    assert np.array_equal(ids, ti)
+    a, _ = R.search(ix, q, 4, 10, 40, estimator="lut")
+    b4, _ = R.search(ix, q, 4, 10, 40)
+    assert R.recall_at(x, q, a, td, 10) >= R.recall_at(x, q, b4, td, 10) - 0.02
+
+
 def test_estimator_unbiased_over_rotations():
     # E_P[s_hat] = <u_x, u_q> for Haar P (the RaBitQ estimator property).
     rng = np.random.default_rng(10)
@@ -456,6 +526,29 @@ def test_prune_is_lossless_including_ties():
         a = R.select_candidates(d, ids, n_sel, prune=True)
         assert np.array_equal(a, R.select_candidates(d, ids, n_sel, prune=False))
         assert np.array_equal(R.key_id(a), ids[:n_sel])
+
+
+def test_first_bound_window_and_tightness():
+    """The first bound looks at max(1024, n_sel, min(16 n_sel, 32768))
+    candidates in probe order (values by hand), is the n_sel-th smallest of
+    them exactly, never falls below the n_sel-th smallest of all candidates,
+    and tightens as the window grows."""
+    assert [R.bound_window(v) for v in (1, 10, 64, 100, 2000, 2048, 4096, 40000)] == \
+        [1024, 1024, 1024, 1600, 32000, 32768, 32768, 40000]
+    rng = np.random.default_rng(21)
+    d = rng.standard_normal(50000).astype(F32)
+    d[:5000] -= np.float32(1.0)            # the nearest lists come first
+    for n_sel in (10, 100, 2000):
+        m = R.bound_window(n_sel)
+        dd = d.copy()
+        dd[m - 1] = np.float32(-100.0)     # the window's last candidate is the best one
+        tau = R.first_bound(dd, n_sel)
+        assert tau == int(np.sort(R.orderable(dd[:m]))[n_sel - 1])
+        assert tau < int(np.sort(R.orderable(dd[:m - 1]))[n_sel - 1])
+        assert tau >= int(np.sort(R.orderable(dd))[n_sel - 1])
+        looser = R.first_bound(dd, n_sel, window=max(1024, n_sel))
+        assert looser >= tau
+    assert R.first_bound(d[:5], 10) == R.U32_MAX
 
 
 def test_running_bound_form_equals_first_bound_form():
