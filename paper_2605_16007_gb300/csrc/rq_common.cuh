@@ -273,7 +273,19 @@ __device__ inline void block_narrow(const K* src, int m, int shift, int width, K
   const K dmask = ((K)1 << width) - 1;
   for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
   __syncthreads();
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+  // four keys per thread per round, their loads issued together (src may be
+  // global memory)
+  const int stride = blockDim.x;
+  int i = threadIdx.x;
+  for (; i + 3 * stride < m; i += 4 * stride) {
+    K k[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) k[j] = src[i + j * stride];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if ((k[j] & mask) == prefix) atomicAdd(&hist[(int)((k[j] >> shift) & dmask)], 1);
+  }
+  for (; i < m; i += stride) {
     const K k = src[i];
     if ((k & mask) == prefix) atomicAdd(&hist[(int)((k >> shift) & dmask)], 1);
   }
@@ -301,7 +313,13 @@ template <typename K>
 __device__ inline int block_top_diff_bit(const K* src, int m, K* red) {
   const K k0 = src[0];
   K x = 0;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) x |= src[i] ^ k0;
+  const int stride = blockDim.x;
+  int i = threadIdx.x;
+  for (; i + 3 * stride < m; i += 4 * stride) {
+    const K a = src[i], b = src[i + stride], c = src[i + 2 * stride], d = src[i + 3 * stride];
+    x |= (a ^ k0) | (b ^ k0) | (c ^ k0) | (d ^ k0);
+  }
+  for (; i < m; i += stride) x |= src[i] ^ k0;
 #pragma unroll
   for (int o = 16; o; o >>= 1) x |= __shfl_xor_sync(0xffffffffu, x, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;

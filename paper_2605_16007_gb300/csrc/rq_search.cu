@@ -789,7 +789,7 @@ __device__ __forceinline__ float exact_dist_lanes(const RawT* __restrict__ x,
 // Per-warp shared memory of the finalize kernel: selection (P keys), top-k
 // (PK keys), histogram (256 ints), bucket (32 keys), query row (dim floats).
 struct FinalizeLayout {
-  int P, PK, S, dim;  // S: candidate keys staged per query (>= 4096: 128 mask words)
+  int P, PK, S, dim;  // S: candidate keys staged per query (2048 or 4096: S/32 mask words)
   __host__ __device__ int bytes() const {
     return (P + PK + S) * 8 + 256 * 4 + 32 * 8 + ((dim * 4 + 15) & ~15);
   }
@@ -806,6 +806,28 @@ __device__ __forceinline__ uint64_t slot_to_id(uint64_t key, const uint32_t* __r
                                                int64_t n_slots, int32_t* err) {
   const uint32_t slot = (uint32_t)key;
   return (key & 0xFFFFFFFF00000000ull) | (index_ok(slot, n_slots, err) ? __ldg(ids + slot) : 0u);
+}
+
+// Copies the n keys of one survivor word to dst with their slots replaced
+// by row ids, eight at a time: the eight key loads, then the eight id loads,
+// each group in flight together.
+__device__ __forceinline__ void copy_word_keys(const uint64_t* __restrict__ kw, int n,
+                                               uint64_t* dst, const uint32_t* __restrict__ ids,
+                                               int64_t n_slots, int32_t* err) {
+  for (int b0 = 0; b0 < n; b0 += 8) {
+    uint64_t kv[8];
+    uint32_t iv[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) kv[j] = (b0 + j < n) ? kw[b0 + j] : 0ull;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint32_t slot = (uint32_t)kv[j];
+      iv[j] = (b0 + j < n && index_ok(slot, n_slots, err)) ? __ldg(ids + slot) : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (b0 + j < n) dst[b0 + j] = (kv[j] & 0xFFFFFFFF00000000ull) | iv[j];
+  }
 }
 
 template <typename RawT>
@@ -872,27 +894,24 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
 #pragma unroll
       for (int r = 0; r < kRegWords; ++r) {
         const int n = __popc(mw[r]);
-        const uint64_t* kw = krow + (int64_t)(tid + 128 * r) * 32;
-#pragma unroll 4
-        for (int b = 0; b < n; ++b) s_stage[pos + b] = slot_to_id(kw[b], ids, n_slots, err);
+        copy_word_keys(krow + (int64_t)(tid + 128 * r) * 32, n, s_stage + pos, ids, n_slots, err);
         pos += n;
       }
     } else {
       for (int i = tid; i < T; i += blockDim.x) {
         const int n = __popc(mrow[i]);
-        const uint64_t* kw = krow + (int64_t)i * 32;
-#pragma unroll 4
-        for (int b = 0; b < n; ++b) s_stage[pos + b] = slot_to_id(kw[b], ids, n_slots, err);
+        copy_word_keys(krow + (int64_t)i * 32, n, s_stage + pos, ids, n_slots, err);
         pos += n;
       }
     }
   } else {
-    // Many: compact the keys to the front of the query's key slots, 128 mask
-    // words (at most 4096 keys <= S) at a time through shared memory. The
-    // keys written never reach the slots of words not yet staged.
+    // Many: compact the keys to the front of the query's key slots, S / 32
+    // mask words (at most S keys) at a time through shared memory. The keys
+    // written never reach the slots of words not yet staged.
+    const int wpi = lay.S / 32;  // words per pass: 64 or 128
     int64_t run = 0;
-    for (int c0 = 0; c0 < T; c0 += 128) {
-      const uint32_t w = (c0 + tid < T) ? mrow[c0 + tid] : 0u;
+    for (int c0 = 0; c0 < T; c0 += wpi) {
+      const uint32_t w = (tid < wpi && c0 + tid < T) ? mrow[c0 + tid] : 0u;
       const int pc = __popc(w);
       int ps = pc;
 #pragma unroll
@@ -906,8 +925,7 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
       if (pc) {
         int at = ps - pc;
         for (int w2 = 0; w2 < warp; ++w2) at += s_scan[w2];
-        const uint64_t* kw = krow + (int64_t)(c0 + tid) * 32;
-        for (int b = 0; b < pc; ++b) s_stage[at + b] = slot_to_id(kw[b], ids, n_slots, err);
+        copy_word_keys(krow + (int64_t)(c0 + tid) * 32, pc, s_stage + at, ids, n_slots, err);
       }
       __syncthreads();
       for (int i = tid; i < tot; i += blockDim.x) krow[run + i] = s_stage[i];
@@ -1581,8 +1599,10 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
   // 5-6. candidate selection and exact re-rank
   tm.mark(RQ_STAGE_SELECT, st);
   {
-    const FinalizeLayout lay{next_pow2_host(sh.nsel_max), next_pow2_host(sh.k_stride), 4096,
-                             ix->dim};
+    // candidates staged in shared memory: more for large selections (whose
+    // first bound lets more survive), fewer to keep more blocks per SM
+    const FinalizeLayout lay{next_pow2_host(sh.nsel_max), next_pow2_host(sh.k_stride),
+                             sh.nsel_max > 512 ? 4096 : 2048, ix->dim};
     const size_t smem = lay.bytes();
     RQ_TRY(allow_dynamic_smem((const void*)finalize_kernel<uint8_t>, 200 * 1024));
     RQ_TRY(allow_dynamic_smem((const void*)finalize_kernel<float>, 200 * 1024));
