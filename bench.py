@@ -128,7 +128,7 @@ def parse(argv=None):
                     help="(internal) the oracle's CPU leg, run in its own CUDA-free process")
     ap.add_argument("--profile", default=None,
                     help="only build the skewed index and run --warmup + --steps searches of "
-                         "one case (nq,nprobe,mode[,chunk]), for ncu captures")
+                         "one case (nq,nprobe,mode[,chunk[,n_rerank]]), for ncu captures")
     return ap.parse_args(argv)
 
 
@@ -919,7 +919,8 @@ def run_reference(args):
 # ---------------------------------------------------------------- profile
 def run_profile(args):
     """Build the skewed index, then --warmup + --steps searches of one case
-    (nq, uniform nprobe, scan mode[, plain chunk]) and nothing else."""
+    (nq, uniform nprobe, scan mode[, plain chunk[, n_rerank]]) and nothing
+    else."""
     import torch
 
     import paper_2605_16007_gb300 as rq
@@ -934,6 +935,7 @@ def run_profile(args):
     parts = [int(v) for v in args.profile.split(",")]
     nq, nprobe, mode = parts[:3]
     chunk = parts[3] if len(parts) > 3 else 0
+    n_rerank = parts[4] if len(parts) > 4 else 1000
     q = torch.from_numpy(wl["mix"].queries(nq)).to(dev)
     ids = torch.empty((nq, 10), dtype=torch.int64, device=dev)
     dist = torch.empty((nq, 10), dtype=torch.float32, device=dev)
@@ -942,10 +944,10 @@ def run_profile(args):
     for i in range(args.warmup + args.steps):
         flush.zero_()
         st = {}
-        ix.search(q, nprobe, 10, 1000, out_ids=ids, out_dist=dist, scan_mode=mode,
+        ix.search(q, nprobe, 10, n_rerank, out_ids=ids, out_dist=dist, scan_mode=mode,
                   plain_chunk=chunk, stage_times=st)
-        out.append(st["scan"])
-    print(json.dumps({"profile": args.profile, "scan_ms": out[args.warmup:],
+        out.append(st)
+    print(json.dumps({"profile": args.profile, "stage_ms": out[args.warmup:],
                       "device_error": ix.device_error()}), flush=True)
 
 

@@ -786,52 +786,45 @@ __device__ __forceinline__ float exact_dist_lanes(const RawT* __restrict__ x,
 // block of several warps serves several queries at once.
 // ---------------------------------------------------------------------------
 
-// Per-warp shared memory of the finalize kernel: selection (P keys), top-k
-// (PK keys), histogram (256 ints), bucket (32 keys), query row (dim floats).
+// Shared memory of the finalize kernel: selection (P keys, at least
+// kFinDescKeys: it holds the word descriptors while the candidates are
+// collected), top-k (PK keys), histogram (256 ints), bucket (32 keys),
+// staging (S keys), query row (dim floats).
+constexpr int kFinThreads = 256;
+constexpr int kFinWordsPerThread = 16;                            // four 16-byte mask loads
+constexpr int kFinRoundWords = kFinThreads * kFinWordsPerThread;  // mask words per round
+constexpr int kFinDescKeys = kFinRoundWords / 2;                  // 4-byte descriptors, in keys
+
 struct FinalizeLayout {
-  int P, PK, S, dim;  // S: candidate keys staged per query (2048 or 4096: S/32 mask words)
+  int P, PK, S, dim;  // S: candidate keys staged per query
+  __host__ __device__ int sel_keys() const { return P > kFinDescKeys ? P : kFinDescKeys; }
   __host__ __device__ int bytes() const {
-    return (P + PK + S) * 8 + 256 * 4 + 32 * 8 + ((dim * 4 + 15) & ~15);
+    return (sel_keys() + PK + S) * 8 + 256 * 4 + 32 * 8 + ((dim * 4 + 15) & ~15);
   }
 };
 
-// Four warps per query: the candidates are collected from the scan's
-// survivor masks into shared memory (or compacted in place when there are
-// more than S), warp 0 selects (radix passes), all 128 threads gather and
-// re-rank, warp 0 selects the final k.
+// One block of kFinThreads per query. The candidates are collected from the
+// scan's survivor masks into shared memory (moved to the front of the
+// query's key slots when there are more than S), then selected (radix
+// passes), gathered and re-ranked, and the final k selected.
 // Survivor keys leave the scans as (estimate, slot); the row id of the slot
 // replaces it as the candidates are collected, so that every selection ranks
 // by (estimate, row id).
-__device__ __forceinline__ uint64_t slot_to_id(uint64_t key, const uint32_t* __restrict__ ids,
-                                               int64_t n_slots, int32_t* err) {
-  const uint32_t slot = (uint32_t)key;
-  return (key & 0xFFFFFFFF00000000ull) | (index_ok(slot, n_slots, err) ? __ldg(ids + slot) : 0u);
-}
-
-// Copies the n keys of one survivor word to dst with their slots replaced
-// by row ids, eight at a time: the eight key loads, then the eight id loads,
-// each group in flight together.
-__device__ __forceinline__ void copy_word_keys(const uint64_t* __restrict__ kw, int n,
-                                               uint64_t* dst, const uint32_t* __restrict__ ids,
-                                               int64_t n_slots, int32_t* err) {
-  for (int b0 = 0; b0 < n; b0 += 8) {
-    uint64_t kv[8];
-    uint32_t iv[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) kv[j] = (b0 + j < n) ? kw[b0 + j] : 0ull;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const uint32_t slot = (uint32_t)kv[j];
-      iv[j] = (b0 + j < n && index_ok(slot, n_slots, err)) ? __ldg(ids + slot) : 0u;
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-      if (b0 + j < n) dst[b0 + j] = (kv[j] & 0xFFFFFFFF00000000ull) | iv[j];
-  }
-}
-
+//
+// Collection goes in rounds of kFinRoundWords mask words; thread t holds
+// kFinWordsPerThread consecutive words of the round (four 16-byte loads, all
+// in flight together). A block scan of the per-thread key counts gives every
+// key its position in word order. Each nonzero word leaves one descriptor
+// (position of its first key, word) in shared memory. Then thread t copies
+// the keys at positions t, t + kFinThreads, ... (found by binary search over
+// the descriptors), eight key loads and then eight id loads in flight.
+// When the staging area fills, it is written to the query's key slots at
+// the running position. A key's position never exceeds its slot (a word has
+// at most 32 keys, packed at the front of its 32 slots), and every key read
+// before a write has a smaller position than every key not yet read, so the
+// writes never reach a key that is still to be read.
 template <typename RawT>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kFinThreads)
 finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ wtotal,
                 int64_t mwords, uint64_t* __restrict__ cand, const uint32_t* __restrict__ ids,
                 int64_t n_slots, int32_t* err, int32_t* __restrict__ counts,
@@ -839,111 +832,138 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
                 const int32_t* __restrict__ rerank_on, int nsel_max, uint64_t* __restrict__ sel,
                 const RawT* __restrict__ raw, const float* __restrict__ q, int dim, int k_stride,
                 FinalizeLayout lay, int64_t* __restrict__ out_ids, float* __restrict__ out_d) {
+  constexpr int NWARP = kFinThreads / 32;
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ int s_ctl[8];
-  __shared__ int s_part[4];
-  __shared__ int s_scan[4];
+  __shared__ int s_warp[NWARP];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t row = blockIdx.x;
   uint64_t* s_sel = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* s_top = s_sel + lay.P;
+  uint32_t* s_desc = reinterpret_cast<uint32_t*>(smem);  // during collection only
+  uint64_t* s_top = s_sel + lay.sel_keys();
   int* hist = reinterpret_cast<int*>(s_top + lay.PK);
   uint64_t* small = reinterpret_cast<uint64_t*>(hist + 256);
   uint64_t* s_stage = small + 32;
   float* s_q = reinterpret_cast<float*>(s_stage + lay.S);
-  const uint32_t* mrow = mask + row * mwords;
+  // mwords is a multiple of 4 and the mask 16-byte aligned
+  const uint4* mrow4 = reinterpret_cast<const uint4*>(mask + row * mwords);
   uint64_t* krow = cand + row * mwords * 32;
   const int T = wtotal[row];
-  // Thread t takes mask words t, t + 128, ...: up to kRegWords of them are
-  // kept in registers; a block scan of their popcounts gives each thread its
-  // first staging position.
-  constexpr int kRegWords = 8;
-  const bool in_regs = T <= kRegWords * 128;
-  uint32_t mw[kRegWords];
-  int c = 0;
-  if (in_regs) {
+  for (int d = tid; d < dim; d += kFinThreads) s_q[d] = q[row * dim + d];
+  int staged = 0;       // keys in s_stage (the same in every thread)
+  int64_t flushed = 0;  // keys already moved to krow[0, flushed)
+  for (int c0 = 0; c0 < T; c0 += kFinRoundWords) {
+    const int wfirst = c0 + tid * kFinWordsPerThread;
+    uint32_t w[kFinWordsPerThread];
 #pragma unroll
-    for (int r = 0; r < kRegWords; ++r) {
-      const int i = tid + 128 * r;
-      mw[r] = i < T ? mrow[i] : 0u;
-      c += __popc(mw[r]);
+    for (int j = 0; j < kFinWordsPerThread / 4; ++j) {
+      const uint4 v = (wfirst + 4 * j < T) ? mrow4[(wfirst >> 2) + j] : make_uint4(0, 0, 0, 0);
+      w[4 * j] = v.x;
+      w[4 * j + 1] = v.y;
+      w[4 * j + 2] = v.z;
+      w[4 * j + 3] = v.w;
     }
-  } else {
-    for (int i = tid; i < T; i += blockDim.x) c += __popc(mrow[i]);
-  }
-  int incl = c;
+    int c = 0, nz = 0;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
+    for (int e = 0; e < kFinWordsPerThread; ++e) {
+      if (wfirst + e >= T) w[e] = 0u;  // words past the query's last probed list
+      const int n = __popc(w[e]);
+      c += n;
+      nz += n != 0;
+    }
+    // one scan of both counts: keys (< 2^18 per round) in the low 18 bits,
+    // nonzero words (<= kFinRoundWords) above
+    const int v = c | (nz << 18);
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    int ex = incl - v, tot = 0;
+#pragma unroll
+    for (int i = 0; i < NWARP; ++i) {
+      const int s = s_warp[i];
+      if (i < warp) ex += s;
+      tot += s;
+    }
+    const int tot_keys = tot & 0x3FFFF, tot_desc = tot >> 18;
+    {
+      int p = ex & 0x3FFFF, d = ex >> 18;
+#pragma unroll
+      for (int e = 0; e < kFinWordsPerThread; ++e) {
+        const int n = __popc(w[e]);
+        if (n) s_desc[d++] = ((uint32_t)p << 12) | (uint32_t)(tid * kFinWordsPerThread + e);
+        p += n;
+      }
+    }
+    __syncthreads();
+    for (int w0 = 0; w0 < tot_keys;) {
+      if (staged == lay.S) {
+        for (int i = tid; i < staged; i += kFinThreads) krow[flushed + i] = s_stage[i];
+        flushed += staged;
+        staged = 0;
+        __syncthreads();
+      }
+      const int wn = min(lay.S - staged, tot_keys - w0);
+      for (int jb = w0 + tid; jb < w0 + wn; jb += 8 * kFinThreads) {
+        int64_t src[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int j = jb + u * kFinThreads;
+          src[u] = -1;
+          if (j < w0 + wn) {
+            int lo = 0, hi = tot_desc - 1;  // last descriptor whose first key is <= j
+            while (lo < hi) {
+              const int mid = (lo + hi + 1) >> 1;
+              if ((int)(s_desc[mid] >> 12) <= j) lo = mid; else hi = mid - 1;
+            }
+            const uint32_t dsc = s_desc[lo];
+            src[u] = (int64_t)(c0 + (int)(dsc & 4095u)) * 32 + (j - (int)(dsc >> 12));
+          }
+        }
+        uint64_t kv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) kv[u] = src[u] >= 0 ? krow[src[u]] : 0ull;
+        uint32_t iv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const uint32_t slot = (uint32_t)kv[u];
+          iv[u] = (src[u] >= 0 && index_ok(slot, n_slots, err)) ? __ldg(ids + slot) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (src[u] >= 0)
+            s_stage[staged + (jb + u * kFinThreads - w0)] = (kv[u] & 0xFFFFFFFF00000000ull) | iv[u];
+      }
+      __syncthreads();
+      staged += wn;
+      w0 += wn;
+    }
   }
-  if (lane == 31) s_part[warp] = incl;
-  for (int d = tid; d < dim; d += blockDim.x) s_q[d] = q[row * dim + d];
-  __syncthreads();
-  int pos = incl - c;
-  for (int w = 0; w < warp; ++w) pos += s_part[w];
-  const int count = s_part[0] + s_part[1] + s_part[2] + s_part[3];
+  const int64_t count64 = flushed + staged;
+  const int count = (int)count64;
   if (tid == 0) counts[row] = count;
-  const int n_sel = nsel[row];
-  const int k = kq[row];
-  const bool rerank = rerank_on[row] != 0;
   const uint64_t* src = s_stage;
-  if (count <= lay.S) {
-    // The keys of a word are packed at the front of its 32 slots.
-    if (in_regs) {
-#pragma unroll
-      for (int r = 0; r < kRegWords; ++r) {
-        const int n = __popc(mw[r]);
-        copy_word_keys(krow + (int64_t)(tid + 128 * r) * 32, n, s_stage + pos, ids, n_slots, err);
-        pos += n;
-      }
-    } else {
-      for (int i = tid; i < T; i += blockDim.x) {
-        const int n = __popc(mrow[i]);
-        copy_word_keys(krow + (int64_t)i * 32, n, s_stage + pos, ids, n_slots, err);
-        pos += n;
-      }
-    }
-  } else {
-    // Many: compact the keys to the front of the query's key slots, S / 32
-    // mask words (at most S keys) at a time through shared memory. The keys
-    // written never reach the slots of words not yet staged.
-    const int wpi = lay.S / 32;  // words per pass: 64 or 128
-    int64_t run = 0;
-    for (int c0 = 0; c0 < T; c0 += wpi) {
-      const uint32_t w = (tid < wpi && c0 + tid < T) ? mrow[c0 + tid] : 0u;
-      const int pc = __popc(w);
-      int ps = pc;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, ps, o);
-        if (lane >= o) ps += t;
-      }
-      if (lane == 31) s_scan[warp] = ps;
-      __syncthreads();
-      const int tot = s_scan[0] + s_scan[1] + s_scan[2] + s_scan[3];
-      if (pc) {
-        int at = ps - pc;
-        for (int w2 = 0; w2 < warp; ++w2) at += s_scan[w2];
-        copy_word_keys(krow + (int64_t)(c0 + tid) * 32, pc, s_stage + at, ids, n_slots, err);
-      }
-      __syncthreads();
-      for (int i = tid; i < tot; i += blockDim.x) krow[run + i] = s_stage[i];
-      __syncthreads();
-      run += tot;
-    }
+  if (flushed > 0) {
+    for (int i = tid; i < staged; i += kFinThreads) krow[flushed + i] = s_stage[i];
     src = krow;
   }
   __syncthreads();
+  const int n_sel = nsel[row];
+  const int k = kq[row];
+  const bool rerank = rerank_on[row] != 0;
   // Without re-rank the selection is the answer and is sorted; with re-rank
   // only the set matters and the exact keys are selected below.
   const int got = block_select_smallest(src, count, n_sel, s_sel, hist, small, s_ctl, !rerank);
-  for (int j = tid; j < nsel_max; j += blockDim.x) sel[row * nsel_max + j] = (j < got) ? s_sel[j] : kU64Max;
+  for (int j = tid; j < nsel_max; j += kFinThreads) sel[row * nsel_max + j] = (j < got) ? s_sel[j] : kU64Max;
   const float inf = __int_as_float(0x7f800000);
   const uint64_t* res = s_sel;
   int kk = min(k, got);
   if (rerank) {
-    for (int i = tid; i < got; i += blockDim.x) {
+    for (int i = tid; i < got; i += kFinThreads) {
       const uint32_t id = (uint32_t)s_sel[i];
       const float dist = exact_dist_lanes<RawT>(raw + (int64_t)id * dim, s_q, dim);
       s_sel[i] = make_key(dist, id);
@@ -952,7 +972,7 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
     kk = block_select_smallest(s_sel, got, k, s_top, hist, small, s_ctl, true);
     res = s_top;
   }
-  for (int j = tid; j < k_stride; j += blockDim.x) {
+  for (int j = tid; j < k_stride; j += kFinThreads) {
     const uint64_t key = (j < kk) ? res[j] : kU64Max;
     out_ids[row * k_stride + j] = (key == kU64Max) ? -1 : (int64_t)(uint32_t)key;
     out_d[row * k_stride + j] = (key == kU64Max) ? inf : from_orderable((uint32_t)(key >> 32));
@@ -1348,7 +1368,8 @@ constexpr size_t kWorkspaceBudget = size_t(8) << 30;
 void layout_workspace(const rq_index* ix, const SearchShape& sh, Workspace& ws) {
   const int64_t nq = sh.nq, np = sh.npmax;
   const int W = ix->dp / 32;
-  ws.mwords = std::max<int64_t>(1, ix->top_words_prefix[std::min(np, (int64_t)ix->nlist)]);
+  // a multiple of 4: the finalize kernel reads the mask rows 16 bytes at a time
+  ws.mwords = (std::max<int64_t>(1, ix->top_words_prefix[std::min(np, (int64_t)ix->nlist)]) + 3) & ~int64_t(3);
   ws.cap = 32 * ws.mwords;
   Layout L;
   L.take(&ws.q, nq * ix->dim);
@@ -1602,17 +1623,17 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
     // candidates staged in shared memory: more for large selections (whose
     // first bound lets more survive), fewer to keep more blocks per SM
     const FinalizeLayout lay{next_pow2_host(sh.nsel_max), next_pow2_host(sh.k_stride),
-                             sh.nsel_max > 512 ? 4096 : 2048, ix->dim};
+                             sh.nsel_max > 512 ? 8192 : 4096, ix->dim};
     const size_t smem = lay.bytes();
     RQ_TRY(allow_dynamic_smem((const void*)finalize_kernel<uint8_t>, 200 * 1024));
     RQ_TRY(allow_dynamic_smem((const void*)finalize_kernel<float>, 200 * 1024));
     if (ix->raw_dtype == RQ_U8)
-      finalize_kernel<uint8_t><<<(unsigned)nq, 128, smem, st>>>(
+      finalize_kernel<uint8_t><<<(unsigned)nq, kFinThreads, smem, st>>>(
           ws.mask, ws.wtotal, ws.mwords, ws.cand, ix->ids, ix->n, ix->d_err, ws.counts, ws.nsel, ws.kq, ws.rerank_on,
           sh.nsel_max, ws.sel, static_cast<const uint8_t*>(ix->raw), ws.q, ix->dim, sh.k_stride, lay,
           ws.out_ids, ws.out_d);
     else
-      finalize_kernel<float><<<(unsigned)nq, 128, smem, st>>>(
+      finalize_kernel<float><<<(unsigned)nq, kFinThreads, smem, st>>>(
           ws.mask, ws.wtotal, ws.mwords, ws.cand, ix->ids, ix->n, ix->d_err, ws.counts, ws.nsel, ws.kq, ws.rerank_on,
           sh.nsel_max, ws.sel, static_cast<const float*>(ix->raw), ws.q, ix->dim, sh.k_stride, lay,
           ws.out_ids, ws.out_d);
