@@ -105,7 +105,6 @@ struct Workspace {
   int32_t* wtotal = nullptr;    // nq: mask words of the query's probes
   uint64_t* cand = nullptr;     // nq x cap, cap = 32 mwords
   uint64_t* sel = nullptr;      // nq x nsel_max
-  uint32_t* bkeys = nullptr;    // nq x bound_window(nsel_max): first-bound estimates
   int32_t* nprobe = nullptr;    // nq
   int32_t* kq = nullptr;        // nq
   int32_t* nsel = nullptr;      // nq

@@ -152,24 +152,16 @@ select_rows_kernel(const uint64_t* __restrict__ keys, int64_t row_stride,
 // (dimension d -> word d/32, bit d%32).
 // ---------------------------------------------------------------------------
 template <int NW4>
-__device__ __forceinline__ void quantize_pair(int64_t pair, int64_t q, int c, int lane,
-                                              const float* __restrict__ qrot, int64_t nq,
-                                              const float* __restrict__ cR, int dp,
+__device__ __forceinline__ void quantize_pair(int64_t pair, int64_t q, int c, int slot, int lane,
+                                              const float (&qv)[4 * NW4],
+                                              const float (&cv)[4 * NW4], int64_t nq, int dp,
                                               float4* __restrict__ qparams,
                                               uint32_t* __restrict__ planes,
-                                              int32_t* __restrict__ list_count,
                                               int32_t* __restrict__ list_pairs,
                                               uint8_t* __restrict__ qdb,
                                               float4* __restrict__ qpb,
                                               uint8_t* __restrict__ qrec, uint64_t* slot_out) {
   constexpr int PER = 4 * NW4;  // values per lane (dp / 32)
-  // Grouped scans: the pair takes the next slot of its list's bucket (room
-  // for every query of the batch).
-  int slot = 0;
-  if (list_count) {
-    if (lane == 0) slot = atomicAdd(&list_count[c], 1);
-    slot = __shfl_sync(0xffffffffu, slot, 0);
-  }
   // Streaming scan: the pair's record in its list's bucket (planes, then
   // {vl, delta, nq2, Sq}; query, mask word and bound are added once the
   // bound is known).
@@ -180,8 +172,7 @@ __device__ __forceinline__ void quantize_pair(int64_t pair, int64_t q, int c, in
   float vl = __int_as_float(0x7f800000), vr = -vl, acc = 0.0f;
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
-    const int d = lane + 32 * i;
-    r[i] = __fsub_rn(qrot[q * dp + d], cR[(int64_t)c * dp + d]);
+    r[i] = __fsub_rn(qv[i], cv[i]);
     vl = fminf(vl, r[i]);
     vr = fmaxf(vr, r[i]);
     acc = __fadd_rn(acc, __fmul_rn(r[i], r[i]));
@@ -437,6 +428,102 @@ scan_lut_kernel(const int32_t* __restrict__ nchunks, const int32_t* __restrict__
 
 // The FastScan quantities of one pair (a warp): nq2 = ||r||^2 and S = sum_d
 // r_d, both in the 32-lane order, stored as {0, 0, nq2, S}.
+// ---------------------------------------------------------------------------
+// The first bound's n-th smallest estimate, kept in shared memory while the
+// estimates stream in (Section 3.3.3). The block offers keys in rounds; a
+// key below the threshold `thr` goes to the buffer, a key equal to it is
+// only counted (eqc), a larger one is dropped. When the buffer could
+// overflow in the next round, thr becomes the buffer's n-th smallest key and
+// only the keys below it stay. Every dropped key is larger than a threshold
+// with at least n keys at or below it, so the n-th smallest of everything
+// offered is the n-th smallest of (buffer, eqc copies of thr). The result
+// does not depend on the order of the keys.
+// ---------------------------------------------------------------------------
+struct KthState {
+  int nbuf;      // keys in the buffer (all below thr)
+  int eqc;       // keys equal to thr seen since thr was set
+  uint32_t thr;  // all ones until the first compaction
+  int cnt;       // compaction scratch
+  int eq2;
+};
+
+__device__ __forceinline__ void kth_init(KthState* ks) {
+  if (threadIdx.x == 0) {
+    ks->nbuf = 0;
+    ks->eqc = 0;
+    ks->thr = kU32Max;
+  }
+}
+
+// One key per thread (valid false: none). Every thread of the block calls
+// it with the same thr (read after the round's barrier).
+__device__ __forceinline__ void kth_offer(KthState* ks, uint32_t* buf, uint32_t thr, uint32_t key,
+                                          bool valid) {
+  const int lane = threadIdx.x & 31;
+  const bool keep = valid && key < thr;
+  const uint32_t mk = __ballot_sync(0xffffffffu, keep);
+  const uint32_t me = __ballot_sync(0xffffffffu, valid && key == thr);
+  int base = 0;
+  if (lane == 0) {
+    if (mk) base = atomicAdd(&ks->nbuf, __popc(mk));
+    if (me) atomicAdd(&ks->eqc, __popc(me));
+  }
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (keep) buf[base + __popc(mk & ((1u << lane) - 1u))] = key;
+}
+
+// Called by the whole block after a round's barrier: compacts when fewer
+// than `room` slots are left (cap >= n + 2 room).
+__device__ inline void kth_maybe_compact(KthState* ks, uint32_t* buf, int cap, int room, int n,
+                                         int* hist, uint64_t* small, int* ctl) {
+  const int nb = ks->nbuf;
+  if (nb <= cap - room) return;
+  const uint32_t t2 = block_kth_u32(buf, nb, n, hist, small, ctl);  // nb > n: a key below thr
+  if (threadIdx.x == 0) {
+    ks->cnt = 0;
+    ks->eq2 = 0;
+  }
+  __syncthreads();
+  // keep the keys below t2, in rounds whose reads all come before their
+  // writes (a kept key's new position is below every unread position)
+  for (int r0 = 0; r0 < nb; r0 += blockDim.x * 8) {
+    uint32_t v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = r0 + threadIdx.x + blockDim.x * u;
+      v[u] = i < nb ? buf[i] : kU32Max;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = r0 + threadIdx.x + blockDim.x * u;
+      if (i < nb) {
+        if (v[u] < t2) buf[atomicAdd(&ks->cnt, 1)] = v[u];
+        else if (v[u] == t2) atomicAdd(&ks->eq2, 1);
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    ks->nbuf = ks->cnt;
+    ks->eqc = ks->eq2;
+    ks->thr = t2;
+  }
+  __syncthreads();
+}
+
+// The n-th smallest of all keys offered, `total` of them (all ones when
+// total < n).
+__device__ inline uint32_t kth_result(KthState* ks, uint32_t* buf, int total, int n, int* hist,
+                                      uint64_t* small, int* ctl) {
+  __syncthreads();
+  if (total < n) return kU32Max;
+  const int nb = ks->nbuf;
+  const uint32_t thr = ks->thr;
+  if (nb >= n) return block_kth_u32(buf, nb, n, hist, small, ctl);
+  return thr;  // nb < n <= nb + eqc
+}
+
 template <int NW4>
 __device__ __forceinline__ void lut_pair(int64_t pair, int64_t q, int c, int lane,
                                          const float* __restrict__ qrot,
@@ -458,7 +545,7 @@ __device__ __forceinline__ void lut_pair(int64_t pair, int64_t q, int c, int lan
 // First bound with the FastScan estimator (the same candidates and rank as
 // bound_block): per probe the block builds the pair's tables in `lut`
 // (D_p/8 x 256 floats, then D_p residual floats) and estimates the list's
-// first vectors.
+// first vectors. `buf` is shared memory for `cap` keys.
 template <int NW4>
 __device__ inline uint32_t bound_block_lut(int64_t qi, int npmax, int npq, int n_sel,
                                            const uint64_t* lists,
@@ -468,11 +555,13 @@ __device__ inline uint32_t bound_block_lut(int64_t qi, int npmax, int npq, int n
                                            const int64_t* __restrict__ offsets,
                                            const uint8_t* __restrict__ codes,
                                            const float2* __restrict__ fac, int dp,
-                                           uint32_t* s_bkeys, float* lut, int* hist,
+                                           uint32_t* buf, int cap, float* lut, int* hist,
                                            uint64_t* small, int* ctl) {
+  __shared__ KthState ks;
   const int tid = threadIdx.x;
   const int cap1 = bound_window(n_sel);
   float* r = lut + 32 * dp;
+  kth_init(&ks);
   int taken = 0;
   for (int p = 0; p < npq && taken < cap1; ++p) {
     const int64_t pair = qi * npmax + p;
@@ -484,17 +573,23 @@ __device__ inline uint32_t bound_block_lut(int64_t qi, int npmax, int npq, int n
     __syncthreads();
     build_lut(r, lut, dp / 8);
     const float4 qp = qparams[pair];
-    for (int i = tid; i < m; i += blockDim.x) {
-      uint4 code[NW4];
-      const uint4* cp = reinterpret_cast<const uint4*>(codes + (lo + i) * (dp / 8));
+    for (int base = 0; base < m; base += blockDim.x) {
+      const int i = base + tid;
+      uint32_t key = 0;
+      if (i < m) {
+        uint4 code[NW4];
+        const uint4* cp = reinterpret_cast<const uint4*>(codes + (lo + i) * (dp / 8));
 #pragma unroll
-      for (int w = 0; w < NW4; ++w) code[w] = __ldg(cp + w);
-      s_bkeys[taken + i] = orderable(estimate_lut_regs<NW4>(code, lut, __ldg(fac + lo + i), qp.z, qp.w));
+        for (int w = 0; w < NW4; ++w) code[w] = __ldg(cp + w);
+        key = orderable(estimate_lut_regs<NW4>(code, lut, __ldg(fac + lo + i), qp.z, qp.w));
+      }
+      kth_offer(&ks, buf, ks.thr, key, i < m);
+      __syncthreads();
+      kth_maybe_compact(&ks, buf, cap, blockDim.x, n_sel, hist, small, ctl);
     }
     taken += m;
   }
-  __syncthreads();
-  return taken >= n_sel ? block_kth_u32(s_bkeys, taken, n_sel, hist, small, ctl) : kU32Max;
+  return kth_result(&ks, buf, taken, n_sel, hist, small, ctl);
 }
 
 // ---------------------------------------------------------------------------
@@ -1163,24 +1258,26 @@ __device__ inline void probe_outputs(const uint64_t* dst, int got, int np, int64
 }
 
 // First bound (Section 3.3.3): lists in probe order give the first
-// max(1024, n_sel) candidates, estimated by all 128 threads (each thread's
-// codes loaded before its estimates); the block takes the n_sel-th smallest
-// orderable estimate (all ones when the query has fewer candidates). `lists`
-// holds the query's probed list ids (npq of them), `s_bkeys` room for
-// max(1024, n_sel) values.
+// bound_window(n_sel) candidates, estimated by all 128 threads (each
+// thread's codes loaded before its estimates) and offered to the streaming
+// n-th smallest in `buf` (shared memory for `cap` keys); the bound is the
+// n_sel-th smallest orderable estimate (all ones when the query has fewer
+// candidates). `lists` holds the query's probed list ids (npq of them).
 template <int NW4>
 __device__ inline uint32_t bound_block(int64_t qi, int npmax, int npq, int n_sel,
                                        const uint64_t* lists, const float4* __restrict__ qparams,
                                        const uint32_t* __restrict__ planes,
                                        const int64_t* __restrict__ offsets,
                                        const uint8_t* __restrict__ codes,
-                                       const float2* __restrict__ fac, int dp, uint32_t* s_bkeys,
-                                       int* hist, uint64_t* small, int* ctl) {
+                                       const float2* __restrict__ fac, int dp, uint32_t* buf,
+                                       int cap, int* hist, uint64_t* small, int* ctl) {
   constexpr int W = 4 * NW4;
   constexpr int RB = NW4 >= 4 ? 1 : 4 / NW4;  // codes in flight per thread
   __shared__ __align__(16) uint32_t s_pl[4 * W];
+  __shared__ KthState ks;
   const int tid = threadIdx.x;
   const int cap1 = bound_window(n_sel);
+  kth_init(&ks);
   int taken = 0;
   for (int p = 0; p < npq && taken < cap1; ++p) {
     const int64_t pair = qi * npmax + p;
@@ -1204,23 +1301,27 @@ __device__ inline uint32_t bound_block(int64_t qi, int npmax, int npq, int n_sel
           fv[r] = __ldg(fac + lo + i);
         }
       }
+      const uint32_t thr = ks.thr;
 #pragma unroll
       for (int r = 0; r < RB; ++r) {
         const int i = base + tid + 128 * r;
+        uint32_t key = 0;
         if (i < m) {
           int pc = 0;
 #pragma unroll
           for (int w = 0; w < NW4; ++w)
             pc += __popc(code[r][w].x) + __popc(code[r][w].y) + __popc(code[r][w].z) +
                   __popc(code[r][w].w);
-          s_bkeys[taken + i] = orderable(estimate_regs<NW4>(code[r], pc, fv[r], s_pl, qp, dp));
+          key = orderable(estimate_regs<NW4>(code[r], pc, fv[r], s_pl, qp, dp));
         }
+        kth_offer(&ks, buf, thr, key, i < m);
       }
+      __syncthreads();
+      kth_maybe_compact(&ks, buf, cap, 128 * RB, n_sel, hist, small, ctl);
     }
     taken += m;
   }
-  __syncthreads();
-  return taken >= n_sel ? block_kth_u32(s_bkeys, taken, n_sel, hist, small, ctl) : kU32Max;
+  return kth_result(&ks, buf, taken, n_sel, hist, small, ctl);
 }
 
 // Query preparation, one block of 128 threads per query: probe selection,
@@ -1258,8 +1359,7 @@ struct PrepArgs {
   int32_t* nchunks;   // plain scan: `chunk`-vector chunks of each probe (null otherwise)
   int chunk;
   int lut;            // 1: FastScan estimator (residual sums; tables for the bound)
-  uint32_t* bkeys;    // per query: the first bound's candidate estimates (global scratch)
-  int64_t bkeys_stride;
+  int bound_cap;      // keys the shared region holds for the first bound
   int lut_offset;     // byte offset of the table region in dynamic shared memory
   int32_t* err;
 };
@@ -1302,14 +1402,41 @@ __global__ void __launch_bounds__(128, NW4 >= 4 ? 4 : 8) prep_kernel(PrepArgs a)
   // pair's bucket slot in the high word, which held the distance: every
   // reader of the distances above is done after this barrier)
   __syncthreads();
-  for (int p = warp; p < npq; p += 4) {
-    if (a.lut)
+  if (a.lut) {
+    for (int p = warp; p < npq; p += 4)
       lut_pair<NW4>(row * a.npmax + p, row, (int)(uint32_t)dst[p], lane, a.qrot, a.cR, a.dp,
                     a.qparams);
-    else
-      quantize_pair<NW4>(row * a.npmax + p, row, (int)(uint32_t)dst[p], lane, a.qrot, a.nq,
-                         a.cR, a.dp, a.qparams, a.planes, a.list_count, a.list_pairs, a.qdb,
-                         a.qpb, a.qrec, &dst[p]);
+  } else {
+    // A warp per probe. The query's values are loaded once; the next
+    // probe's centroid row and (grouped scans) bucket slot are requested
+    // before the current probe is quantised. Grouped scans: a pair takes
+    // the next slot of its list's bucket (room for every query of the batch).
+    constexpr int PER = 4 * NW4;
+    float qv[PER], cv[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) qv[i] = a.qrot[row * a.dp + lane + 32 * i];
+    int c = 0, slot = 0;
+    auto request = [&](int pp) {
+      c = (int)(uint32_t)dst[pp];
+#pragma unroll
+      for (int i = 0; i < PER; ++i) cv[i] = a.cR[(int64_t)c * a.dp + lane + 32 * i];
+      if (a.list_count && lane == 0) slot = atomicAdd(&a.list_count[c], 1);
+    };
+    // (no look-ahead above D_p 1024, where the registers run out)
+    constexpr bool kAhead = NW4 <= 8;
+    if (kAhead && warp < npq) request(warp);
+    for (int p = warp; p < npq; p += 4) {
+      if (!kAhead) request(p);
+      float cur[PER];
+#pragma unroll
+      for (int i = 0; i < PER; ++i) cur[i] = cv[i];
+      const int cc = c;
+      const int sl = __shfl_sync(0xffffffffu, slot, 0);
+      if (kAhead && p + 4 < npq) request(p + 4);
+      quantize_pair<NW4>(row * a.npmax + p, row, cc, sl, lane, qv, cur, a.nq, a.dp, a.qparams,
+                         a.planes, a.list_pairs, a.qdb, a.qpb, a.qrec,
+                         &dst[p]);
+    }
   }
   // The block's own writes of planes and parameters are visible to it
   // after the barrier.
@@ -1317,14 +1444,14 @@ __global__ void __launch_bounds__(128, NW4 >= 4 ? 4 : 8) prep_kernel(PrepArgs a)
   const int n_sel = a.nsel[row];
   uint32_t tau = kU32Max;
   if (!*a.no_prune && n_sel > 0) {
-    uint32_t* bk = a.bkeys + row * a.bkeys_stride;
+    uint32_t* bk = reinterpret_cast<uint32_t*>(region);
     if (a.lut)
       tau = bound_block_lut<NW4>(row, a.npmax, npq, n_sel, dst, a.qparams, a.qrot, a.cR,
-                                 a.offsets, a.codes, a.fac, a.dp, bk, lut_region, hist, small,
-                                 ctl);
+                                 a.offsets, a.codes, a.fac, a.dp, bk, a.bound_cap, lut_region,
+                                 hist, small, ctl);
     else
       tau = bound_block<NW4>(row, a.npmax, npq, n_sel, dst, a.qparams, a.planes, a.offsets,
-                             a.codes, a.fac, a.dp, bk, hist, small, ctl);
+                             a.codes, a.fac, a.dp, bk, a.bound_cap, hist, small, ctl);
   }
   if (tid == 0) a.bound[row] = tau;
   if (a.qrec) {
@@ -1387,7 +1514,6 @@ void layout_workspace(const rq_index* ix, const SearchShape& sh, Workspace& ws) 
   L.take(&ws.wtotal, nq);
   L.take(&ws.cand, nq * ws.cap);
   L.take(&ws.sel, nq * sh.nsel_max);
-  L.take(&ws.bkeys, nq * bound_window(sh.nsel_max));
   // the per-query parameters in one region (one copy from the pinned staging
   // buffer, which has the same layout): nprobe, k, selection size, re-rank
   // flag (+1: the no-prune flag)
@@ -1457,7 +1583,6 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
   rebase(ws.wtotal, b);
   rebase(ws.cand, b);
   rebase(ws.sel, b);
-  rebase(ws.bkeys, b);
   rebase(ws.nprobe, b);
   ws.kq = ws.nprobe + nq;
   ws.nsel = ws.nprobe + 2 * nq;
@@ -1528,8 +1653,6 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
     a.nchunks = grouped ? nullptr : ws.nchunks;
     a.chunk = sh.chunk;
     a.lut = sh.lut;
-    a.bkeys = ws.bkeys;
-    a.bkeys_stride = bound_window(sh.nsel_max);
     a.err = ix->d_err;
     // the probe selection's shared region: the certified form's keys, rows,
     // candidates and query; the exact form stages the nlist keys when they fit
@@ -1537,7 +1660,12 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
         certified ? ((std::max<size_t>((size_t)ix->nlist * 8, (size_t)kProbeRowStage * dp * 4) +
                       15) & ~(size_t)15) + kProbeCandCap * 4 + (size_t)dp * 4
                   : (ix->nlist <= kProbeStageKeys ? (size_t)ix->nlist * 8 : 0);
-    size_t smem = (size_t)std::max(2, next_pow2_host(np)) * 8 + std::max<size_t>(stage, 64);
+    // ... and then the first bound's keys: n_sel plus two rounds of
+    // estimates (at most 512 keys each) fit with room to spare
+    const size_t bound_bytes = (size_t)4 * (2 * (size_t)sh.nsel_max + 1024);
+    const size_t region = (std::max<size_t>({stage, bound_bytes, 64}) + 15) & ~(size_t)15;
+    a.bound_cap = (int)(region / 4);
+    size_t smem = (size_t)std::max(2, next_pow2_host(np)) * 8 + region;
     smem = (smem + 15) & ~(size_t)15;
     a.lut_offset = (int)smem;
     if (sh.lut) smem += (size_t)(32 * dp + dp) * sizeof(float);
