@@ -75,6 +75,10 @@ __device__ __forceinline__ void emit_chunk(uint32_t passbits, const float (&d)[J
                                            bool word_valid, uint32_t id,
                                            uint32_t* __restrict__ mask,
                                            uint64_t* __restrict__ cand, int lane) {
+  if (!__any_sync(0xffffffffu, passbits != 0)) {  // the common case: no pair passes
+    if (word_valid && lane < J && lane < nvalid) mask[wrow[lane] + word] = 0u;
+    return;
+  }
   uint32_t mine = 0;
 #pragma unroll
   for (int j = 0; j < J; ++j) {

@@ -111,6 +111,14 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// The bound as a float32 threshold. The estimates compared with it are
+// never -0 or NaN, and neither is a bound taken from them, so
+// orderable(d) <= tau exactly when d <= tau_threshold(tau) (all ones: no
+// bound, +inf).
+__device__ __forceinline__ float tau_threshold(uint32_t tau) {
+  return tau == kU32Max ? __int_as_float(0x7f800000) : from_orderable(tau);
+}
+
 // Packed two-lane float32 arithmetic (add / mul / fma .rn.f32x2), each lane
 // rounded once to nearest even. A packed multiply whose result feeds a packed
 // add can still come out fused into one rounding, so they are used only where
@@ -226,13 +234,13 @@ __device__ void producer_loop(uint8_t* sm, uint32_t sbase, const int2* __restric
       const uint32_t full = sbase + kSmBar + 8 * st;
       const int np = min(kMmaNmax, jc);
       const int32_t* lp = list_pairs + (int64_t)jl * pair_stride;
-      uint32_t* tau = reinterpret_cast<uint32_t*>(sm + kSmTau) + st * kMmaNmax;
+      float* tau = reinterpret_cast<float*>(sm + kSmTau) + st * kMmaNmax;
       int64_t* wrow = reinterpret_cast<int64_t*>(sm + kSmWrow) + st * kMmaNmax;
       for (int g = lane; g < np; g += 32) {
         const int pair = lp[g];
         const int q = pair / npmax;
         wrow[g] = (int64_t)q * mwords + wbase[pair];
-        tau[g] = bound[q];
+        tau[g] = tau_threshold(bound[q]);
       }
       __syncwarp();
       if (lane == 0) {
@@ -336,7 +344,7 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items,
       const float2* fac_s = reinterpret_cast<const float2*>(sm + kSmFac + st * kFacBytes) +
                             (m.lo & 1);
       const float4* qp_s = reinterpret_cast<const float4*>(sm + kSmQp + st * kMmaNmax * 16);
-      uint32_t* s_tau = reinterpret_cast<uint32_t*>(sm + kSmTau) + st * kMmaNmax;
+      float* s_tau = reinterpret_cast<float*>(sm + kSmTau) + st * kMmaNmax;
       int64_t* s_wrow = reinterpret_cast<int64_t*>(sm + kSmWrow) + st * kMmaNmax;
       const int32_t* lp = list_pairs + (int64_t)m.l * pair_stride;
       const uint64_t bdesc = sdesc_sw128(sbase + kSmB + st * kMmaNmax * kMmaK);
@@ -359,7 +367,7 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items,
             const int pair = lp[g0 + g];
             const int q = pair / npmax;
             s_wrow[g] = (int64_t)q * mwords + wbase[pair];
-            s_tau[g] = bound[q];
+            s_tau[g] = tau_threshold(bound[q]);
           }
           if (tid == 0) s_ok[2] = mbar_wait_bounded(bar_aux, ph_aux, wait_ns) ? 1 : 0;
           ph_aux ^= 1u;
@@ -412,9 +420,10 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items,
         // float2 operations. The estimator's operations are the popcount
         // form's, each rounded once: a = 2 ip - Sq is an exact small integer
         // (one FMA with -Sq gives it exactly); x - 2 y is x + (-2) y (the
-        // negation and the doubling are exact, so fusing them with the add
+        // negation and the doubling are exact, so one fused multiply-add
         // rounds the same); the final + 0 of the popcount form is left out
-        // because (nq2 + r^2) - x with nq2, r^2 >= +0 is never -0.
+        // because (nq2 + r^2) - x with nq2, r^2 >= +0 is never -0. Pairs past
+        // np are computed on stale parameters and masked off.
         {
           const int quarter = warp & 3, tile = warp >> 2;
           if (tile < ntiles) {
@@ -431,7 +440,7 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items,
             const float2 r2 = make_float2(f.x, f.x);
             const float2 f2 = make_float2(f.y, f.y);
             const float2 two = make_float2(2.0f, 2.0f), mtwo = make_float2(-2.0f, -2.0f);
-            const uint2* tau2 = reinterpret_cast<const uint2*>(s_tau);
+            const float2* tau2 = reinterpret_cast<const float2*>(s_tau);
             const uint32_t tl = taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tile * kMmaNmax);
             const int64_t word = m.v0 / 32 + warp;
             for (int c1 = 0; c1 < np; c1 += 8) {
@@ -442,27 +451,25 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items,
 #pragma unroll
               for (int h = 0; h < 4; ++h) {
                 const int g = c1 + 2 * h;
-                d[2 * h] = 0.0f;
-                d[2 * h + 1] = 0.0f;
-                if (g < np) {
-                  const float4 qa = qp_s[g];      // {vl, vl', delta, delta'}
-                  const float4 qb = qp_s[g + 1];  // {nq2, nq2', -Sq, -Sq'}
-                  const float2 ip = make_float2(__uint_as_float(r[2 * h]), __uint_as_float(r[2 * h + 1]));
-                  const float2 a = fma2_rn(two, ip, make_float2(qb.z, qb.w));
-                  // t in scalar operations: a packed multiply feeding a packed
-                  // add may be contracted into one fused operation.
-                  const float2 t = make_float2(
-                      __fadd_rn(__fmul_rn(qa.z, a.x), __fmul_rn(qa.x, bterm)),
-                      __fadd_rn(__fmul_rn(qa.w, a.y), __fmul_rn(qa.y, bterm)));
-                  const float2 base = add2_rn(make_float2(qb.x, qb.y), r2);
-                  const float2 dd = add2_rn(base, mul2_rn(mtwo, mul2_rn(f2, t)));
-                  d[2 * h] = dd.x;
-                  d[2 * h + 1] = dd.y;
-                  const uint2 tt = tau2[g >> 1];
-                  if (valid && orderable(dd.x) <= tt.x) passbits |= 1u << (2 * h);
-                  if (valid && g + 1 < np && orderable(dd.y) <= tt.y) passbits |= 2u << (2 * h);
-                }
+                const float4 qa = qp_s[g];      // {vl, vl', delta, delta'}
+                const float4 qb = qp_s[g + 1];  // {nq2, nq2', -Sq, -Sq'}
+                const float2 ip = make_float2(__uint_as_float(r[2 * h]), __uint_as_float(r[2 * h + 1]));
+                const float2 a = fma2_rn(two, ip, make_float2(qb.z, qb.w));
+                // t in scalar operations: a packed multiply feeding a packed
+                // add may be contracted into one fused operation.
+                const float2 t = make_float2(
+                    __fadd_rn(__fmul_rn(qa.z, a.x), __fmul_rn(qa.x, bterm)),
+                    __fadd_rn(__fmul_rn(qa.w, a.y), __fmul_rn(qa.y, bterm)));
+                const float2 base = add2_rn(make_float2(qb.x, qb.y), r2);
+                const float2 dd = fma2_rn(mtwo, mul2_rn(f2, t), base);
+                d[2 * h] = dd.x;
+                d[2 * h + 1] = dd.y;
+                const float2 tt = tau2[g >> 1];
+                passbits |= (dd.x <= tt.x ? 1u : 0u) << (2 * h);
+                passbits |= (dd.y <= tt.y ? 2u : 0u) << (2 * h);
               }
+              const int left = np - c1;
+              passbits &= valid ? (left >= 8 ? 0xFFu : (1u << left) - 1u) : 0u;
               emit_chunk<8>(passbits, d, s_wrow + c1, np - c1, word, warp * 32 < m.nvec,
                             (uint32_t)(m.lo + v), mask, cand, lane);
             }
