@@ -1079,7 +1079,7 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
 // always the fixed-order float32 one (the terms (q'_d - c_d)^2 added in
 // increasing d, no fused multiply-add).
 constexpr int kProbeStageKeys = 4096;
-constexpr int kProbeCandCap = 256;
+constexpr int kProbeCandCap = 1024;
 constexpr int kProbeRowStage = 32;  // candidates whose rows are staged in shared memory
 
 // Exact form: select from the full exact ranking (pkeys, nlist keys per
@@ -1102,16 +1102,22 @@ __device__ inline int probe_select_exact(const uint64_t* __restrict__ pkeys, int
 __device__ __forceinline__ float seq_sqdist(const float* qs, const float* __restrict__ c, int dp) {
   float acc = 0.0f;
   const float4* c4 = reinterpret_cast<const float4*>(c);
-  for (int d = 0; d < dp; d += 4) {
-    const float4 v = __ldg(c4 + (d >> 2));
-    float df = __fsub_rn(qs[d], v.x);
-    acc = __fadd_rn(acc, __fmul_rn(df, df));
-    df = __fsub_rn(qs[d + 1], v.y);
-    acc = __fadd_rn(acc, __fmul_rn(df, df));
-    df = __fsub_rn(qs[d + 2], v.z);
-    acc = __fadd_rn(acc, __fmul_rn(df, df));
-    df = __fsub_rn(qs[d + 3], v.w);
-    acc = __fadd_rn(acc, __fmul_rn(df, df));
+  for (int d0 = 0; d0 < dp; d0 += 32) {  // D_p is a multiple of 32
+    float4 v[8];                          // a 128-byte row piece in flight
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __ldg(c4 + (d0 >> 2) + j);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int d = d0 + 4 * j;
+      float df = __fsub_rn(qs[d], v[j].x);
+      acc = __fadd_rn(acc, __fmul_rn(df, df));
+      df = __fsub_rn(qs[d + 1], v[j].y);
+      acc = __fadd_rn(acc, __fmul_rn(df, df));
+      df = __fsub_rn(qs[d + 2], v[j].z);
+      acc = __fadd_rn(acc, __fmul_rn(df, df));
+      df = __fsub_rn(qs[d + 3], v[j].w);
+      acc = __fadd_rn(acc, __fmul_rn(df, df));
+    }
   }
   return acc;
 }
@@ -1125,7 +1131,8 @@ __device__ __forceinline__ float seq_sqdist(const float* qs, const float* __rest
 // ||q'||^2 + ||c||^2 -- a factor of more than 3 to spare. U = the np-th
 // smallest a + e bounds the np-th smallest exact distance from above, so a
 // centroid with a - e > U is not among the np nearest (not even on a tie);
-// the others (a few dozen) get the exact distance and the exact selection.
+// the others (np and a few more) get the exact distance and the exact
+// selection.
 // If more than kProbeCandCap remain, every centroid gets the exact distance.
 // Shared memory: `region` holds max(nlist keys, kProbeRowStage rows of D_p
 // floats) + kProbeCandCap ints + D_p floats.
