@@ -98,12 +98,10 @@ struct Workspace {
   int32_t* counts = nullptr;    // nq: candidates that passed (written by the finalize)
   // Scan output: for probe p of query q, word w of the probed list's
   // survivor mask sits at mask[q * mwords + wbase[q * npmax + p] + w] (bit i:
-  // vector 32 w + i passed the bound), and that vector's key at
-  // cand[32 * (that index) + i].
+  // vector 32 w + i passed the bound).
   uint32_t* mask = nullptr;     // nq x mwords
   int32_t* wbase = nullptr;     // nq x npmax: first mask word of each probe
   int32_t* wtotal = nullptr;    // nq: mask words of the query's probes
-  uint64_t* cand = nullptr;     // nq x cap, cap = 32 mwords
   uint64_t* sel = nullptr;      // nq x nsel_max
   int32_t* nprobe = nullptr;    // nq
   int32_t* kq = nullptr;        // nq
@@ -118,10 +116,10 @@ struct Workspace {
   uint8_t* qdig = nullptr;        // nlist x nq x D_p: per-list buckets of FP8 query digits
   float4* qpb = nullptr;          // nlist x nq (+2): per-list buckets of {vl, delta, nq2, -Sq},
                                   // interleaved by slot couples
+  float* resid = nullptr;         // FastScan: nq x npmax x D_p residuals
   uint8_t* qrec = nullptr;        // nlist x nq pair records of the streaming scan
                                   // (pair_rec_bytes(D_p) each)
   int64_t mwords = 0;             // mask words per query
-  int64_t cap = 0;                // key slots per query (32 mwords)
 };
 
 struct Plan {

@@ -44,62 +44,38 @@ __device__ __forceinline__ float estimate_regs(const uint4 (&code)[NW4], int pc,
 }
 
 
-// Scan output without atomics. The vectors of a probed list are cut into
-// 32-vector words; word w of probe p of query q has the fixed mask index
-// x = q * mwords + wbase[q, p] + w (bit i set: vector 32 w + i of the list
-// passed the query's bound) and 32 key slots from 32 x, where the keys of the
-// passing vectors are packed in lane order. A key is (orderable estimate,
-// slot of the vector in the list layout); the finalize kernel replaces the
-// slot by the row id when it collects the candidates. A warp holds one word
-// (lane i = vector 32 w + i); every word of every probed list is written on
-// every search, so neither buffer is cleared.
-__device__ __forceinline__ void emit_word(bool pass, float d, uint32_t id, int64_t widx,
-                                          uint32_t* __restrict__ mask,
-                                          uint64_t* __restrict__ cand, int lane) {
+// Scan output without atomics: survivor masks only. The vectors of a probed
+// list are cut into 32-vector words; word w of probe p of query q has the
+// fixed mask index x = q * mwords + wbase[q, p] + w (bit i set: vector
+// 32 w + i of the list passed the query's bound). Every word of every probed
+// list is written on every search, so the masks are never cleared. The
+// finalize kernel recomputes the estimate of each surviving vector (every
+// scan form computes the same float32 value) and pairs it with the row id.
+// A warp holds one word (lane i = vector 32 w + i).
+__device__ __forceinline__ void emit_word(bool pass, int64_t widx, uint32_t* __restrict__ mask,
+                                          int lane) {
   const uint32_t m = __ballot_sync(0xffffffffu, pass);
   if (lane == 0) mask[widx] = m;
-  if (pass) cand[widx * 32 + __popc(m & ((1u << lane) - 1u))] = make_key(d, id);
 }
 
 // The same for a chunk of J pairs over one word: bit j of `passbits` says
 // whether this lane's vector passes for pair j, whose first mask index is
 // wrow[j] (the word's index is wrow[j] + word); lane j writes pair j's mask
 // word. Pairs j >= nvalid and words past the list's end (word_valid false,
-// where no lane passes) write no mask. The keys are written in a loop that
-// takes one passing pair per lane per round, as many rounds as the lane with
-// the most passing pairs needs (few: most pairs fail). All 32 lanes must
-// call it.
+// where no lane passes) write no mask. All 32 lanes must call it.
 template <int J>
-__device__ __forceinline__ void emit_chunk(uint32_t passbits, const float (&d)[J],
-                                           const int64_t* wrow, int nvalid, int64_t word,
-                                           bool word_valid, uint32_t id,
-                                           uint32_t* __restrict__ mask,
-                                           uint64_t* __restrict__ cand, int lane) {
-  if (!__any_sync(0xffffffffu, passbits != 0)) {  // the common case: no pair passes
-    if (word_valid && lane < J && lane < nvalid) mask[wrow[lane] + word] = 0u;
-    return;
-  }
+__device__ __forceinline__ void emit_chunk(uint32_t passbits, const int64_t* wrow, int nvalid,
+                                           int64_t word, bool word_valid,
+                                           uint32_t* __restrict__ mask, int lane) {
   uint32_t mine = 0;
+  if (__any_sync(0xffffffffu, passbits != 0)) {  // else (the common case) every word is 0
 #pragma unroll
-  for (int j = 0; j < J; ++j) {
-    const uint32_t m = __ballot_sync(0xffffffffu, (passbits >> j) & 1u);
-    if (lane == j) mine = m;
-  }
-  if (word_valid && lane < J && lane < nvalid) mask[wrow[lane] + word] = mine;
-  const uint32_t lt = (1u << lane) - 1u;
-  uint32_t pb = passbits;
-  while (__any_sync(0xffffffffu, pb != 0)) {
-    const int j = pb ? __ffs(pb) - 1 : 0;
-    const uint32_t mj = __shfl_sync(0xffffffffu, mine, j);
-    if (pb) {
-      pb &= pb - 1;
-      float dj = d[0];
-#pragma unroll
-      for (int k = 1; k < J; ++k)
-        if (j == k) dj = d[k];
-      cand[(wrow[j] + word) * 32 + __popc(mj & lt)] = make_key(dj, id);
+    for (int j = 0; j < J; ++j) {
+      const uint32_t m = __ballot_sync(0xffffffffu, (passbits >> j) & 1u);
+      if (lane == j) mine = m;
     }
   }
+  if (word_valid && lane < J && lane < nvalid) mask[wrow[lane] + word] = mine;
 }
 
 // FP8 E4M3 encoding of an integer 0..15 (exact): v = 2^e (1 + m/8) with

@@ -298,7 +298,7 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items,
                 const uint8_t* __restrict__ codes, const float2* __restrict__ fac,
                 const uint32_t* __restrict__ bound,
                 const int32_t* __restrict__ wbase, int64_t mwords, uint32_t* __restrict__ mask,
-                uint64_t* __restrict__ cand, int32_t* err, uint64_t wait_ns, int withhold) {
+                int32_t* err, uint64_t wait_ns, int withhold) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ volatile int s_ok[4];  // results of the polled waits
   const uint32_t raw_addr = smem_u32(smem_raw);
@@ -446,7 +446,6 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items,
             for (int c1 = 0; c1 < np; c1 += 8) {
               uint32_t r[8];
               tmem_ld8(tl + (uint32_t)c1, r);
-              float d[8];
               uint32_t passbits = 0;
 #pragma unroll
               for (int h = 0; h < 4; ++h) {
@@ -462,16 +461,13 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items,
                     __fadd_rn(__fmul_rn(qa.w, a.y), __fmul_rn(qa.y, bterm)));
                 const float2 base = add2_rn(make_float2(qb.x, qb.y), r2);
                 const float2 dd = fma2_rn(mtwo, mul2_rn(f2, t), base);
-                d[2 * h] = dd.x;
-                d[2 * h + 1] = dd.y;
                 const float2 tt = tau2[g >> 1];
                 passbits |= (dd.x <= tt.x ? 1u : 0u) << (2 * h);
                 passbits |= (dd.y <= tt.y ? 2u : 0u) << (2 * h);
               }
               const int left = np - c1;
               passbits &= valid ? (left >= 8 ? 0xFFu : (1u << left) - 1u) : 0u;
-              emit_chunk<8>(passbits, d, s_wrow + c1, np - c1, word, warp * 32 < m.nvec,
-                            (uint32_t)(m.lo + v), mask, cand, lane);
+              emit_chunk<8>(passbits, s_wrow + c1, np - c1, word, warp * 32 < m.nvec, mask, lane);
             }
           }
         }
@@ -509,7 +505,7 @@ rq_status launch_scan_mma(rq_index* ix, const SearchShape& sh, Workspace& ws, cu
   const unsigned grid = (unsigned)std::max(1, std::min(sms * 3, ix->n_items));
   scan_mma_kernel<<<grid, kMmaThreads, kSmAlloc, st>>>(
       ix->items, ix->n_items, ws.list_count, ws.list_pairs, sh.nq, ws.qpb, ws.qdig, sh.npmax,
-      ix->offsets, ix->codes, ix->fac, ws.bound, ws.wbase, ws.mwords, ws.mask, ws.cand,
+      ix->offsets, ix->codes, ix->fac, ws.bound, ws.wbase, ws.mwords, ws.mask,
       ix->d_err, withhold ? kTestWaitLimitNs : kWaitLimitNs, withhold);
   RQ_CUDA(cudaGetLastError());
   return RQ_OK;

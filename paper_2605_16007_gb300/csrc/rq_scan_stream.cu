@@ -214,7 +214,7 @@ __device__ void stream_consumer(const uint8_t* sm, uint32_t sbase, int* s_next,
                                 const volatile int* s_issued,
                                 const uint8_t* __restrict__ recs, int64_t pair_stride,
                                 int64_t mwords, int64_t mask_words, uint32_t* __restrict__ mask,
-                                uint64_t* __restrict__ cand, int32_t* err, uint64_t wait_ns) {
+                                int32_t* err, uint64_t wait_ns) {
   using Cfg = StreamCfg<NW4>;
   constexpr int S = Cfg::kStages;
   constexpr int DP = 128 * NW4;
@@ -223,7 +223,6 @@ __device__ void stream_consumer(const uint8_t* sm, uint32_t sbase, int* s_next,
   const StreamMeta* meta = reinterpret_cast<const StreamMeta*>(sm + Cfg::kMetaOff);
   const uint32_t bar_full = sbase + Cfg::kBarOff;
   const uint32_t bar_empty = bar_full + 8 * S;
-  const uint32_t lt = (1u << lane) - 1u;
   for (;;) {
     int i = 0;
     if (lane == 0) i = atomicAdd(s_next, 1);
@@ -290,24 +289,20 @@ __device__ void stream_consumer(const uint8_t* sm, uint32_t sbase, int* s_next,
         const float4 qp = *reinterpret_cast<const float4*>(rp + 64 * NW4);
         const int4 rm = *reinterpret_cast<const int4*>(rp + 64 * NW4 + 16);  // q, wbase, tau
         const int64_t wrow = (int64_t)rm.x * mwords + rm.y + word0;
-        float d[SB];
         uint32_t mw[SB];
 #pragma unroll
         for (int b = 0; b < SB; ++b) {
           const bool valid = b0 + 32 * b + lane < m.nvec;
-          d[b] = estimate_regs<NW4>(code[b], pc[b], f[b], reinterpret_cast<const uint32_t*>(rp),
-                                    qp, DP);
-          mw[b] = __ballot_sync(0xffffffffu, valid && orderable(d[b]) <= (uint32_t)rm.z);
+          const float d = estimate_regs<NW4>(code[b], pc[b], f[b],
+                                             reinterpret_cast<const uint32_t*>(rp), qp, DP);
+          mw[b] = __ballot_sync(0xffffffffu, valid && orderable(d) <= (uint32_t)rm.z);
         }
-        // lane b writes the mask word of block b; passing lanes write keys
+        // lane b writes the mask word of block b
 #pragma unroll
         for (int b = 0; b < SB; ++b) {
           if (b0 + 32 * b >= m.nvec) break;  // warp-uniform: past the item's end
           if (!index_ok(wrow + b, mask_words, err)) break;
           if (lane == b) mask[wrow + b] = mw[b];
-          if ((mw[b] >> lane) & 1u)
-            cand[(wrow + b) * 32 + __popc(mw[b] & lt)] =
-                make_key(d[b], (uint32_t)(m.lo + b0 + 32 * b + lane));
         }
       }
     }
@@ -322,7 +317,7 @@ scan_stream_kernel(const int2* __restrict__ items, int n_items,
                    const int32_t* __restrict__ list_count, const uint8_t* __restrict__ recs,
                    int64_t pair_stride, const int64_t* __restrict__ offsets,
                    const uint8_t* __restrict__ codes, const float2* __restrict__ fac,
-                   int64_t mwords, uint32_t* __restrict__ mask, uint64_t* __restrict__ cand,
+                   int64_t mwords, uint32_t* __restrict__ mask,
                    int32_t* err, uint64_t wait_ns, int withhold) {
   using Cfg = StreamCfg<NW4>;
   extern __shared__ uint8_t smem_raw[];
@@ -346,7 +341,7 @@ scan_stream_kernel(const int2* __restrict__ items, int n_items,
                          fac, s_issued, err, wait_ns, withhold);
   else
     stream_consumer<NW4>(sm, sbase, s_next, s_issued, recs, pair_stride, mwords,
-                         pair_stride * mwords, mask, cand, err, wait_ns);
+                         pair_stride * mwords, mask, err, wait_ns);
 }
 
 template <int NW4>
@@ -357,7 +352,7 @@ rq_status launch_stream(rq_index* ix, const SearchShape& sh, Workspace& ws, cuda
   const unsigned grid = (unsigned)std::max(1, std::min(sms, ix->n_items));
   scan_stream_kernel<NW4><<<grid, kStreamThreads, Cfg::kSmem, st>>>(
       ix->items, ix->n_items, ws.list_count, ws.qrec, sh.nq, ix->offsets, ix->codes, ix->fac,
-      ws.mwords, ws.mask, ws.cand, ix->d_err, wait_ns, withhold);
+      ws.mwords, ws.mask, ix->d_err, wait_ns, withhold);
   RQ_CUDA(cudaGetLastError());
   return RQ_OK;
 }

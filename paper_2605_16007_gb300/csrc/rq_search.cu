@@ -238,9 +238,8 @@ __device__ __forceinline__ void quantize_pair(int64_t pair, int64_t q, int c, in
 // vectors) -- the query-level schedule of Section 3.3.1, with long lists cut
 // into chunks so that they do not leave one block running alone. A thread
 // loads the codes of up to eight 128-vector steps before estimating them,
-// then writes, per warp, the survivor mask word and the keys of its 32
-// vectors (emit_word). Keys carry the vector's slot; the finalize kernel maps
-// the slots of the candidates it collects to row ids.
+// then each warp writes the survivor mask word of its 32 vectors
+// (emit_word).
 // ---------------------------------------------------------------------------
 constexpr int kPlainChunk = 1024;  // default vectors of one list per block of the plain scan
 
@@ -252,7 +251,7 @@ scan_plain_kernel(const int32_t* __restrict__ nchunks, const int32_t* __restrict
                   const uint8_t* __restrict__ codes, const float2* __restrict__ fac,
                   int dp, const uint32_t* __restrict__ bound,
                   const int32_t* __restrict__ wbase, int64_t mwords, uint32_t* __restrict__ mask,
-                  uint64_t* __restrict__ cand, int64_t mask_words, int32_t* err) {
+                  int64_t mask_words, int32_t* err) {
   constexpr int W = 4 * NW4;
   constexpr int RB = NW4 >= 8 ? 1 : 8 / NW4;  // 128-vector steps with their loads in flight
   __shared__ __align__(16) uint32_t s_pl[4 * W];
@@ -284,20 +283,18 @@ scan_plain_kernel(const int32_t* __restrict__ nchunks, const int32_t* __restrict
         fv[r] = __ldg(fac + s);
       }
     }
-    float dv[RB];
     uint32_t passm = 0;
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
       const int64_t s = b0 + 128 * r + threadIdx.x;
-      dv[r] = 0.0f;
       if (s < end) {
         int pc = 0;
 #pragma unroll
         for (int w = 0; w < NW4; ++w)
           pc += __popc(code[r][w].x) + __popc(code[r][w].y) + __popc(code[r][w].z) +
                 __popc(code[r][w].w);
-        dv[r] = estimate_regs<NW4>(code[r], pc, fv[r], s_pl, qp, dp);
-        if (orderable(dv[r]) <= tau) passm |= 1u << r;
+        if (orderable(estimate_regs<NW4>(code[r], pc, fv[r], s_pl, qp, dp)) <= tau)
+          passm |= 1u << r;
       }
     }
 #pragma unroll
@@ -306,7 +303,7 @@ scan_plain_kernel(const int32_t* __restrict__ nchunks, const int32_t* __restrict
       if (s0 + warp * 32 >= end) break;  // warp-uniform: this word is past the chunk's end
       const int64_t widx = wrow + (s0 - lo) / 32 + warp;
       if (!index_ok(widx, mask_words, err)) continue;
-      emit_word((passm >> r) & 1u, dv[r], (uint32_t)(s0 + threadIdx.x), widx, mask, cand, lane);
+      emit_word((passm >> r) & 1u, widx, mask, lane);
     }
   }
 }
@@ -355,6 +352,34 @@ __device__ __forceinline__ float estimate_lut_regs(const uint4 (&code)[NW4], con
   return __fadd_rn(d, 0.0f);
 }
 
+// The same value without the tables, from the residual r itself (global or
+// shared memory): entry T[g][v] is built from T[g][0] = 0 by adding r[8 g + i]
+// for the set bits i of v in increasing order, which is what the inner loop
+// adds here, in the same order and from the same +0.
+template <int NW4>
+__device__ __forceinline__ float estimate_lut_direct(const uint4 (&code)[NW4],
+                                                     const float* __restrict__ r, float2 fac,
+                                                     float nq2, float S) {
+  float sum = 0.0f;
+#pragma unroll
+  for (int w = 0; w < NW4; ++w) {
+    const uint32_t word[4] = {code[w].x, code[w].y, code[w].z, code[w].w};
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int g = 16 * w + j;
+      const uint32_t v = (word[j >> 2] >> (8 * (j & 3))) & 255u;
+      float e = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if ((v >> i) & 1u) e = __fadd_rn(e, r[8 * g + i]);
+      sum = (g == 0) ? e : __fadd_rn(sum, e);
+    }
+  }
+  const float t = __fsub_rn(__fmul_rn(2.0f, sum), S);
+  const float d = __fsub_rn(__fadd_rn(nq2, fac.x), __fmul_rn(2.0f, __fmul_rn(fac.y, t)));
+  return __fadd_rn(d, 0.0f);
+}
+
 // The residual r = q' - P^T c of one (query, probed list) pair into shared
 // memory (D_p floats), by the whole block.
 __device__ __forceinline__ void residual_to_smem(const float* __restrict__ qrot, int64_t q,
@@ -368,7 +393,7 @@ __device__ __forceinline__ void residual_to_smem(const float* __restrict__ qrot,
 // (query, probed list, chunk of 1024 list vectors); the block builds its
 // pair's tables in shared memory, then each thread estimates its vectors
 // (the codes of its 128-vector steps loaded before they are estimated) and
-// each warp writes the survivor mask word and keys of its 32 vectors.
+// each warp writes the survivor mask word of its 32 vectors.
 template <int NW4>
 __global__ void __launch_bounds__(128)
 scan_lut_kernel(const int32_t* __restrict__ nchunks, const int32_t* __restrict__ probe_ids,
@@ -376,8 +401,7 @@ scan_lut_kernel(const int32_t* __restrict__ nchunks, const int32_t* __restrict__
                 const float* __restrict__ cR, const int64_t* __restrict__ offsets,
                 const uint8_t* __restrict__ codes, const float2* __restrict__ fac, int dp,
                 const uint32_t* __restrict__ bound, const int32_t* __restrict__ wbase,
-                int64_t mwords, uint32_t* __restrict__ mask, uint64_t* __restrict__ cand,
-                int64_t mask_words, int32_t* err) {
+                int64_t mwords, uint32_t* __restrict__ mask, int64_t mask_words, int32_t* err) {
   constexpr int RB = NW4 >= 2 ? 4 : 8;
   extern __shared__ __align__(16) float s_lut[];  // D_p/8 x 256 table, then D_p residual
   float* s_r = s_lut + 32 * dp;
@@ -413,21 +437,15 @@ scan_lut_kernel(const int32_t* __restrict__ nchunks, const int32_t* __restrict__
       const int64_t s0 = b0 + 128 * r;
       if (s0 + warp * 32 >= end) break;  // warp-uniform: this word is past the chunk's end
       const int64_t sl = s0 + threadIdx.x;
-      float d = 0.0f;
-      bool pass = false;
-      if (sl < end) {
-        d = estimate_lut_regs<NW4>(code[r], s_lut, fv[r], qp.z, qp.w);
-        pass = orderable(d) <= tau;
-      }
+      const bool pass =
+          sl < end && orderable(estimate_lut_regs<NW4>(code[r], s_lut, fv[r], qp.z, qp.w)) <= tau;
       const int64_t widx = wrow + (s0 - lo) / 32 + warp;
       if (!index_ok(widx, mask_words, err)) continue;
-      emit_word(pass, d, (uint32_t)sl, widx, mask, cand, lane);
+      emit_word(pass, widx, mask, lane);
     }
   }
 }
 
-// The FastScan quantities of one pair (a warp): nq2 = ||r||^2 and S = sum_d
-// r_d, both in the 32-lane order, stored as {0, 0, nq2, S}.
 // ---------------------------------------------------------------------------
 // The first bound's n-th smallest estimate, kept in shared memory while the
 // estimates stream in (Section 3.3.3). The block offers keys in rounds; a
@@ -524,16 +542,20 @@ __device__ inline uint32_t kth_result(KthState* ks, uint32_t* buf, int total, in
   return thr;  // nb < n <= nb + eqc
 }
 
+// The FastScan quantities of one pair (a warp): nq2 = ||r||^2 and S = sum_d
+// r_d, both in the 32-lane order, stored as {0, 0, nq2, S}; the residual
+// itself goes to `resid` (D_p floats per pair) for the finalize kernel.
 template <int NW4>
 __device__ __forceinline__ void lut_pair(int64_t pair, int64_t q, int c, int lane,
                                          const float* __restrict__ qrot,
                                          const float* __restrict__ cR, int dp,
-                                         float4* __restrict__ qparams) {
+                                         float4* __restrict__ qparams, float* __restrict__ resid) {
   float acc2 = 0.0f, acc1 = 0.0f;
 #pragma unroll
   for (int i = 0; i < 4 * NW4; ++i) {
     const int d = lane + 32 * i;
     const float r = __fsub_rn(qrot[q * dp + d], cR[(int64_t)c * dp + d]);
+    resid[pair * dp + d] = r;
     acc2 = __fadd_rn(acc2, __fmul_rn(r, r));
     acc1 = __fadd_rn(acc1, r);
   }
@@ -881,72 +903,116 @@ __device__ __forceinline__ float exact_dist_lanes(const RawT* __restrict__ x,
 // block of several warps serves several queries at once.
 // ---------------------------------------------------------------------------
 
-// Shared memory of the finalize kernel: selection (P keys, at least
-// kFinDescKeys: it holds the word descriptors while the candidates are
-// collected), top-k (PK keys), histogram (256 ints), bucket (32 keys),
-// staging (S keys), query row (dim floats).
+// ---------------------------------------------------------------------------
+// Finalize: one block of kFinThreads per query. The survivors are read from
+// the scan's masks, their estimates recomputed (every scan form computes the
+// popcount form's float32 value, and the FastScan form's direct sums equal
+// its table sums), the n_sel smallest (estimate, row id) keys kept, then
+// gathered and re-ranked exactly, and the final k selected.
+//
+// Masks go in rounds of kFinRoundWords words; thread t holds
+// kFinWordsPerThread consecutive words of the round (four 16-byte loads in
+// flight together). A block scan of the per-thread counts gives each
+// nonzero word a descriptor (position of its first survivor, word offset)
+// and its mask word in shared memory. The survivors are then taken a thread
+// each, up to four at a time with all their loads in flight: the
+// descriptor by binary search, the bit by its rank in the word, the probe by
+// binary search over the probes' first words.
+//
+// Selection streams: a key below the threshold goes to the staging area;
+// when that could overflow in the next step, the n_sel smallest staged keys
+// are kept and the threshold becomes the largest of them. Keys are distinct
+// (one per vector), so a dropped key is above n_sel kept ones and is not
+// among the n_sel smallest of all.
+// ---------------------------------------------------------------------------
 constexpr int kFinThreads = 256;
 constexpr int kFinWordsPerThread = 16;                            // four 16-byte mask loads
 constexpr int kFinRoundWords = kFinThreads * kFinWordsPerThread;  // mask words per round
-constexpr int kFinDescKeys = kFinRoundWords / 2;                  // 4-byte descriptors, in keys
+constexpr int kFinStepMax = kFinThreads * 4;                      // survivors per step, at most
 
+// Shared memory, in order: selection (P keys), top-k (PK keys), staging (S
+// keys), probe slot bases (NP int64), bucket (32 keys), histogram (256
+// ints), descriptors and mask words (kFinRoundWords each), probe first words
+// (NP ints), query row (dim floats).
 struct FinalizeLayout {
-  int P, PK, S, dim;  // S: candidate keys staged per query
-  __host__ __device__ int sel_keys() const { return P > kFinDescKeys ? P : kFinDescKeys; }
+  int P, PK, S, NP, dim;
   __host__ __device__ int bytes() const {
-    return (sel_keys() + PK + S) * 8 + 256 * 4 + 32 * 8 + ((dim * 4 + 15) & ~15);
+    return (P + PK + S + NP + 32) * 8 + 256 * 4 + 2 * kFinRoundWords * 4 +
+           ((NP * 4 + 15) & ~15) + ((dim * 4 + 15) & ~15);
   }
 };
 
-// One block of kFinThreads per query. The candidates are collected from the
-// scan's survivor masks into shared memory (moved to the front of the
-// query's key slots when there are more than S), then selected (radix
-// passes), gathered and re-ranked, and the final k selected.
-// Survivor keys leave the scans as (estimate, slot); the row id of the slot
-// replaces it as the candidates are collected, so that every selection ranks
-// by (estimate, row id).
-//
-// Collection goes in rounds of kFinRoundWords mask words; thread t holds
-// kFinWordsPerThread consecutive words of the round (four 16-byte loads, all
-// in flight together). A block scan of the per-thread key counts gives every
-// key its position in word order. Each nonzero word leaves one descriptor
-// (position of its first key, word) in shared memory. Then thread t copies
-// the keys at positions t, t + kFinThreads, ... (found by binary search over
-// the descriptors), eight key loads and then eight id loads in flight.
-// When the staging area fills, it is written to the query's key slots at
-// the running position. A key's position never exceeds its slot (a word has
-// at most 32 keys, packed at the front of its 32 slots), and every key read
-// before a write has a smaller position than every key not yet read, so the
-// writes never reach a key that is still to be read.
-template <typename RawT>
-__global__ void __launch_bounds__(kFinThreads)
-finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ wtotal,
-                int64_t mwords, uint64_t* __restrict__ cand, const uint32_t* __restrict__ ids,
-                int64_t n_slots, int32_t* err, int32_t* __restrict__ counts,
-                const int32_t* __restrict__ nsel, const int32_t* __restrict__ kq,
-                const int32_t* __restrict__ rerank_on, int nsel_max, uint64_t* __restrict__ sel,
-                const RawT* __restrict__ raw, const float* __restrict__ q, int dim, int k_stride,
-                FinalizeLayout lay, int64_t* __restrict__ out_ids, float* __restrict__ out_d) {
+struct FinalizeArgs {
+  const uint32_t* mask;
+  const int32_t* wtotal;
+  int64_t mwords;
+  const int32_t* wbase;      // nq x npmax
+  const int32_t* probe_ids;  // nq x npmax
+  const int32_t* nprobe;     // nq
+  int npmax;
+  const int64_t* offsets;
+  const uint8_t* codes;
+  const float2* fac;
+  const uint32_t* planes;    // popcount form: nq x npmax x 4 x W words
+  const float4* qparams;     // nq x npmax
+  const float* resid;        // FastScan form: nq x npmax x D_p, else null
+  int dp;
+  const uint32_t* ids;
+  int64_t n_slots;
+  int32_t* err;
+  int32_t* counts;
+  const int32_t* nsel;
+  const int32_t* kq;
+  const int32_t* rerank_on;
+  int nsel_max;
+  uint64_t* sel;
+  const void* raw;
+  const float* q;
+  int dim, k_stride;
+  FinalizeLayout lay;
+  int64_t* out_ids;
+  float* out_d;
+};
+
+template <typename RawT, int NW4>
+__global__ void __launch_bounds__(kFinThreads) finalize_kernel(FinalizeArgs a) {
   constexpr int NWARP = kFinThreads / 32;
+  constexpr int W = 4 * NW4;
+  constexpr int PT = NW4 <= 2 ? 4 : (NW4 <= 4 ? 2 : 1);  // survivors per thread per step
+  constexpr int STEP = kFinThreads * PT;
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ int s_ctl[8];
   __shared__ int s_warp[NWARP];
+  __shared__ int s_nbuf;
+  __shared__ uint64_t s_thr;
+  const FinalizeLayout& lay = a.lay;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t row = blockIdx.x;
   uint64_t* s_sel = reinterpret_cast<uint64_t*>(smem);
-  uint32_t* s_desc = reinterpret_cast<uint32_t*>(smem);  // during collection only
-  uint64_t* s_top = s_sel + lay.sel_keys();
-  int* hist = reinterpret_cast<int*>(s_top + lay.PK);
-  uint64_t* small = reinterpret_cast<uint64_t*>(hist + 256);
-  uint64_t* s_stage = small + 32;
-  float* s_q = reinterpret_cast<float*>(s_stage + lay.S);
+  uint64_t* s_top = s_sel + lay.P;
+  uint64_t* s_stage = s_top + lay.PK;
+  int64_t* s_base = reinterpret_cast<int64_t*>(s_stage + lay.S);
+  uint64_t* small = reinterpret_cast<uint64_t*>(s_base + lay.NP);
+  int* hist = reinterpret_cast<int*>(small + 32);
+  uint32_t* s_desc = reinterpret_cast<uint32_t*>(hist + 256);
+  uint32_t* s_dword = s_desc + kFinRoundWords;
+  int* s_wb = reinterpret_cast<int*>(s_dword + kFinRoundWords);
+  float* s_q = reinterpret_cast<float*>(s_wb + ((lay.NP + 3) & ~3));
   // mwords is a multiple of 4 and the mask 16-byte aligned
-  const uint4* mrow4 = reinterpret_cast<const uint4*>(mask + row * mwords);
-  uint64_t* krow = cand + row * mwords * 32;
-  const int T = wtotal[row];
-  for (int d = tid; d < dim; d += kFinThreads) s_q[d] = q[row * dim + d];
-  int staged = 0;       // keys in s_stage (the same in every thread)
-  int64_t flushed = 0;  // keys already moved to krow[0, flushed)
+  const uint4* mrow4 = reinterpret_cast<const uint4*>(a.mask + row * a.mwords);
+  const int T = a.wtotal[row];
+  const int npq = min(a.nprobe[row], a.npmax);
+  const int n_sel = a.nsel[row];
+  for (int d = tid; d < a.dim; d += kFinThreads) s_q[d] = a.q[row * a.dim + d];
+  for (int p = tid; p < npq; p += kFinThreads) {
+    s_wb[p] = a.wbase[row * a.npmax + p];
+    s_base[p] = a.offsets[a.probe_ids[row * a.npmax + p]];
+  }
+  if (tid == 0) {
+    s_nbuf = 0;
+    s_thr = kU64Max;
+  }
+  int64_t count = 0;  // survivors (the same in every thread)
   for (int c0 = 0; c0 < T; c0 += kFinRoundWords) {
     const int wfirst = c0 + tid * kFinWordsPerThread;
     uint32_t w[kFinWordsPerThread];
@@ -966,8 +1032,8 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
       c += n;
       nz += n != 0;
     }
-    // one scan of both counts: keys (< 2^18 per round) in the low 18 bits,
-    // nonzero words (<= kFinRoundWords) above
+    // one scan of both counts: survivors (< 2^18 per round) in the low 18
+    // bits, nonzero words (<= kFinRoundWords) above
     const int v = c | (nz << 18);
     int incl = v;
 #pragma unroll
@@ -975,14 +1041,15 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
       const int t = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += t;
     }
+    __syncthreads();  // the previous round is done with s_warp and the descriptors
     if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
     int ex = incl - v, tot = 0;
 #pragma unroll
     for (int i = 0; i < NWARP; ++i) {
-      const int s = s_warp[i];
-      if (i < warp) ex += s;
-      tot += s;
+      const int sw = s_warp[i];
+      if (i < warp) ex += sw;
+      tot += sw;
     }
     const int tot_keys = tot & 0x3FFFF, tot_desc = tot >> 18;
     {
@@ -990,87 +1057,150 @@ finalize_kernel(const uint32_t* __restrict__ mask, const int32_t* __restrict__ w
 #pragma unroll
       for (int e = 0; e < kFinWordsPerThread; ++e) {
         const int n = __popc(w[e]);
-        if (n) s_desc[d++] = ((uint32_t)p << 12) | (uint32_t)(tid * kFinWordsPerThread + e);
+        if (n) {
+          s_desc[d] = ((uint32_t)p << 12) | (uint32_t)(tid * kFinWordsPerThread + e);
+          s_dword[d] = w[e];
+          ++d;
+        }
         p += n;
       }
     }
     __syncthreads();
-    for (int w0 = 0; w0 < tot_keys;) {
-      if (staged == lay.S) {
-        for (int i = tid; i < staged; i += kFinThreads) krow[flushed + i] = s_stage[i];
-        flushed += staged;
-        staged = 0;
-        __syncthreads();
-      }
-      const int wn = min(lay.S - staged, tot_keys - w0);
-      for (int jb = w0 + tid; jb < w0 + wn; jb += 8 * kFinThreads) {
-        int64_t src[8];
+    count += tot_keys;
+    for (int j0 = 0; j0 < tot_keys; j0 += STEP) {
+      const uint64_t thr = s_thr;
+      uint64_t key[PT];
+      bool have[PT];
+      int64_t slot[PT];
+      int64_t pair[PT];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int j = jb + u * kFinThreads;
-          src[u] = -1;
-          if (j < w0 + wn) {
-            int lo = 0, hi = tot_desc - 1;  // last descriptor whose first key is <= j
-            while (lo < hi) {
-              const int mid = (lo + hi + 1) >> 1;
-              if ((int)(s_desc[mid] >> 12) <= j) lo = mid; else hi = mid - 1;
-            }
-            const uint32_t dsc = s_desc[lo];
-            src[u] = (int64_t)(c0 + (int)(dsc & 4095u)) * 32 + (j - (int)(dsc >> 12));
+      for (int u = 0; u < PT; ++u) {
+        const int j = j0 + tid + u * kFinThreads;
+        have[u] = j < tot_keys;
+        slot[u] = 0;
+        pair[u] = row * a.npmax;
+        if (have[u]) {
+          int lo = 0, hi = tot_desc - 1;  // the last descriptor whose first survivor is <= j
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if ((int)(s_desc[mid] >> 12) <= j) lo = mid; else hi = mid - 1;
           }
+          const uint32_t dsc = s_desc[lo];
+          const int word = c0 + (int)(dsc & 4095u);
+          uint32_t mw = s_dword[lo];  // the survivor's bit: drop the lower set bits
+          for (int r = j - (int)(dsc >> 12); r > 0; --r) mw &= mw - 1u;
+          const int bit = __ffs(mw) - 1;
+          int plo = 0, phi = npq - 1;  // the probe holding `word`
+          while (plo < phi) {
+            const int mid = (plo + phi + 1) >> 1;
+            if (s_wb[mid] <= word) plo = mid; else phi = mid - 1;
+          }
+          slot[u] = s_base[plo] + (int64_t)(word - s_wb[plo]) * 32 + bit;
+          pair[u] = row * a.npmax + plo;
+          if (!index_ok(slot[u], a.n_slots, a.err)) have[u] = false;
         }
-        uint64_t kv[8];
+      }
+      // every load of the step in flight: codes, factors, ids, parameters
+      uint4 code[PT][NW4];
+      float2 fv[PT];
+      uint32_t rid[PT];
+      float4 qp[PT];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) kv[u] = src[u] >= 0 ? krow[src[u]] : 0ull;
-        uint32_t iv[8];
+      for (int u = 0; u < PT; ++u) {
+        if (have[u]) {
+          const uint4* cp = reinterpret_cast<const uint4*>(a.codes + slot[u] * (a.dp / 8));
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const uint32_t slot = (uint32_t)kv[u];
-          iv[u] = (src[u] >= 0 && index_ok(slot, n_slots, err)) ? __ldg(ids + slot) : 0u;
+          for (int x = 0; x < NW4; ++x) code[u][x] = __ldg(cp + x);
+          fv[u] = __ldg(a.fac + slot[u]);
+          rid[u] = __ldg(a.ids + slot[u]);
+          qp[u] = __ldg(a.qparams + pair[u]);
         }
+      }
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (src[u] >= 0)
-            s_stage[staged + (jb + u * kFinThreads - w0)] = (kv[u] & 0xFFFFFFFF00000000ull) | iv[u];
+      for (int u = 0; u < PT; ++u) {
+        key[u] = kU64Max;
+        if (have[u]) {
+          float d;
+          if (a.resid) {
+            d = estimate_lut_direct<NW4>(code[u], a.resid + pair[u] * a.dp, fv[u], qp[u].z,
+                                         qp[u].w);
+          } else {
+            int pc = 0;
+#pragma unroll
+            for (int x = 0; x < NW4; ++x)
+              pc += __popc(code[u][x].x) + __popc(code[u][x].y) + __popc(code[u][x].z) +
+                    __popc(code[u][x].w);
+            d = estimate_regs<NW4>(code[u], pc, fv[u], a.planes + pair[u] * 4 * W, qp[u], a.dp);
+          }
+          key[u] = make_key(d, rid[u]);
+        }
+      }
+      // offer: keys below the threshold go to the staging area
+#pragma unroll
+      for (int u = 0; u < PT; ++u) {
+        const bool keep = have[u] && key[u] < thr;
+        const uint32_t mk = __ballot_sync(0xffffffffu, keep);
+        int base = 0;
+        if (lane == 0 && mk) base = atomicAdd(&s_nbuf, __popc(mk));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (keep) s_stage[base + __popc(mk & ((1u << lane) - 1u))] = key[u];
       }
       __syncthreads();
-      staged += wn;
-      w0 += wn;
+      const int nb = s_nbuf;
+      if (nb > lay.S - STEP) {
+        // keep the n_sel smallest (nb > S - STEP > n_sel)
+        block_select_smallest(s_stage, nb, n_sel, s_sel, hist, small, s_ctl, false);
+        uint64_t mx = 0;
+        for (int i = tid; i < n_sel; i += kFinThreads) {
+          const uint64_t k = s_sel[i];
+          s_stage[i] = k;
+          mx = k > mx ? k : mx;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          const uint64_t t = __shfl_xor_sync(0xffffffffu, mx, o);
+          mx = t > mx ? t : mx;
+        }
+        if (lane == 0) small[warp] = mx;
+        __syncthreads();
+        if (tid == 0) {
+          uint64_t m2 = 0;
+          for (int i = 0; i < NWARP; ++i) m2 = small[i] > m2 ? small[i] : m2;
+          s_thr = m2;
+          s_nbuf = n_sel;
+        }
+        __syncthreads();
+      }
     }
   }
-  const int64_t count64 = flushed + staged;
-  const int count = (int)count64;
-  if (tid == 0) counts[row] = count;
-  const uint64_t* src = s_stage;
-  if (flushed > 0) {
-    for (int i = tid; i < staged; i += kFinThreads) krow[flushed + i] = s_stage[i];
-    src = krow;
-  }
   __syncthreads();
-  const int n_sel = nsel[row];
-  const int k = kq[row];
-  const bool rerank = rerank_on[row] != 0;
+  if (tid == 0) a.counts[row] = (int)min(count, (int64_t)INT32_MAX);
+  const int staged = s_nbuf;
+  const int k = a.kq[row];
+  const bool rerank = a.rerank_on[row] != 0;
   // Without re-rank the selection is the answer and is sorted; with re-rank
   // only the set matters and the exact keys are selected below.
-  const int got = block_select_smallest(src, count, n_sel, s_sel, hist, small, s_ctl, !rerank);
-  for (int j = tid; j < nsel_max; j += kFinThreads) sel[row * nsel_max + j] = (j < got) ? s_sel[j] : kU64Max;
+  const int got = block_select_smallest(s_stage, staged, n_sel, s_sel, hist, small, s_ctl, !rerank);
+  for (int j = tid; j < a.nsel_max; j += kFinThreads)
+    a.sel[row * a.nsel_max + j] = (j < got) ? s_sel[j] : kU64Max;
   const float inf = __int_as_float(0x7f800000);
   const uint64_t* res = s_sel;
   int kk = min(k, got);
   if (rerank) {
+    const RawT* raw = static_cast<const RawT*>(a.raw);
     for (int i = tid; i < got; i += kFinThreads) {
       const uint32_t id = (uint32_t)s_sel[i];
-      const float dist = exact_dist_lanes<RawT>(raw + (int64_t)id * dim, s_q, dim);
+      const float dist = exact_dist_lanes<RawT>(raw + (int64_t)id * a.dim, s_q, a.dim);
       s_sel[i] = make_key(dist, id);
     }
     __syncthreads();
     kk = block_select_smallest(s_sel, got, k, s_top, hist, small, s_ctl, true);
     res = s_top;
   }
-  for (int j = tid; j < k_stride; j += kFinThreads) {
+  for (int j = tid; j < a.k_stride; j += kFinThreads) {
     const uint64_t key = (j < kk) ? res[j] : kU64Max;
-    out_ids[row * k_stride + j] = (key == kU64Max) ? -1 : (int64_t)(uint32_t)key;
-    out_d[row * k_stride + j] = (key == kU64Max) ? inf : from_orderable((uint32_t)(key >> 32));
+    a.out_ids[row * a.k_stride + j] = (key == kU64Max) ? -1 : (int64_t)(uint32_t)key;
+    a.out_d[row * a.k_stride + j] = (key == kU64Max) ? inf : from_orderable((uint32_t)(key >> 32));
   }
 }
 
@@ -1366,6 +1496,7 @@ struct PrepArgs {
   int32_t* nchunks;   // plain scan: `chunk`-vector chunks of each probe (null otherwise)
   int chunk;
   int lut;            // 1: FastScan estimator (residual sums; tables for the bound)
+  float* resid;       // FastScan: the residual of each pair (D_p floats)
   int bound_cap;      // keys the shared region holds for the first bound
   int lut_offset;     // byte offset of the table region in dynamic shared memory
   int32_t* err;
@@ -1412,7 +1543,7 @@ __global__ void __launch_bounds__(128, NW4 >= 4 ? 4 : 8) prep_kernel(PrepArgs a)
   if (a.lut) {
     for (int p = warp; p < npq; p += 4)
       lut_pair<NW4>(row * a.npmax + p, row, (int)(uint32_t)dst[p], lane, a.qrot, a.cR, a.dp,
-                    a.qparams);
+                    a.qparams, a.resid);
   } else {
     // A warp per probe. The query's values are loaded once; the next
     // probe's centroid row and (grouped scans) bucket slot are requested
@@ -1504,7 +1635,6 @@ void layout_workspace(const rq_index* ix, const SearchShape& sh, Workspace& ws) 
   const int W = ix->dp / 32;
   // a multiple of 4: the finalize kernel reads the mask rows 16 bytes at a time
   ws.mwords = (std::max<int64_t>(1, ix->top_words_prefix[std::min(np, (int64_t)ix->nlist)]) + 3) & ~int64_t(3);
-  ws.cap = 32 * ws.mwords;
   Layout L;
   L.take(&ws.q, nq * ix->dim);
   L.take(&ws.qrot, nq * ix->dp);
@@ -1519,7 +1649,6 @@ void layout_workspace(const rq_index* ix, const SearchShape& sh, Workspace& ws) 
   L.take(&ws.mask, nq * ws.mwords);
   L.take(&ws.wbase, nq * np);
   L.take(&ws.wtotal, nq);
-  L.take(&ws.cand, nq * ws.cap);
   L.take(&ws.sel, nq * sh.nsel_max);
   // the per-query parameters in one region (one copy from the pinned staging
   // buffer, which has the same layout): nprobe, k, selection size, re-rank
@@ -1527,6 +1656,7 @@ void layout_workspace(const rq_index* ix, const SearchShape& sh, Workspace& ws) 
   L.take(&ws.nprobe, 4 * nq + 1);
   L.take(&ws.out_ids, nq * sh.k_stride);
   L.take(&ws.out_d, nq * sh.k_stride);
+  if (sh.lut) L.take(&ws.resid, nq * np * ix->dp);
   if (sh.mode != RQ_SCAN_PLAIN) {
     L.take(&ws.list_count, ix->nlist);
   } else {
@@ -1588,7 +1718,6 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
   rebase(ws.mask, b);
   rebase(ws.wbase, b);
   rebase(ws.wtotal, b);
-  rebase(ws.cand, b);
   rebase(ws.sel, b);
   rebase(ws.nprobe, b);
   ws.kq = ws.nprobe + nq;
@@ -1596,6 +1725,7 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
   ws.rerank_on = ws.nprobe + 3 * nq;
   rebase(ws.out_ids, b);
   rebase(ws.out_d, b);
+  if (sh.lut) rebase(ws.resid, b);
   if (sh.mode != RQ_SCAN_PLAIN) {
     rebase(ws.list_count, b);
   } else {
@@ -1660,6 +1790,7 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
     a.nchunks = grouped ? nullptr : ws.nchunks;
     a.chunk = sh.chunk;
     a.lut = sh.lut;
+    a.resid = ws.resid;
     a.err = ix->d_err;
     // the probe selection's shared region: the certified form's keys, rows,
     // candidates and query; the exact form stages the nlist keys when they fit
@@ -1687,8 +1818,7 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
     const size_t lsm = (size_t)(32 * dp + dp) * sizeof(float);
     scan_lut_kernel<NW4 <= 2 ? NW4 : 1><<<dim3((unsigned)pairs, chunks), 128, lsm, st>>>(
         ws.nchunks, ws.probe_ids, np, ws.qparams, ws.qrot, ix->cR, ix->offsets, ix->codes,
-        ix->fac, dp, ws.bound, ws.wbase, ws.mwords, ws.mask, ws.cand, nq * ws.mwords,
-        ix->d_err);
+        ix->fac, dp, ws.bound, ws.wbase, ws.mwords, ws.mask, nq * ws.mwords, ix->d_err);
   } else if (sh.mode == RQ_SCAN_PLAIN) {
     tm.mark(RQ_STAGE_SCAN, st);
     const unsigned chunks =
@@ -1698,7 +1828,7 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
     if (NW4 <= 2 && sh.chunk == 4096) kern = scan_plain_kernel<NW4, (NW4 <= 2 ? 4096 : 1024)>;
     kern<<<dim3((unsigned)pairs, chunks), 128, 0, st>>>(
         ws.nchunks, ws.probe_ids, np, ws.qparams, ws.planes, ix->offsets, ix->codes, ix->fac,
-        dp, ws.bound, ws.wbase, ws.mwords, ws.mask, ws.cand, nq * ws.mwords, ix->d_err);
+        dp, ws.bound, ws.wbase, ws.mwords, ws.mask, nq * ws.mwords, ix->d_err);
   } else {
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
@@ -1710,6 +1840,48 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
                                 sh.withhold));
     }
   }
+  // 5-6. candidate selection and exact re-rank
+  tm.mark(RQ_STAGE_SELECT, st);
+  FinalizeArgs f;
+  f.mask = ws.mask;
+  f.wtotal = ws.wtotal;
+  f.mwords = ws.mwords;
+  f.wbase = ws.wbase;
+  f.probe_ids = ws.probe_ids;
+  f.nprobe = ws.nprobe;
+  f.npmax = np;
+  f.offsets = ix->offsets;
+  f.codes = ix->codes;
+  f.fac = ix->fac;
+  f.planes = ws.planes;
+  f.qparams = ws.qparams;
+  f.resid = sh.lut ? ws.resid : nullptr;
+  f.dp = dp;
+  f.ids = ix->ids;
+  f.n_slots = ix->n;
+  f.err = ix->d_err;
+  f.counts = ws.counts;
+  f.nsel = ws.nsel;
+  f.kq = ws.kq;
+  f.rerank_on = ws.rerank_on;
+  f.nsel_max = sh.nsel_max;
+  f.sel = ws.sel;
+  f.raw = ix->raw;
+  f.q = ws.q;
+  f.dim = ix->dim;
+  f.k_stride = sh.k_stride;
+  // staging: room for n_sel keys plus a step of survivors, with more for
+  // large selections (whose first bound lets more survive). With nprobe,
+  // n_sel and k at most 4096 and D at most 2048 this is at most 217 KB.
+  f.lay = FinalizeLayout{next_pow2_host(sh.nsel_max),
+                         next_pow2_host(std::min<int64_t>(sh.k_stride, kMaxSelect)),
+                         sh.nsel_max > 512 ? 8192 : 4096, np, ix->dim};
+  f.out_ids = ws.out_ids;
+  f.out_d = ws.out_d;
+  const size_t smem = f.lay.bytes();
+  auto kern = ix->raw_dtype == RQ_U8 ? finalize_kernel<uint8_t, NW4> : finalize_kernel<float, NW4>;
+  RQ_TRY(allow_dynamic_smem((const void*)kern, 220 * 1024));
+  kern<<<(unsigned)nq, kFinThreads, smem, st>>>(f);
   return RQ_OK;
 }
 
@@ -1751,27 +1923,6 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
     default:
       return fail(RQ_ERR_NOT_IMPLEMENTED, "padded dimension " + std::to_string(dp) +
                                               " has no scan kernel (built: 128..1024, 1536, 2048)");
-  }
-  // 5-6. candidate selection and exact re-rank
-  tm.mark(RQ_STAGE_SELECT, st);
-  {
-    // candidates staged in shared memory: more for large selections (whose
-    // first bound lets more survive), fewer to keep more blocks per SM
-    const FinalizeLayout lay{next_pow2_host(sh.nsel_max), next_pow2_host(sh.k_stride),
-                             sh.nsel_max > 512 ? 8192 : 4096, ix->dim};
-    const size_t smem = lay.bytes();
-    RQ_TRY(allow_dynamic_smem((const void*)finalize_kernel<uint8_t>, 200 * 1024));
-    RQ_TRY(allow_dynamic_smem((const void*)finalize_kernel<float>, 200 * 1024));
-    if (ix->raw_dtype == RQ_U8)
-      finalize_kernel<uint8_t><<<(unsigned)nq, kFinThreads, smem, st>>>(
-          ws.mask, ws.wtotal, ws.mwords, ws.cand, ix->ids, ix->n, ix->d_err, ws.counts, ws.nsel, ws.kq, ws.rerank_on,
-          sh.nsel_max, ws.sel, static_cast<const uint8_t*>(ix->raw), ws.q, ix->dim, sh.k_stride, lay,
-          ws.out_ids, ws.out_d);
-    else
-      finalize_kernel<float><<<(unsigned)nq, kFinThreads, smem, st>>>(
-          ws.mask, ws.wtotal, ws.mwords, ws.cand, ix->ids, ix->n, ix->d_err, ws.counts, ws.nsel, ws.kq, ws.rerank_on,
-          sh.nsel_max, ws.sel, static_cast<const float*>(ix->raw), ws.q, ix->dim, sh.k_stride, lay,
-          ws.out_ids, ws.out_d);
   }
   tm.mark(RQ_STAGE_RERANK, st);
   tm.mark(RQ_STAGE_COUNT, st);
