@@ -122,10 +122,15 @@ def parse(argv=None):
     ap.add_argument("--setting", default=None, help="scale,n_rerank: skip the sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--no-secondary", action="store_true", help="skip the SIFT1M-shaped key")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the SIFT1M-shaped and high-dimensional keys")
+    ap.add_argument("--no-highdim", action="store_true", help="skip the high-dimensional key")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--cpu-leg", action="store_true",
                     help="(internal) the oracle's CPU leg, run in its own CUDA-free process")
+    ap.add_argument("--profile-schedule", action="store_true",
+                    help="only build the skewed index and run --warmup + --steps cycles of the "
+                         "headline schedule in the tensor-core form, for the launch list")
     ap.add_argument("--profile", default=None,
                     help="only build the skewed index and run --warmup + --steps searches of "
                          "one case (nq,nprobe,mode[,chunk[,n_rerank]]), for ncu captures")
@@ -774,6 +779,66 @@ def run_sift1m(rq, args, rank, world, pg, dev, flush, stream):
     return res
 
 
+def run_highdim(rq, args, rank, world, pg, dev, flush, stream):
+    """Secondary key: the high-dimensional recipe (1M x 960, D_p 1024). The
+    tensor-core scan is built for D_p = 128 and the FastScan form for D_p <=
+    256, so the popcount forms run here: the plain scan and the streaming
+    grouped scan, each timed."""
+    import torch
+
+    wl = W.WORKLOADS["highdim"]
+    mix = wl["mix"]
+    t0 = time.perf_counter()
+    x = mix.base(wl["n"])
+    q = mix.queries(wl["nq"])
+    gen_s = time.perf_counter() - t0
+    x_dev = torch.from_numpy(x).to(dev)
+    del x
+    q_dev = torch.from_numpy(q).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ix = rq.rq_build(x_dev, wl["nlist"], seed=0, kmeans_iters=wl["iters"])
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    nq, k, nrr = wl["nq"], 10, wl["n_rerank"]
+    kth = exact_kth(x_dev, q_dev, k, False)
+    ids = torch.empty((nq, k), dtype=torch.int64, device=dev)
+    dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    res = {"workload": f"highdim-shaped: N={wl['n']} D={mix.dim} (D_p {ix.stats()['dim_pad']}) "
+                       f"float32, 512-component mixture with per-dimension variance U(0.5, 2), "
+                       f"nlist={wl['nlist']}, one batch of {nq} queries, k={k}, n_rerank={nrr}, "
+                       f"B_q=4",
+           "build_s": round(build_s, 3), "gen_s": round(gen_s, 1), "by_nprobe": {}}
+    for npb in wl["nprobe"]:
+        row = {}
+        for name, mode in (("plain", rq.RQ_SCAN_PLAIN), ("grouped", rq.RQ_SCAN_GROUPED)):
+            for _ in range(3):
+                ix.search(q_dev, npb, k, nrr, out_ids=ids, out_dist=dist, scan_mode=mode,
+                          use_graph=True, stream=stream)
+            steps = max(5, args.steps // 2)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(steps)]
+            torch.cuda.synchronize()
+            for i in range(steps):
+                flush.zero_()
+                evs[i][0].record(stream)
+                ix.search(q_dev, npb, k, nrr, out_ids=ids, out_dist=dist, scan_mode=mode,
+                          use_graph=True, stream=stream)
+                evs[i][1].record(stream)
+            torch.cuda.synchronize()
+            t = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+            stt = {}
+            ix.search(q_dev, npb, k, nrr, out_ids=ids, out_dist=dist, scan_mode=mode,
+                      stream=stream, stage_times=stt)
+            torch.cuda.synchronize()
+            row[name] = {"qps": round(steps * nq / t, 1),
+                         "stage_ms": {a: round(b, 4) for a, b in stt.items()}}
+        row["recall_at_10"] = round(recall_of(x_dev, q_dev, ids, kth, k), 4)
+        res["by_nprobe"][str(npb)] = row
+    ix.free()
+    return res
+
+
 # ---------------------------------------------------------------- CPU oracle
 def cpu_model() -> str:
     try:
@@ -951,6 +1016,43 @@ def run_profile(args):
                       "device_error": ix.device_error()}), flush=True)
 
 
+def run_profile_schedule(args):
+    """Build the skewed index, then --warmup + --steps cycles of the headline
+    schedule (setting --setting, default 2,2000) in the tensor-core form with
+    graphs, as the timed region runs them, and nothing else: the command
+    behind the launch-list summary."""
+    import torch
+
+    import paper_2605_16007_gb300 as rq
+
+    rq.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    wl = W.WORKLOADS["skewed"]
+    x_dev = torch.from_numpy(wl["mix"].base(args.n or wl["n"])).to(dev)
+    ix = rq.rq_build(x_dev, wl["nlist"], seed=0, kmeans_iters=wl["iters"], train_size=SKEW_TRAIN)
+    del x_dev
+    scale, nrr = (int(v) for v in (args.setting or "2,2000").split(","))
+    npb, kk, nr = skew_params(SKEW_POOL, scale, nrr, ix.stats()["nlist"])
+    q_dev = torch.from_numpy(wl["mix"].queries(SKEW_POOL)).to(dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    kmax = 100
+    out = {}
+    for b, row in skew_schedule((args.warmup + args.steps) * len(SKEW_BATCHES)):
+        sl = slice(row, row + b)
+        if b not in out:
+            out[b] = (torch.empty((b, kmax), dtype=torch.int64, device=dev),
+                      torch.empty((b, kmax), dtype=torch.float32, device=dev))
+        flush.zero_()
+        ix.search_mixed(q_dev[sl].contiguous(), np.ascontiguousarray(npb[sl]),
+                        np.ascontiguousarray(kk[sl]), np.ascontiguousarray(nr[sl]), k_stride=kmax,
+                        out_ids=out[b][0], out_dist=out[b][1], scan_mode=rq.RQ_SCAN_MMA,
+                        use_graph=True, stream=stream)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_schedule": [scale, nrr], "cycles": args.warmup + args.steps,
+                      "device_error": ix.device_error()}), flush=True)
+
+
 # ---------------------------------------------------------------- main
 def run_ours(args, rank, world, local, pg):
     import torch
@@ -965,6 +1067,9 @@ def run_ours(args, rank, world, local, pg):
     res = run_skewed(rq, args, rank, world, local, pg, dev, flush, stream)
     if not args.no_secondary:
         res["secondary"] = {"sift1m": run_sift1m(rq, args, rank, world, pg, dev, flush, stream)}
+        if not args.no_highdim:
+            res["secondary"]["highdim"] = run_highdim(rq, args, rank, world, pg, dev, flush,
+                                                      stream)
     return res
 
 
@@ -972,6 +1077,9 @@ def main():
     args = parse()
     if args.cpu_leg:
         print(json.dumps(cpu_leg(args)), flush=True)
+        return
+    if args.profile_schedule:
+        run_profile_schedule(args)
         return
     if args.profile:
         run_profile(args)

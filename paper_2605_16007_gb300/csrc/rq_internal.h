@@ -111,7 +111,10 @@ struct Workspace {
   float* out_d = nullptr;       // nq x k_stride
   // grouped scans: (query, probe) pairs bucketed by list
   int32_t* list_count = nullptr;  // nlist: pairs probing each list
-  int32_t* list_pairs = nullptr;  // nlist x nq: pair ids (q * npmax + p) per list
+  int64_t* qwrow = nullptr;       // nlist x nq (stride rounded up to 4, +2): per bucket slot,
+                                  // the pair's first mask index
+  float* qtau = nullptr;          // nlist x nq (same stride, +4): per bucket slot, the bound
+                                  // as a float32 threshold
   int32_t* nchunks = nullptr;     // plain scan: nq x npmax chunk counts
   uint8_t* qdig = nullptr;        // nlist x nq x D_p: per-list buckets of FP8 query digits
   float4* qpb = nullptr;          // nlist x nq (+2): per-list buckets of {vl, delta, nq2, -Sq},

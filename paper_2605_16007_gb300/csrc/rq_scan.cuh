@@ -44,6 +44,14 @@ __device__ __forceinline__ float estimate_regs(const uint4 (&code)[NW4], int pc,
 }
 
 
+// The bound as a float32 threshold. The estimates compared with it are
+// never -0 or NaN, and neither is a bound taken from them, so
+// orderable(d) <= tau exactly when d <= tau_threshold(tau) (all ones: no
+// bound, +inf).
+__device__ __forceinline__ float tau_threshold(uint32_t tau) {
+  return tau == kU32Max ? __int_as_float(0x7f800000) : from_orderable(tau);
+}
+
 // Scan output without atomics: survivor masks only. The vectors of a probed
 // list are cut into 32-vector words; word w of probe p of query q has the
 // fixed mask index x = q * mwords + wbase[q, p] + w (bit i set: vector

@@ -157,7 +157,6 @@ __device__ __forceinline__ void quantize_pair(int64_t pair, int64_t q, int c, in
                                               const float (&cv)[4 * NW4], int64_t nq, int dp,
                                               float4* __restrict__ qparams,
                                               uint32_t* __restrict__ planes,
-                                              int32_t* __restrict__ list_pairs,
                                               uint8_t* __restrict__ qdb,
                                               float4* __restrict__ qpb,
                                               uint8_t* __restrict__ qrec, uint64_t* slot_out) {
@@ -217,18 +216,15 @@ __device__ __forceinline__ void quantize_pair(int64_t pair, int64_t q, int c, in
     const float4 qp = make_float4(vl, delta, nq2, __int_as_float(sq));
     qparams[pair] = qp;
     if (rec) *reinterpret_cast<float4*>(rec + 4 * W) = qp;
-    if (list_pairs) {
-      list_pairs[(int64_t)c * nq + slot] = (int32_t)pair;
-      if (qpb) {
-        // The tensor-core scan's copy, interleaved by slot couples for its
-        // packed float2 arithmetic: slots 2k, 2k + 1 of a bucket hold
-        // {vl, vl', delta, delta'} {nq2, nq2', -Sq, -Sq'} (Sq as a float).
-        float* cp = reinterpret_cast<float*>(qpb + (int64_t)c * nq + (slot & ~1)) + (slot & 1);
-        cp[0] = vl;
-        cp[2] = delta;
-        cp[4] = nq2;
-        cp[6] = -(float)sq;
-      }
+    if (qpb) {
+      // The tensor-core scan's copy, interleaved by slot couples for its
+      // packed float2 arithmetic: slots 2k, 2k + 1 of a bucket hold
+      // {vl, vl', delta, delta'} {nq2, nq2', -Sq, -Sq'} (Sq as a float).
+      float* cp = reinterpret_cast<float*>(qpb + (int64_t)c * nq + (slot & ~1)) + (slot & 1);
+      cp[0] = vl;
+      cp[2] = delta;
+      cp[4] = nq2;
+      cp[6] = -(float)sq;
     }
   }
 }
@@ -1208,6 +1204,7 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(FinalizeArgs a) {
 // keys in dst, ascending, and return how many were found; the distance is
 // always the fixed-order float32 one (the terms (q'_d - c_d)^2 added in
 // increasing d, no fused multiply-add).
+constexpr int kPrepThreads = 256;  // threads of the per-query preparation block
 constexpr int kProbeStageKeys = 4096;
 constexpr int kProbeCandCap = 1024;
 constexpr int kProbeRowStage = 32;  // candidates whose rows are staged in shared memory
@@ -1279,7 +1276,7 @@ __device__ inline int probe_select_certified(const float* __restrict__ g,
   const int keys_area = (max(nlist, kProbeRowStage * dp / 2) + 1) & ~1;
   int* cand = reinterpret_cast<int*>(region + keys_area);
   float* qs = reinterpret_cast<float*>(cand + kProbeCandCap);
-  __shared__ float s_red[4];
+  __shared__ float s_red[32];
   float part = 0.0f;
   for (int d = tid; d < dp; d += blockDim.x) {
     const float v = qrot[row * dp + d];
@@ -1290,7 +1287,8 @@ __device__ inline int probe_select_certified(const float* __restrict__ g,
   for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
   if (lane == 0) s_red[warp] = part;
   __syncthreads();
-  const float qn = s_red[0] + s_red[1] + s_red[2] + s_red[3];
+  float qn = 0.0f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) qn += s_red[w];
   const float escale = 16.0f * (float)dp * 5.9604645e-8f;
   const float* grow = g + row * nlist;
 #pragma unroll 8
@@ -1395,7 +1393,7 @@ __device__ inline void probe_outputs(const uint64_t* dst, int got, int np, int64
 }
 
 // First bound (Section 3.3.3): lists in probe order give the first
-// bound_window(n_sel) candidates, estimated by all 128 threads (each
+// bound_window(n_sel) candidates, estimated by all kPrepThreads threads (each
 // thread's codes loaded before its estimates) and offered to the streaming
 // n-th smallest in `buf` (shared memory for `cap` keys); the bound is the
 // n_sel-th smallest orderable estimate (all ones when the query has fewer
@@ -1425,12 +1423,12 @@ __device__ inline uint32_t bound_block(int64_t qi, int npmax, int npq, int n_sel
     for (int i = tid; i < 4 * W; i += blockDim.x) s_pl[i] = planes[pair * 4 * W + i];
     __syncthreads();
     const float4 qp = qparams[pair];
-    for (int base = 0; base < m; base += 128 * RB) {
+    for (int base = 0; base < m; base += kPrepThreads * RB) {
       uint4 code[RB][NW4];
       float2 fv[RB];
 #pragma unroll
       for (int r = 0; r < RB; ++r) {
-        const int i = base + tid + 128 * r;
+        const int i = base + tid + kPrepThreads * r;
         if (i < m) {
           const uint4* cp = reinterpret_cast<const uint4*>(codes + (lo + i) * (dp / 8));
 #pragma unroll
@@ -1441,7 +1439,7 @@ __device__ inline uint32_t bound_block(int64_t qi, int npmax, int npq, int n_sel
       const uint32_t thr = ks.thr;
 #pragma unroll
       for (int r = 0; r < RB; ++r) {
-        const int i = base + tid + 128 * r;
+        const int i = base + tid + kPrepThreads * r;
         uint32_t key = 0;
         if (i < m) {
           int pc = 0;
@@ -1454,14 +1452,14 @@ __device__ inline uint32_t bound_block(int64_t qi, int npmax, int npq, int n_sel
         kth_offer(&ks, buf, thr, key, i < m);
       }
       __syncthreads();
-      kth_maybe_compact(&ks, buf, cap, 128 * RB, n_sel, hist, small, ctl);
+      kth_maybe_compact(&ks, buf, cap, kPrepThreads * RB, n_sel, hist, small, ctl);
     }
     taken += m;
   }
   return kth_result(&ks, buf, taken, n_sel, hist, small, ctl);
 }
 
-// Query preparation, one block of 128 threads per query: probe selection,
+// Query preparation, one block of kPrepThreads threads per query: probe selection,
 // then the quantisation of each probed residual (a warp per probe), then the
 // first bound. Shared memory: the probe keys (next_pow2(np)), then a region
 // used first by the probe selection (nlist keys, plus the certified form's
@@ -1486,7 +1484,10 @@ struct PrepArgs {
   float4* qparams;
   uint32_t* planes;
   int32_t* list_count;
-  int32_t* list_pairs;
+  int64_t* qwrow;     // tensor-core scan: per bucket slot, first mask index
+  float* qtau;        // ... and the bound as a float32 threshold
+  int64_t qstride;    // bucket stride of qwrow / qtau: nq rounded up to 4 (16-byte copies)
+  int64_t mwords;
   uint8_t* qdb;
   float4* qpb;
   uint8_t* qrec;      // streaming scan: per-list pair records (null otherwise)
@@ -1503,7 +1504,7 @@ struct PrepArgs {
 };
 
 template <int NW4>
-__global__ void __launch_bounds__(128, NW4 >= 4 ? 4 : 8) prep_kernel(PrepArgs a) {
+__global__ void __launch_bounds__(kPrepThreads, NW4 >= 4 ? 2 : 4) prep_kernel(PrepArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ int hist[256];
   __shared__ uint64_t small[32];
@@ -1541,7 +1542,7 @@ __global__ void __launch_bounds__(128, NW4 >= 4 ? 4 : 8) prep_kernel(PrepArgs a)
   // reader of the distances above is done after this barrier)
   __syncthreads();
   if (a.lut) {
-    for (int p = warp; p < npq; p += 4)
+    for (int p = warp; p < npq; p += kPrepThreads / 32)
       lut_pair<NW4>(row * a.npmax + p, row, (int)(uint32_t)dst[p], lane, a.qrot, a.cR, a.dp,
                     a.qparams, a.resid);
   } else {
@@ -1563,16 +1564,16 @@ __global__ void __launch_bounds__(128, NW4 >= 4 ? 4 : 8) prep_kernel(PrepArgs a)
     // (no look-ahead above D_p 1024, where the registers run out)
     constexpr bool kAhead = NW4 <= 8;
     if (kAhead && warp < npq) request(warp);
-    for (int p = warp; p < npq; p += 4) {
+    for (int p = warp; p < npq; p += kPrepThreads / 32) {
       if (!kAhead) request(p);
       float cur[PER];
 #pragma unroll
       for (int i = 0; i < PER; ++i) cur[i] = cv[i];
       const int cc = c;
       const int sl = __shfl_sync(0xffffffffu, slot, 0);
-      if (kAhead && p + 4 < npq) request(p + 4);
+      if (kAhead && p + kPrepThreads / 32 < npq) request(p + kPrepThreads / 32);
       quantize_pair<NW4>(row * a.npmax + p, row, cc, sl, lane, qv, cur, a.nq, a.dp, a.qparams,
-                         a.planes, a.list_pairs, a.qdb, a.qpb, a.qrec,
+                         a.planes, a.qdb, a.qpb, a.qrec,
                          &dst[p]);
     }
   }
@@ -1592,6 +1593,16 @@ __global__ void __launch_bounds__(128, NW4 >= 4 ? 4 : 8) prep_kernel(PrepArgs a)
                              a.codes, a.fac, a.dp, bk, a.bound_cap, hist, small, ctl);
   }
   if (tid == 0) a.bound[row] = tau;
+  if (a.qwrow) {
+    // each pair's first mask index and bound, at its bucket slot
+    const float tf = tau_threshold(tau);
+    for (int p = tid; p < npq; p += blockDim.x) {
+      const uint64_t e = dst[p];
+      const int64_t c = (uint32_t)e, slot = (uint32_t)(e >> 32);
+      a.qwrow[c * a.qstride + slot] = row * a.mwords + a.wbase[row * a.npmax + p];
+      a.qtau[c * a.qstride + slot] = tf;
+    }
+  }
   if (a.qrec) {
     // the rest of each pair record: query, first mask word, bound
     const int rb = pair_rec_bytes(a.dp);
@@ -1664,7 +1675,10 @@ void layout_workspace(const rq_index* ix, const SearchShape& sh, Workspace& ws) 
   }
   if (sh.mode == RQ_SCAN_GROUPED) L.take(&ws.qrec, (int64_t)ix->nlist * nq * pair_rec_bytes(ix->dp));
   if (sh.mode == RQ_SCAN_MMA) {
-    L.take(&ws.list_pairs, (int64_t)ix->nlist * nq);
+    // bucket stride rounded up to 4 slots, so that every group's copies
+    // start 16-byte aligned; + what a group's copy reads past the end
+    L.take(&ws.qwrow, (int64_t)ix->nlist * ((nq + 3) & ~int64_t(3)) + 2);
+    L.take(&ws.qtau, (int64_t)ix->nlist * ((nq + 3) & ~int64_t(3)) + 4);
     L.take(&ws.qdig, (int64_t)ix->nlist * nq * ix->dp);
     L.take(&ws.qpb, (int64_t)ix->nlist * nq + 2);  // + a couple read past the last bucket
   }
@@ -1733,7 +1747,8 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
   }
   if (sh.mode == RQ_SCAN_GROUPED) rebase(ws.qrec, b);
   if (sh.mode == RQ_SCAN_MMA) {
-    rebase(ws.list_pairs, b);
+    rebase(ws.qwrow, b);
+    rebase(ws.qtau, b);
     rebase(ws.qdig, b);
     rebase(ws.qpb, b);
   }
@@ -1780,7 +1795,10 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
     a.qparams = ws.qparams;
     a.planes = ws.planes;
     a.list_count = grouped ? ws.list_count : nullptr;
-    a.list_pairs = sh.mode == RQ_SCAN_MMA ? ws.list_pairs : nullptr;
+    a.qwrow = sh.mode == RQ_SCAN_MMA ? ws.qwrow : nullptr;
+    a.qtau = ws.qtau;
+    a.qstride = (nq + 3) & ~int64_t(3);
+    a.mwords = ws.mwords;
     a.qdb = sh.mode == RQ_SCAN_MMA ? ws.qdig : nullptr;
     a.qpb = sh.mode == RQ_SCAN_MMA ? ws.qpb : nullptr;
     a.qrec = sh.mode == RQ_SCAN_GROUPED ? ws.qrec : nullptr;
@@ -1799,8 +1817,12 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
                       15) & ~(size_t)15) + kProbeCandCap * 4 + (size_t)dp * 4
                   : (ix->nlist <= kProbeStageKeys ? (size_t)ix->nlist * 8 : 0);
     // ... and then the first bound's keys: n_sel plus two rounds of
-    // estimates (at most 512 keys each) fit with room to spare
-    const size_t bound_bytes = (size_t)4 * (2 * (size_t)sh.nsel_max + 1024);
+    // estimates (at most 1024 keys each), or the whole window when it is
+    // small (no compaction then), up to 8192 keys
+    const size_t bound_keys =
+        std::max<size_t>(2 * (size_t)sh.nsel_max + 2048,
+                         std::min<size_t>((size_t)bound_window(sh.nsel_max) + 1024, 8192));
+    const size_t bound_bytes = 4 * bound_keys;
     const size_t region = (std::max<size_t>({stage, bound_bytes, 64}) + 15) & ~(size_t)15;
     a.bound_cap = (int)(region / 4);
     size_t smem = (size_t)std::max(2, next_pow2_host(np)) * 8 + region;
@@ -1808,7 +1830,7 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
     a.lut_offset = (int)smem;
     if (sh.lut) smem += (size_t)(32 * dp + dp) * sizeof(float);
     RQ_TRY(allow_dynamic_smem((const void*)prep_kernel<NW4>, 200 * 1024));
-    prep_kernel<NW4><<<(unsigned)nq, 128, smem, st>>>(a);
+    prep_kernel<NW4><<<(unsigned)nq, kPrepThreads, smem, st>>>(a);
   }
   tm.mark(RQ_STAGE_BOUND, st);
   tm.mark(RQ_STAGE_WORKLIST, st);
