@@ -128,8 +128,8 @@ typedef enum rq_stage {
   RQ_STAGE_WORKLIST = 4, /* (pairs are grouped by list inside
                             RQ_STAGE_QUANTIZE; reads 0) */
   RQ_STAGE_SCAN = 5,     /* the code scan */
-  RQ_STAGE_SELECT = 6,   /* candidate selection fused with the exact re-rank */
-  RQ_STAGE_RERANK = 7,   /* (runs inside RQ_STAGE_SELECT; reads 0) */
+  RQ_STAGE_SELECT = 6,   /* candidate collection: survivor keys from the masks */
+  RQ_STAGE_RERANK = 7,   /* selection of the n_rerank smallest and exact re-rank */
   RQ_STAGE_COUNT = 8
 } rq_stage;
 

@@ -103,6 +103,8 @@ struct Workspace {
   int32_t* wbase = nullptr;     // nq x npmax: first mask word of each probe
   int32_t* wtotal = nullptr;    // nq: mask words of the query's probes
   uint64_t* sel = nullptr;      // nq x nsel_max
+  uint64_t* keys = nullptr;     // nq x kcap survivor keys (collection -> selection)
+  int32_t* kcount = nullptr;    // nq: survivors of each query
   int32_t* nprobe = nullptr;    // nq
   int32_t* kq = nullptr;        // nq
   int32_t* nsel = nullptr;      // nq
@@ -123,6 +125,7 @@ struct Workspace {
   uint8_t* qrec = nullptr;        // nlist x nq pair records of the streaming scan
                                   // (pair_rec_bytes(D_p) each)
   int64_t mwords = 0;             // mask words per query
+  int64_t kcap = 0;               // survivor keys each query's buffer holds
 };
 
 struct Plan {

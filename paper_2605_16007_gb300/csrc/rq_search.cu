@@ -894,47 +894,58 @@ __device__ __forceinline__ float exact_dist_lanes(const RawT* __restrict__ x,
 }
 
 // ---------------------------------------------------------------------------
-// One warp per query: probe selection, first bound, and candidate selection
-// fused with the exact re-rank. Warps only synchronise with themselves, so a
-// block of several warps serves several queries at once.
-// ---------------------------------------------------------------------------
-
-// ---------------------------------------------------------------------------
-// Finalize: one block of kFinThreads per query. The survivors are read from
-// the scan's masks, their estimates recomputed (every scan form computes the
-// popcount form's float32 value, and the FastScan form's direct sums equal
-// its table sums), the n_sel smallest (estimate, row id) keys kept, then
-// gathered and re-ranked exactly, and the final k selected.
+// Candidate collection, selection and re-rank (three kernels per search).
 //
-// Masks go in rounds of kFinRoundWords words; thread t holds
-// kFinWordsPerThread consecutive words of the round (four 16-byte loads in
-// flight together). A block scan of the per-thread counts gives each
-// nonzero word a descriptor (position of its first survivor, word offset)
-// and its mask word in shared memory. The survivors are then taken a thread
-// each, up to four at a time with all their loads in flight: the
-// descriptor by binary search, the bit by its rank in the word, the probe by
-// binary search over the probes' first words.
+// The survivors are read from the scan's masks and their estimates
+// recomputed (every scan form computes the popcount form's float32 value,
+// and the FastScan form's direct sums equal its table sums), paired with
+// their row ids as (estimate, row id) keys.
 //
-// Selection streams: a key below the threshold goes to the staging area;
-// when that could overflow in the next step, the n_sel smallest staged keys
-// are kept and the threshold becomes the largest of them. Keys are distinct
-// (one per vector), so a dropped key is above n_sel kept ones and is not
-// among the n_sel smallest of all.
+// 1. collect_kernel: one block per (query, round of kFinRoundWords mask
+//    words), the query in x. Thread t holds kFinWordsPerThread consecutive words of the round
+//    (four 16-byte loads in flight together); a block scan of the per-thread
+//    counts gives each nonzero word a descriptor (position of its first
+//    survivor, word offset) and its mask word in shared memory. The survivors
+//    are then taken a thread each, up to four at a time with all their loads
+//    in flight: the descriptor by binary search, the bit by its rank in the
+//    word, the probe by binary search over the probes' first words. The block
+//    reserves room in its query's key buffer with one atomic and writes the
+//    keys there (in no fixed order; the selection does not depend on it).
+// 2. select_kernel: one block per query selects the n_sel smallest keys from
+//    the buffer (block radix selection), gathers and re-ranks them exactly and
+//    selects the final k.
+// 3. finalize_kernel: only for a query with more survivors than its buffer
+//    holds. It reads the masks again in rounds and keeps the n_sel smallest
+//    keys in shared memory by a streaming threshold: a key below the
+//    threshold goes to the staging area; when that could overflow in the next
+//    step, the n_sel smallest staged keys are kept and the threshold becomes
+//    the largest of them. Keys are distinct (one per vector), so a dropped key
+//    is above n_sel kept ones and is not among the n_sel smallest of all.
 // ---------------------------------------------------------------------------
 constexpr int kFinThreads = 256;
 constexpr int kFinWordsPerThread = 16;                            // four 16-byte mask loads
 constexpr int kFinRoundWords = kFinThreads * kFinWordsPerThread;  // mask words per round
 constexpr int kFinStepMax = kFinThreads * 4;                      // survivors per step, at most
+constexpr int64_t kKeyCap = 65536;                                // key buffer per query
 
-// Shared memory, in order: selection (P keys), top-k (PK keys), staging (S
-// keys), probe slot bases (NP int64), bucket (32 keys), histogram (256
-// ints), descriptors and mask words (kFinRoundWords each), probe first words
-// (NP ints), query row (dim floats).
+// Shared memory of the streaming finalize, in order: selection (P keys),
+// top-k (PK keys), staging (S keys), probe slot bases (NP int64), bucket (32
+// keys), histogram (256 ints), descriptors and mask words (kFinRoundWords
+// each), probe first words (NP ints), query row (dim floats).
 struct FinalizeLayout {
   int P, PK, S, NP, dim;
   __host__ __device__ int bytes() const {
     return (P + PK + S + NP + 32) * 8 + 256 * 4 + 2 * kFinRoundWords * 4 +
            ((NP * 4 + 15) & ~15) + ((dim * 4 + 15) & ~15);
+  }
+  // the collection kernel: probe slot bases, descriptors and words, probe
+  // first words
+  __host__ __device__ int collect_bytes() const {
+    return NP * 8 + 2 * kFinRoundWords * 4 + ((NP * 4 + 15) & ~15);
+  }
+  // the selection kernel: selection, top-k, bucket, histogram, query row
+  __host__ __device__ int select_bytes() const {
+    return (P + PK + 32) * 8 + 256 * 4 + ((dim * 4 + 15) & ~15);
   }
 };
 
@@ -968,12 +979,252 @@ struct FinalizeArgs {
   FinalizeLayout lay;
   int64_t* out_ids;
   float* out_d;
+  uint64_t* keys;            // nq x kcap survivor keys (collect -> select)
+  int32_t* kcount;           // nq: survivors of each query (cleared before collect)
+  int64_t kcap;
 };
+
+// One round of a query's mask words from word c0: the descriptors and words
+// of the nonzero words into shared memory; every thread gets the round's
+// survivor and descriptor counts. All threads call it.
+__device__ inline void fin_round(const uint4* __restrict__ mrow4, int T, int c0,
+                                 uint32_t* s_desc, uint32_t* s_dword, int* s_warp,
+                                 int& tot_keys, int& tot_desc) {
+  constexpr int NWARP = kFinThreads / 32;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wfirst = c0 + tid * kFinWordsPerThread;
+  uint32_t w[kFinWordsPerThread];
+#pragma unroll
+  for (int j = 0; j < kFinWordsPerThread / 4; ++j) {
+    const uint4 v = (wfirst + 4 * j < T) ? mrow4[(wfirst >> 2) + j] : make_uint4(0, 0, 0, 0);
+    w[4 * j] = v.x;
+    w[4 * j + 1] = v.y;
+    w[4 * j + 2] = v.z;
+    w[4 * j + 3] = v.w;
+  }
+  int c = 0, nz = 0;
+#pragma unroll
+  for (int e = 0; e < kFinWordsPerThread; ++e) {
+    if (wfirst + e >= T) w[e] = 0u;  // words past the query's last probed list
+    const int n = __popc(w[e]);
+    c += n;
+    nz += n != 0;
+  }
+  // one scan of both counts: survivors (< 2^18 per round) in the low 18
+  // bits, nonzero words (<= kFinRoundWords) above
+  const int v = c | (nz << 18);
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  __syncthreads();  // the previous round is done with s_warp and the descriptors
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  int ex = incl - v, tot = 0;
+#pragma unroll
+  for (int i = 0; i < NWARP; ++i) {
+    const int sw = s_warp[i];
+    if (i < warp) ex += sw;
+    tot += sw;
+  }
+  tot_keys = tot & 0x3FFFF;
+  tot_desc = tot >> 18;
+  int p = ex & 0x3FFFF, d = ex >> 18;
+#pragma unroll
+  for (int e = 0; e < kFinWordsPerThread; ++e) {
+    const int n = __popc(w[e]);
+    if (n) {
+      s_desc[d] = ((uint32_t)p << 12) | (uint32_t)(tid * kFinWordsPerThread + e);
+      s_dword[d] = w[e];
+      ++d;
+    }
+    p += n;
+  }
+  __syncthreads();
+}
+
+// Up to PT survivors of the round (positions j0 + tid + u kFinThreads) as
+// keys: have[u] false past the round's survivors (or for a slot out of range
+// in a checked build).
+template <int NW4, int PT>
+__device__ inline void fin_keys(const FinalizeArgs& a, int64_t row, int c0, int j0, int tot_keys,
+                                int tot_desc, const uint32_t* s_desc, const uint32_t* s_dword,
+                                const int* s_wb, const int64_t* s_base, int npq,
+                                bool (&have)[PT], uint64_t (&key)[PT]) {
+  constexpr int W = 4 * NW4;
+  int64_t slot[PT], pair[PT];
+#pragma unroll
+  for (int u = 0; u < PT; ++u) {
+    const int j = j0 + threadIdx.x + u * kFinThreads;
+    have[u] = j < tot_keys;
+    slot[u] = 0;
+    pair[u] = row * a.npmax;
+    if (have[u]) {
+      int lo = 0, hi = tot_desc - 1;  // the last descriptor whose first survivor is <= j
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((int)(s_desc[mid] >> 12) <= j) lo = mid; else hi = mid - 1;
+      }
+      const uint32_t dsc = s_desc[lo];
+      const int word = c0 + (int)(dsc & 4095u);
+      uint32_t mw = s_dword[lo];  // the survivor's bit: drop the lower set bits
+      for (int r = j - (int)(dsc >> 12); r > 0; --r) mw &= mw - 1u;
+      const int bit = __ffs(mw) - 1;
+      int plo = 0, phi = npq - 1;  // the probe holding `word`
+      while (plo < phi) {
+        const int mid = (plo + phi + 1) >> 1;
+        if (s_wb[mid] <= word) plo = mid; else phi = mid - 1;
+      }
+      slot[u] = s_base[plo] + (int64_t)(word - s_wb[plo]) * 32 + bit;
+      pair[u] = row * a.npmax + plo;
+      if (!index_ok(slot[u], a.n_slots, a.err)) have[u] = false;
+    }
+  }
+  // every load of the step in flight: codes, factors, ids, parameters
+  uint4 code[PT][NW4];
+  float2 fv[PT];
+  uint32_t rid[PT];
+  float4 qp[PT];
+#pragma unroll
+  for (int u = 0; u < PT; ++u) {
+    if (have[u]) {
+      const uint4* cp = reinterpret_cast<const uint4*>(a.codes + slot[u] * (a.dp / 8));
+#pragma unroll
+      for (int x = 0; x < NW4; ++x) code[u][x] = __ldg(cp + x);
+      fv[u] = __ldg(a.fac + slot[u]);
+      rid[u] = __ldg(a.ids + slot[u]);
+      qp[u] = __ldg(a.qparams + pair[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < PT; ++u) {
+    key[u] = kU64Max;
+    if (have[u]) {
+      float d;
+      if (a.resid) {
+        d = estimate_lut_direct<NW4>(code[u], a.resid + pair[u] * a.dp, fv[u], qp[u].z, qp[u].w);
+      } else {
+        int pc = 0;
+#pragma unroll
+        for (int x = 0; x < NW4; ++x)
+          pc += __popc(code[u][x].x) + __popc(code[u][x].y) + __popc(code[u][x].z) +
+                __popc(code[u][x].w);
+        d = estimate_regs<NW4>(code[u], pc, fv[u], a.planes + pair[u] * 4 * W, qp[u], a.dp);
+      }
+      key[u] = make_key(d, rid[u]);
+    }
+  }
+}
+
+// Stages the query's probes (first mask word, first slot) in shared memory.
+__device__ inline void fin_probes(const FinalizeArgs& a, int64_t row, int npq, int* s_wb,
+                                  int64_t* s_base) {
+  for (int p = threadIdx.x; p < npq; p += kFinThreads) {
+    s_wb[p] = a.wbase[row * a.npmax + p];
+    s_base[p] = a.offsets[a.probe_ids[row * a.npmax + p]];
+  }
+}
+
+// The common end: selection dump, exact re-rank of the `got` selected keys in
+// s_sel, top-k and the outputs.
+template <typename RawT>
+__device__ inline void fin_rerank(const FinalizeArgs& a, int64_t row, uint64_t* s_sel, int got,
+                                  uint64_t* s_top, int* hist, uint64_t* small, int* s_ctl,
+                                  const float* s_q) {
+  const int k = a.kq[row];
+  const bool rerank = a.rerank_on[row] != 0;
+  const int tid = threadIdx.x;
+  for (int j = tid; j < a.nsel_max; j += kFinThreads)
+    a.sel[row * a.nsel_max + j] = (j < got) ? s_sel[j] : kU64Max;
+  const float inf = __int_as_float(0x7f800000);
+  const uint64_t* res = s_sel;
+  int kk = min(k, got);
+  if (rerank) {
+    const RawT* raw = static_cast<const RawT*>(a.raw);
+    for (int i = tid; i < got; i += kFinThreads) {
+      const uint32_t id = (uint32_t)s_sel[i];
+      const float dist = exact_dist_lanes<RawT>(raw + (int64_t)id * a.dim, s_q, a.dim);
+      s_sel[i] = make_key(dist, id);
+    }
+    __syncthreads();
+    kk = block_select_smallest(s_sel, got, k, s_top, hist, small, s_ctl, true);
+    res = s_top;
+  }
+  for (int j = tid; j < a.k_stride; j += kFinThreads) {
+    const uint64_t key = (j < kk) ? res[j] : kU64Max;
+    a.out_ids[row * a.k_stride + j] = (key == kU64Max) ? -1 : (int64_t)(uint32_t)key;
+    a.out_d[row * a.k_stride + j] = (key == kU64Max) ? inf : from_orderable((uint32_t)(key >> 32));
+  }
+}
+
+template <int NW4>
+__global__ void __launch_bounds__(kFinThreads) collect_kernel(FinalizeArgs a) {
+  constexpr int PT = NW4 <= 2 ? 4 : (NW4 <= 4 ? 2 : 1);  // survivors per thread per step
+  constexpr int STEP = kFinThreads * PT;
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ int s_warp[kFinThreads / 32];
+  __shared__ int s_pos;
+  const int64_t row = blockIdx.x;
+  const int c0 = blockIdx.y * kFinRoundWords;
+  const int T = a.wtotal[row];
+  if (c0 >= T) return;  // block-uniform: past the query's mask words
+  const FinalizeLayout& lay = a.lay;
+  int64_t* s_base = reinterpret_cast<int64_t*>(smem);
+  uint32_t* s_desc = reinterpret_cast<uint32_t*>(s_base + lay.NP);
+  uint32_t* s_dword = s_desc + kFinRoundWords;
+  int* s_wb = reinterpret_cast<int*>(s_dword + kFinRoundWords);
+  const int npq = min(a.nprobe[row], a.npmax);
+  fin_probes(a, row, npq, s_wb, s_base);
+  // mwords is a multiple of 4 and the mask 16-byte aligned
+  const uint4* mrow4 = reinterpret_cast<const uint4*>(a.mask + row * a.mwords);
+  int tot_keys, tot_desc;
+  fin_round(mrow4, T, c0, s_desc, s_dword, s_warp, tot_keys, tot_desc);
+  if (tot_keys == 0) return;  // block-uniform
+  if (threadIdx.x == 0) s_pos = atomicAdd(&a.kcount[row], tot_keys);
+  __syncthreads();
+  const int64_t pos0 = s_pos;
+  uint64_t* krow = a.keys + row * a.kcap;
+  for (int j0 = 0; j0 < tot_keys; j0 += STEP) {
+    bool have[PT];
+    uint64_t key[PT];
+    fin_keys<NW4, PT>(a, row, c0, j0, tot_keys, tot_desc, s_desc, s_dword, s_wb, s_base, npq,
+                      have, key);
+#pragma unroll
+    for (int u = 0; u < PT; ++u) {
+      const int64_t at = pos0 + j0 + threadIdx.x + u * kFinThreads;
+      if (have[u] && at < a.kcap) krow[at] = key[u];
+    }
+  }
+}
+
+template <typename RawT>
+__global__ void __launch_bounds__(kFinThreads) select_kernel(FinalizeArgs a) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ int s_ctl[8];
+  const int64_t row = blockIdx.x;
+  const int count = a.kcount[row];
+  if (count > a.kcap) return;  // block-uniform: the streaming finalize takes it
+  const FinalizeLayout& lay = a.lay;
+  uint64_t* s_sel = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* s_top = s_sel + lay.P;
+  uint64_t* small = s_top + lay.PK;
+  int* hist = reinterpret_cast<int*>(small + 32);
+  float* s_q = reinterpret_cast<float*>(hist + 256);
+  for (int d = threadIdx.x; d < a.dim; d += kFinThreads) s_q[d] = a.q[row * a.dim + d];
+  if (threadIdx.x == 0) a.counts[row] = count;
+  // Without re-rank the selection is the answer and is sorted; with re-rank
+  // only the set matters and the exact keys are selected below.
+  const bool rerank = a.rerank_on[row] != 0;
+  const int got = block_select_smallest(a.keys + row * a.kcap, count, a.nsel[row], s_sel, hist,
+                                        small, s_ctl, !rerank);
+  fin_rerank<RawT>(a, row, s_sel, got, s_top, hist, small, s_ctl, s_q);
+}
 
 template <typename RawT, int NW4>
 __global__ void __launch_bounds__(kFinThreads) finalize_kernel(FinalizeArgs a) {
   constexpr int NWARP = kFinThreads / 32;
-  constexpr int W = 4 * NW4;
   constexpr int PT = NW4 <= 2 ? 4 : (NW4 <= 4 ? 2 : 1);  // survivors per thread per step
   constexpr int STEP = kFinThreads * PT;
   extern __shared__ __align__(16) uint8_t smem[];
@@ -981,9 +1232,10 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(FinalizeArgs a) {
   __shared__ int s_warp[NWARP];
   __shared__ int s_nbuf;
   __shared__ uint64_t s_thr;
+  const int64_t row = blockIdx.x;
+  if (a.kcount[row] <= a.kcap) return;  // block-uniform: the selection kernel took it
   const FinalizeLayout& lay = a.lay;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t row = blockIdx.x;
   uint64_t* s_sel = reinterpret_cast<uint64_t*>(smem);
   uint64_t* s_top = s_sel + lay.P;
   uint64_t* s_stage = s_top + lay.PK;
@@ -1000,137 +1252,22 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(FinalizeArgs a) {
   const int npq = min(a.nprobe[row], a.npmax);
   const int n_sel = a.nsel[row];
   for (int d = tid; d < a.dim; d += kFinThreads) s_q[d] = a.q[row * a.dim + d];
-  for (int p = tid; p < npq; p += kFinThreads) {
-    s_wb[p] = a.wbase[row * a.npmax + p];
-    s_base[p] = a.offsets[a.probe_ids[row * a.npmax + p]];
-  }
+  fin_probes(a, row, npq, s_wb, s_base);
   if (tid == 0) {
     s_nbuf = 0;
     s_thr = kU64Max;
   }
   int64_t count = 0;  // survivors (the same in every thread)
   for (int c0 = 0; c0 < T; c0 += kFinRoundWords) {
-    const int wfirst = c0 + tid * kFinWordsPerThread;
-    uint32_t w[kFinWordsPerThread];
-#pragma unroll
-    for (int j = 0; j < kFinWordsPerThread / 4; ++j) {
-      const uint4 v = (wfirst + 4 * j < T) ? mrow4[(wfirst >> 2) + j] : make_uint4(0, 0, 0, 0);
-      w[4 * j] = v.x;
-      w[4 * j + 1] = v.y;
-      w[4 * j + 2] = v.z;
-      w[4 * j + 3] = v.w;
-    }
-    int c = 0, nz = 0;
-#pragma unroll
-    for (int e = 0; e < kFinWordsPerThread; ++e) {
-      if (wfirst + e >= T) w[e] = 0u;  // words past the query's last probed list
-      const int n = __popc(w[e]);
-      c += n;
-      nz += n != 0;
-    }
-    // one scan of both counts: survivors (< 2^18 per round) in the low 18
-    // bits, nonzero words (<= kFinRoundWords) above
-    const int v = c | (nz << 18);
-    int incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    __syncthreads();  // the previous round is done with s_warp and the descriptors
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    int ex = incl - v, tot = 0;
-#pragma unroll
-    for (int i = 0; i < NWARP; ++i) {
-      const int sw = s_warp[i];
-      if (i < warp) ex += sw;
-      tot += sw;
-    }
-    const int tot_keys = tot & 0x3FFFF, tot_desc = tot >> 18;
-    {
-      int p = ex & 0x3FFFF, d = ex >> 18;
-#pragma unroll
-      for (int e = 0; e < kFinWordsPerThread; ++e) {
-        const int n = __popc(w[e]);
-        if (n) {
-          s_desc[d] = ((uint32_t)p << 12) | (uint32_t)(tid * kFinWordsPerThread + e);
-          s_dword[d] = w[e];
-          ++d;
-        }
-        p += n;
-      }
-    }
-    __syncthreads();
+    int tot_keys, tot_desc;
+    fin_round(mrow4, T, c0, s_desc, s_dword, s_warp, tot_keys, tot_desc);
     count += tot_keys;
     for (int j0 = 0; j0 < tot_keys; j0 += STEP) {
       const uint64_t thr = s_thr;
-      uint64_t key[PT];
       bool have[PT];
-      int64_t slot[PT];
-      int64_t pair[PT];
-#pragma unroll
-      for (int u = 0; u < PT; ++u) {
-        const int j = j0 + tid + u * kFinThreads;
-        have[u] = j < tot_keys;
-        slot[u] = 0;
-        pair[u] = row * a.npmax;
-        if (have[u]) {
-          int lo = 0, hi = tot_desc - 1;  // the last descriptor whose first survivor is <= j
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if ((int)(s_desc[mid] >> 12) <= j) lo = mid; else hi = mid - 1;
-          }
-          const uint32_t dsc = s_desc[lo];
-          const int word = c0 + (int)(dsc & 4095u);
-          uint32_t mw = s_dword[lo];  // the survivor's bit: drop the lower set bits
-          for (int r = j - (int)(dsc >> 12); r > 0; --r) mw &= mw - 1u;
-          const int bit = __ffs(mw) - 1;
-          int plo = 0, phi = npq - 1;  // the probe holding `word`
-          while (plo < phi) {
-            const int mid = (plo + phi + 1) >> 1;
-            if (s_wb[mid] <= word) plo = mid; else phi = mid - 1;
-          }
-          slot[u] = s_base[plo] + (int64_t)(word - s_wb[plo]) * 32 + bit;
-          pair[u] = row * a.npmax + plo;
-          if (!index_ok(slot[u], a.n_slots, a.err)) have[u] = false;
-        }
-      }
-      // every load of the step in flight: codes, factors, ids, parameters
-      uint4 code[PT][NW4];
-      float2 fv[PT];
-      uint32_t rid[PT];
-      float4 qp[PT];
-#pragma unroll
-      for (int u = 0; u < PT; ++u) {
-        if (have[u]) {
-          const uint4* cp = reinterpret_cast<const uint4*>(a.codes + slot[u] * (a.dp / 8));
-#pragma unroll
-          for (int x = 0; x < NW4; ++x) code[u][x] = __ldg(cp + x);
-          fv[u] = __ldg(a.fac + slot[u]);
-          rid[u] = __ldg(a.ids + slot[u]);
-          qp[u] = __ldg(a.qparams + pair[u]);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < PT; ++u) {
-        key[u] = kU64Max;
-        if (have[u]) {
-          float d;
-          if (a.resid) {
-            d = estimate_lut_direct<NW4>(code[u], a.resid + pair[u] * a.dp, fv[u], qp[u].z,
-                                         qp[u].w);
-          } else {
-            int pc = 0;
-#pragma unroll
-            for (int x = 0; x < NW4; ++x)
-              pc += __popc(code[u][x].x) + __popc(code[u][x].y) + __popc(code[u][x].z) +
-                    __popc(code[u][x].w);
-            d = estimate_regs<NW4>(code[u], pc, fv[u], a.planes + pair[u] * 4 * W, qp[u], a.dp);
-          }
-          key[u] = make_key(d, rid[u]);
-        }
-      }
+      uint64_t key[PT];
+      fin_keys<NW4, PT>(a, row, c0, j0, tot_keys, tot_desc, s_desc, s_dword, s_wb, s_base, npq,
+                        have, key);
       // offer: keys below the threshold go to the staging area
 #pragma unroll
       for (int u = 0; u < PT; ++u) {
@@ -1172,33 +1309,11 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(FinalizeArgs a) {
   __syncthreads();
   if (tid == 0) a.counts[row] = (int)min(count, (int64_t)INT32_MAX);
   const int staged = s_nbuf;
-  const int k = a.kq[row];
   const bool rerank = a.rerank_on[row] != 0;
-  // Without re-rank the selection is the answer and is sorted; with re-rank
-  // only the set matters and the exact keys are selected below.
   const int got = block_select_smallest(s_stage, staged, n_sel, s_sel, hist, small, s_ctl, !rerank);
-  for (int j = tid; j < a.nsel_max; j += kFinThreads)
-    a.sel[row * a.nsel_max + j] = (j < got) ? s_sel[j] : kU64Max;
-  const float inf = __int_as_float(0x7f800000);
-  const uint64_t* res = s_sel;
-  int kk = min(k, got);
-  if (rerank) {
-    const RawT* raw = static_cast<const RawT*>(a.raw);
-    for (int i = tid; i < got; i += kFinThreads) {
-      const uint32_t id = (uint32_t)s_sel[i];
-      const float dist = exact_dist_lanes<RawT>(raw + (int64_t)id * a.dim, s_q, a.dim);
-      s_sel[i] = make_key(dist, id);
-    }
-    __syncthreads();
-    kk = block_select_smallest(s_sel, got, k, s_top, hist, small, s_ctl, true);
-    res = s_top;
-  }
-  for (int j = tid; j < a.k_stride; j += kFinThreads) {
-    const uint64_t key = (j < kk) ? res[j] : kU64Max;
-    a.out_ids[row * a.k_stride + j] = (key == kU64Max) ? -1 : (int64_t)(uint32_t)key;
-    a.out_d[row * a.k_stride + j] = (key == kU64Max) ? inf : from_orderable((uint32_t)(key >> 32));
-  }
+  fin_rerank<RawT>(a, row, s_sel, got, s_top, hist, small, s_ctl, s_q);
 }
+
 
 // Probe selection. Both forms leave the query's np smallest (distance, list)
 // keys in dst, ascending, and return how many were found; the distance is
@@ -1661,6 +1776,11 @@ void layout_workspace(const rq_index* ix, const SearchShape& sh, Workspace& ws) 
   L.take(&ws.wbase, nq * np);
   L.take(&ws.wtotal, nq);
   L.take(&ws.sel, nq * sh.nsel_max);
+  // survivor keys: up to kKeyCap per query (every survivor when the query
+  // has fewer scanned vectors); a query with more takes the streaming form
+  ws.kcap = std::min<int64_t>(kKeyCap, 32 * ws.mwords);
+  L.take(&ws.keys, nq * ws.kcap);
+  L.take(&ws.kcount, nq);
   // the per-query parameters in one region (one copy from the pinned staging
   // buffer, which has the same layout): nprobe, k, selection size, re-rank
   // flag (+1: the no-prune flag)
@@ -1733,6 +1853,8 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
   rebase(ws.wbase, b);
   rebase(ws.wtotal, b);
   rebase(ws.sel, b);
+  rebase(ws.keys, b);
+  rebase(ws.kcount, b);
   rebase(ws.nprobe, b);
   ws.kq = ws.nprobe + nq;
   ws.nsel = ws.nprobe + 2 * nq;
@@ -1900,10 +2022,25 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
                          sh.nsel_max > 512 ? 8192 : 4096, np, ix->dim};
   f.out_ids = ws.out_ids;
   f.out_d = ws.out_d;
-  const size_t smem = f.lay.bytes();
-  auto kern = ix->raw_dtype == RQ_U8 ? finalize_kernel<uint8_t, NW4> : finalize_kernel<float, NW4>;
-  RQ_TRY(allow_dynamic_smem((const void*)kern, 220 * 1024));
-  kern<<<(unsigned)nq, kFinThreads, smem, st>>>(f);
+  f.keys = ws.keys;
+  f.kcount = ws.kcount;
+  f.kcap = ws.kcap;
+  const bool u8 = ix->raw_dtype == RQ_U8;
+  // collection: one block per (query, round of mask words)
+  RQ_CUDA(cudaMemsetAsync(ws.kcount, 0, sizeof(int32_t) * nq, st));
+  const int64_t rounds = std::max<int64_t>(1, (ws.mwords + kFinRoundWords - 1) / kFinRoundWords);
+  if (rounds > 65535) return fail(RQ_ERR_NOT_IMPLEMENTED, "probed lists too long for one search");
+  collect_kernel<NW4><<<dim3((unsigned)nq, (unsigned)rounds), kFinThreads, f.lay.collect_bytes(),
+                        st>>>(f);
+  // selection and re-rank from the key buffers; the streaming form for the
+  // queries whose survivors overflowed them
+  tm.mark(RQ_STAGE_RERANK, st);
+  auto sel = u8 ? select_kernel<uint8_t> : select_kernel<float>;
+  RQ_TRY(allow_dynamic_smem((const void*)sel, 220 * 1024));
+  sel<<<(unsigned)nq, kFinThreads, f.lay.select_bytes(), st>>>(f);
+  auto fin = u8 ? finalize_kernel<uint8_t, NW4> : finalize_kernel<float, NW4>;
+  RQ_TRY(allow_dynamic_smem((const void*)fin, 220 * 1024));
+  fin<<<(unsigned)nq, kFinThreads, f.lay.bytes(), st>>>(f);
   return RQ_OK;
 }
 
@@ -1946,7 +2083,6 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
       return fail(RQ_ERR_NOT_IMPLEMENTED, "padded dimension " + std::to_string(dp) +
                                               " has no scan kernel (built: 128..1024, 1536, 2048)");
   }
-  tm.mark(RQ_STAGE_RERANK, st);
   tm.mark(RQ_STAGE_COUNT, st);
   RQ_CUDA(cudaGetLastError());
   return RQ_OK;

@@ -80,13 +80,14 @@ def test_skewed_full_size_modes_agree_and_replay(skewed):
 
 
 def test_skewed_large_batch_split_equals_small_batches(skewed):
-    """A batch whose survivor slots would pass the workspace budget (2048
-    queries at nprobe 512 on the skewed index: tens of GB) runs as
-    sub-batches of one workspace; its results and dumped intermediates equal
-    those of the same queries searched in small batches, in every mode."""
+    """A batch whose workspace would pass the 8 GiB budget (8192 queries at
+    nprobe 512 on the skewed index: survivor masks, key buffers and the
+    tensor-core scan's per-list buckets) runs as sub-batches of one
+    workspace; its results equal those of the same queries searched in
+    small batches, in every grouped mode."""
     rq, ix = skewed
     wl = W.WORKLOADS["skewed"]
-    nq = 2048
+    nq = 8192
     q = wl["mix"].queries(nq)
     qd = torch.from_numpy(q).cuda()
     ref_i = torch.empty((nq, 10), dtype=torch.int64, device="cuda")
@@ -103,4 +104,28 @@ def test_skewed_large_batch_split_equals_small_batches(skewed):
                   dump={"bound": bound})
         torch.cuda.synchronize()
         assert torch.equal(oi, ref_i) and torch.equal(od, ref_d), mode
+    assert ix.device_error() == 0
+
+
+def test_skewed_unpruned_overflow_takes_streaming_finalize(skewed):
+    """Without pruning every scanned vector survives: hundreds of thousands
+    per query at nprobe 512, more than a query's key buffer holds, so the
+    streaming finalize takes these queries. The results equal the pruned
+    search's (the first bound drops no vector that could be selected), and
+    the candidate count is every scanned pair."""
+    rq, ix = skewed
+    wl = W.WORKLOADS["skewed"]
+    q = wl["mix"].queries(16)
+    pruned = search_dump(ix, q, 512, 10, 200, scan_mode=3)
+    h = host_index(ix)
+    lens = np.diff(h["offsets"])
+    for mode in (3, 1):
+        full = search_dump(ix, q, 512, 10, 200, scan_mode=mode, no_prune=True)
+        assert np.array_equal(full["ids"], pruned["ids"]), mode
+        assert np.array_equal(full["dist"].view(np.uint32), pruned["dist"].view(np.uint32)), mode
+        assert np.array_equal(np.sort(full["selected"], axis=1),
+                              np.sort(pruned["selected"], axis=1)), mode
+        pairs = lens[full["probe_ids"]].sum(axis=1)
+        assert np.array_equal(full["n_candidates"].astype(np.int64), pairs), mode
+        assert pairs.min() > 65536
     assert ix.device_error() == 0
