@@ -9,6 +9,13 @@ namespace rq {
 
 constexpr int kGroupVectors = 256;  // vectors per work item of the persistent scans
 
+// An integer x with |x| < 2^22 as a float32, exactly, without the
+// conversion unit: the bits 0x4B400000 + x are the float 1.5 * 2^23 + x
+// (the same exponent for every such x), and subtracting 1.5 * 2^23 is exact.
+__device__ __forceinline__ float small_int_to_float(int x) {
+  return __fsub_rn(__int_as_float(0x4B400000 + x), 12582912.0f);
+}
+
 // With ip = sum_d bit_d q_u,d (bit-planes: ip = sum_j 2^j popc(code & plane_j))
 // and pc = popc(code):
 //   t  = delta (2 ip - Sq) + vl (2 pc - D_p)
@@ -36,8 +43,8 @@ __device__ __forceinline__ float estimate_regs(const uint4 (&code)[NW4], int pc,
   }
   const int ip = s0 + 2 * s1 + 4 * s2 + 8 * s3;
   const int sq = __float_as_int(qp.w);
-  const float a = (float)(2 * ip - sq);
-  const float b = (float)(2 * pc - dp);
+  const float a = small_int_to_float(2 * ip - sq);
+  const float b = small_int_to_float(2 * pc - dp);
   const float t = __fadd_rn(__fmul_rn(qp.y, a), __fmul_rn(qp.x, b));
   const float d = __fsub_rn(__fadd_rn(qp.z, fac.x), __fmul_rn(2.0f, __fmul_rn(fac.y, t)));
   return __fadd_rn(d, 0.0f);

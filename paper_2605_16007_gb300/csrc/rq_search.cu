@@ -785,112 +785,58 @@ approx_dist_kernel(const float* __restrict__ A, int64_t na, const float* __restr
 }
 
 // ---------------------------------------------------------------------------
-// Exact squared distance of one raw row to the query in the 32-lane order,
-// computed by one thread: partial sum l takes d = l, l + 32, ... in order,
-// then partials l and l + s are added for s = 16, 8, 4, 2, 1.
+// Exact squared distances of selected raw rows to the query in the 32-lane
+// order: partial sum l takes d = l, l + 32, ... (d < dim) in order, then
+// partials l and l + s are added for s = 16, 8, 4, 2, 1. A warp takes eight
+// rows at a time, lane l holding partial l of each: every load is a
+// coalesced 32-float (or 32-byte) piece of a row, and up to 32 of them (8
+// rows x 4 pieces) are in flight per lane; the partials meet by shuffles in
+// the same tree. Row i of `keys` (row id in the low word) gets the key
+// (distance, id).
 // ---------------------------------------------------------------------------
 template <typename RawT>
-__device__ __forceinline__ float exact_dist_lanes(const RawT* __restrict__ x,
-                                                  const float* __restrict__ qs, int dim) {
-  float acc[32];
+__device__ inline void rerank_rows(const RawT* __restrict__ raw, uint64_t* keys, int n,
+                                   const float* __restrict__ qs, int dim) {
+  constexpr int G = 8, JB = 4;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  for (int i0 = warp * G; i0 < n; i0 += nwarps * G) {
+    uint32_t id[G];
+    float acc[G];
 #pragma unroll
-  for (int l = 0; l < 32; ++l) acc[l] = 0.0f;
-  int d0 = 0;
-  if (sizeof(RawT) == 4 && (dim & 3) == 0) {
-    // float rows: two 32-dim chunks per step (sixteen 16-byte loads in
-    // flight), the terms added in increasing d (chunk d0, then d0 + 32).
-    const float4* x4 = reinterpret_cast<const float4*>(x);
-    for (; d0 + 64 <= dim; d0 += 64) {
-      float4 a[8], b[8];
+    for (int g = 0; g < G; ++g) {
+      id[g] = i0 + g < n ? (uint32_t)keys[i0 + g] : 0u;
+      acc[g] = 0.0f;
+    }
+    for (int d0 = 0; d0 < dim; d0 += 32 * JB) {
+      float v[G][JB];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) a[j] = __ldg(x4 + (d0 >> 2) + j);
+      for (int g = 0; g < G; ++g)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) b[j] = __ldg(x4 + (d0 >> 2) + 8 + j);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const float va[4] = {a[j].x, a[j].y, a[j].z, a[j].w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float df = __fsub_rn(va[e], qs[d0 + 4 * j + e]);
-          acc[4 * j + e] = __fadd_rn(acc[4 * j + e], __fmul_rn(df, df));
+        for (int jb = 0; jb < JB; ++jb) {
+          const int d = d0 + 32 * jb + lane;
+          v[g][jb] = (i0 + g < n && d < dim) ? (float)__ldg(raw + (int64_t)id[g] * dim + d) : 0.0f;
         }
-      }
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const float vb[4] = {b[j].x, b[j].y, b[j].z, b[j].w};
+      for (int jb = 0; jb < JB; ++jb) {
+        const int d = d0 + 32 * jb + lane;
+        if (d < dim) {
+          const float qd = qs[d];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float df = __fsub_rn(vb[e], qs[d0 + 32 + 4 * j + e]);
-          acc[4 * j + e] = __fadd_rn(acc[4 * j + e], __fmul_rn(df, df));
+          for (int g = 0; g < G; ++g) {
+            const float df = __fsub_rn(v[g][jb], qd);
+            acc[g] = __fadd_rn(acc[g], __fmul_rn(df, df));
+          }
         }
       }
     }
-    for (; d0 + 32 <= dim; d0 += 32) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const float4 t = __ldg(x4 + (d0 >> 2) + j);
-        const float v[4] = {t.x, t.y, t.z, t.w};
+    for (int g = 0; g < G; ++g) {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float df = __fsub_rn(v[e], qs[d0 + 4 * j + e]);
-          acc[4 * j + e] = __fadd_rn(acc[4 * j + e], __fmul_rn(df, df));
-        }
-      }
-    }
-  } else if (sizeof(RawT) == 1 && (dim & 15) == 0) {
-    // bytes: 128 dimensions (eight 16-byte loads, all in flight) per step
-    for (; d0 + 128 <= dim; d0 += 128) {
-      const uint4* x16 = reinterpret_cast<const uint4*>(x + d0);
-      uint4 t[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) t[j] = __ldg(x16 + j);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const uint32_t w[4] = {t[j].x, t[j].y, t[j].z, t[j].w};
-#pragma unroll
-        for (int b = 0; b < 16; ++b) {
-          const int l = (16 * j + b) & 31;
-          const float v = (float)((w[b >> 2] >> (8 * (b & 3))) & 255u);
-          const float df = __fsub_rn(v, qs[d0 + 16 * j + b]);
-          acc[l] = __fadd_rn(acc[l], __fmul_rn(df, df));
-        }
-      }
-    }
-    for (; d0 + 32 <= dim; d0 += 32) {
-      const uint4* x16 = reinterpret_cast<const uint4*>(x + d0);
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const uint4 t = __ldg(x16 + j);
-        const uint32_t w[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-        for (int b = 0; b < 16; ++b) {
-          const float v = (float)((w[b >> 2] >> (8 * (b & 3))) & 255u);
-          const float df = __fsub_rn(v, qs[d0 + 16 * j + b]);
-          acc[16 * j + b] = __fadd_rn(acc[16 * j + b], __fmul_rn(df, df));
-        }
-      }
-    }
-  } else {
-    for (; d0 + 32 <= dim; d0 += 32) {
-#pragma unroll
-      for (int l = 0; l < 32; ++l) {
-        const float df = __fsub_rn((float)x[d0 + l], qs[d0 + l]);
-        acc[l] = __fadd_rn(acc[l], __fmul_rn(df, df));
-      }
+      for (int s2 = 16; s2; s2 >>= 1) acc[g] = __fadd_rn(acc[g], __shfl_down_sync(0xffffffffu, acc[g], s2));
+      if (lane == 0 && i0 + g < n) keys[i0 + g] = make_key(acc[g], id[g]);
     }
   }
-#pragma unroll
-  for (int l = 0; l < 32; ++l) {
-    if (d0 + l < dim) {
-      const float df = __fsub_rn((float)x[d0 + l], qs[d0 + l]);
-      acc[l] = __fadd_rn(acc[l], __fmul_rn(df, df));
-    }
-  }
-#pragma unroll
-  for (int s = 16; s; s >>= 1)
-#pragma unroll
-    for (int l = 0; l < s; ++l) acc[l] = __fadd_rn(acc[l], acc[l + s]);
-  return acc[0];
 }
 
 // ---------------------------------------------------------------------------
@@ -1142,12 +1088,7 @@ __device__ inline void fin_rerank(const FinalizeArgs& a, int64_t row, uint64_t* 
   const uint64_t* res = s_sel;
   int kk = min(k, got);
   if (rerank) {
-    const RawT* raw = static_cast<const RawT*>(a.raw);
-    for (int i = tid; i < got; i += kFinThreads) {
-      const uint32_t id = (uint32_t)s_sel[i];
-      const float dist = exact_dist_lanes<RawT>(raw + (int64_t)id * a.dim, s_q, a.dim);
-      s_sel[i] = make_key(dist, id);
-    }
+    rerank_rows<RawT>(static_cast<const RawT*>(a.raw), s_sel, got, s_q, a.dim);
     __syncthreads();
     kk = block_select_smallest(s_sel, got, k, s_top, hist, small, s_ctl, true);
     res = s_top;
