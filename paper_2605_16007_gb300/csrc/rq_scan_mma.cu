@@ -114,35 +114,6 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Packed two-lane float32 arithmetic (add / mul / fma .rn.f32x2), each lane
-// rounded once to nearest even. A packed multiply whose result feeds a packed
-// add can still come out fused into one rounding, so they are used only where
-// that cannot change the result (an exact product, as in x + (-2) y).
-__device__ __forceinline__ float2 add2_rn(float2 a, float2 b) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return d;
-}
-__device__ __forceinline__ float2 mul2_rn(float2 a, float2 b) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return d;
-}
-__device__ __forceinline__ float2 fma2_rn(float2 a, float2 b, float2 c) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-      "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-  return d;
-}
-
 // Byte offset of 16-byte chunk c of row r in a 128B-swizzled K-major tile.
 __device__ __forceinline__ uint32_t sw128_offset(int r, int c) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
@@ -395,7 +366,9 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items,
       tc_fence_after();
       // Epilogue: thread t = vector t = TMEM lane 32 (w % 4) + lane of
       // tile w / 4; 8 pairs per TMEM load, two at a time, partly in packed
-      // float2 operations. The estimator's operations are the popcount
+      // float2 operations (each component rounded as the scalar _rn
+      // operation; used only where fusing could not change the result). The
+      // estimator's operations are the popcount
       // form's, each rounded once: a = 2 ip - Sq is an exact small integer
       // (one FMA with -Sq gives it exactly); x - 2 y is x + (-2) y (the
       // negation and the doubling are exact, so one fused multiply-add
@@ -423,18 +396,18 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items,
               const float4 qa = qp_s[g];      // {vl, vl', delta, delta'}
               const float4 qb = qp_s[g + 1];  // {nq2, nq2', -Sq, -Sq'}
               const float2 ip = make_float2(__uint_as_float(r[2 * h]), __uint_as_float(r[2 * h + 1]));
-              const float2 a = fma2_rn(two, ip, make_float2(qb.z, qb.w));
+              const float2 a = __ffma2_rn(two, ip, make_float2(qb.z, qb.w));
               // t in scalar operations: a packed multiply feeding a packed
-              // add may be contracted into one fused operation.
+              // add can come out fused into one rounding.
               const float2 t = make_float2(
                   __fadd_rn(__fmul_rn(qa.z, a.x), __fmul_rn(qa.x, bterm)),
                   __fadd_rn(__fmul_rn(qa.w, a.y), __fmul_rn(qa.y, bterm)));
-              const float2 base = add2_rn(make_float2(qb.x, qb.y), r2);
-              const float2 dd = fma2_rn(mtwo, mul2_rn(f2, t), base);
+              const float2 base = __fadd2_rn(make_float2(qb.x, qb.y), r2);
+              const float2 dd = __ffma2_rn(mtwo, __fmul2_rn(f2, t), base);
               // tau - d rounded once is >= +0 exactly when d <= tau (neither
               // is -0 or NaN; a nonzero difference of floats never rounds to
               // zero; +inf - d = +inf)
-              const float2 df = fma2_rn(mone, dd, tau2[g >> 1]);
+              const float2 df = __ffma2_rn(mone, dd, tau2[g >> 1]);
               sgn[2 * h] = __float_as_uint(df.x);
               sgn[2 * h + 1] = __float_as_uint(df.y);
             }
