@@ -82,21 +82,15 @@ __device__ __forceinline__ uint64_t make_key(float d, uint32_t id) {
 // ---------------------------------------------------------------------------
 // Warp helpers
 // ---------------------------------------------------------------------------
+// Warp minimum / maximum of a float (no NaN): one reduction on the
+// order-preserving integer image.
 __device__ __forceinline__ float warp_min(float v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
+  return from_orderable(__reduce_min_sync(0xffffffffu, orderable(v)));
 }
 __device__ __forceinline__ float warp_max(float v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
+  return from_orderable(__reduce_max_sync(0xffffffffu, orderable(v)));
 }
-__device__ __forceinline__ int warp_sum_int(int v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
+__device__ __forceinline__ int warp_sum_int(int v) { return __reduce_add_sync(0xffffffffu, v); }
 // The 32-lane order: each lane holds its partial sum; combine with strides
 // 16, 8, 4, 2, 1, each addition rounded once.
 __device__ __forceinline__ float lane_tree_sum(float v) {

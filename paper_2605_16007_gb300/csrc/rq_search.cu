@@ -185,12 +185,18 @@ __device__ __forceinline__ void quantize_pair(int64_t pair, int64_t q, int c, in
   const float inv = same ? 0.0f : __fdiv_rn(15.0f, width);
   int sq = 0;
   constexpr int W = PER;  // words per plane
+  constexpr int NWD = (4 * W + 31) / 32;  // plane words held per lane
   uint32_t* pl = planes + pair * 4 * W;
+  // plane word j W + i goes to lane (j W + i) % 32, so that the words leave
+  // in coalesced stores
+  uint32_t mine[NWD];
+#pragma unroll
+  for (int x = 0; x < NWD; ++x) mine[x] = 0u;
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
     int qu = 0;
     if (!same) {
-      qu = (int)floorf(__fadd_rn(__fmul_rn(__fsub_rn(r[i], vl), inv), 0.5f));
+      qu = __float2int_rd(__fadd_rn(__fmul_rn(__fsub_rn(r[i], vl), inv), 0.5f));
       qu = min(qu, 15);
     }
     sq += qu;
@@ -205,10 +211,15 @@ __device__ __forceinline__ void quantize_pair(int64_t pair, int64_t q, int c, in
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const uint32_t w = __ballot_sync(0xffffffffu, (qu >> j) & 1);
-      if (lane == 0) {
-        pl[j * W + i] = w;
-        if (rec) rec[j * W + i] = w;
-      }
+      if (lane == ((j * W + i) & 31)) mine[(j * W + i) >> 5] = w;
+    }
+  }
+#pragma unroll
+  for (int x = 0; x < NWD; ++x) {
+    const int wi = 32 * x + lane;
+    if (wi < 4 * W) {
+      pl[wi] = mine[x];
+      if (rec) rec[wi] = mine[x];
     }
   }
   sq = warp_sum_int(sq);
