@@ -99,6 +99,17 @@ typedef struct rq_build_opts {
                            unchanged, the gather reads 4x fewer bytes);
                            1: always keep float32 */
   int64_t train_size;   /* rows of the k-means training subset; 0 = all rows */
+  int32_t raw_on_host;  /* 1: the re-rank reads the raw rows from the
+                           caller's base buffer in host memory (page-locked:
+                           cudaHostAlloc, cudaMallocHost or
+                           cudaHostRegister), through the GPU's mapping of
+                           it, instead of a device copy; the base stays in its
+                           own dtype. The index keeps a reference: the caller
+                           owns the buffer and keeps it alive and unchanged
+                           until rq_free. Any other base is INVALID_ARG. 0
+                           (default): a device copy (Section 3.3.4 re-ranks
+                           on the host to spare the device the raw vectors;
+                           here the GPU reads them from host memory) */
 } rq_build_opts;
 
 /* Optional device buffers that receive the intermediates of one rq_search

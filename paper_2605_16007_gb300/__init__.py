@@ -34,7 +34,7 @@ class RQError(RuntimeError):
 
 class BuildOpts(C.Structure):
     _fields_ = [("kmeans_iters", C.c_int32), ("keep_float_raw", C.c_int32),
-                ("train_size", C.c_int64)]
+                ("train_size", C.c_int64), ("raw_on_host", C.c_int32)]
 
 
 class SearchDump(C.Structure):
@@ -173,9 +173,13 @@ def _is_u8(a):
 
 # ------------------------------------------------------------------ C names
 def rq_build(base, nlist: int, seed: int, kmeans_iters: int = 10,
-             train_size: int = 0, keep_float_raw: bool = False) -> "Index":
+             train_size: int = 0, keep_float_raw: bool = False,
+             raw_on_host: bool = False) -> "Index":
+    """raw_on_host: `base` is a page-locked host buffer (a pinned torch CPU
+    tensor, for instance) that the index's re-rank reads in place; keep it
+    alive and unchanged while the index lives."""
     n, dim = _shape(base)
-    opts = BuildOpts(kmeans_iters, int(keep_float_raw), train_size)
+    opts = BuildOpts(kmeans_iters, int(keep_float_raw), train_size, int(raw_on_host))
     h = C.c_void_p()
     _check(lib().rq_build(_ptr(base), RQ_U8 if _is_u8(base) else RQ_F32, n, dim, nlist,
                           seed, C.byref(opts), C.byref(h)))

@@ -104,8 +104,8 @@ rq_status check_finite_device(const float* d, int64_t n, const char* what) {
 
 void free_index_arrays(rq_index* ix) {
   void* ptrs[] = {ix->P,     ix->P32,   ix->centroids, ix->cR,     ix->offsets, ix->codes,
-                  ix->r,     ix->alpha, ix->fac,       ix->ids,    ix->assign,  ix->raw,
-                  ix->d_err, ix->items};
+                  ix->r,     ix->alpha, ix->fac,       ix->ids,    ix->assign,
+                  ix->raw_owned ? ix->raw : nullptr, ix->d_err, ix->items};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ix->P = nullptr;
@@ -192,9 +192,20 @@ rq_status compress_raw(rq_index* ix) {
 
 rq_status build_common(const void* base, rq_dtype dt, int64_t n, int32_t dim, int32_t nlist,
                        uint64_t seed, int iters, int64_t train, const float* cent,
-                       const double* P, rq_index** out, bool keep_float_raw = false) {
+                       const double* P, rq_index** out, bool keep_float_raw = false,
+                       bool raw_on_host = false) {
   RQ_TRY(check_build_args(base, dt, n, dim, nlist, out));
   *out = nullptr;
+  void* host_raw = nullptr;  // the GPU's address of the caller's buffer
+  if (raw_on_host) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, base) != cudaSuccess || at.type != cudaMemoryTypeHost ||
+        !at.devicePointer) {
+      cudaGetLastError();
+      return fail(RQ_ERR_INVALID_ARG, "raw_on_host needs a page-locked host base buffer");
+    }
+    host_raw = at.devicePointer;
+  }
   std::unique_ptr<rq_index> ix(new rq_index());
   cudaGetDevice(&ix->device);
   void* d_raw = nullptr;
@@ -225,7 +236,14 @@ rq_status build_common(const void* base, rq_dtype dt, int64_t n, int32_t dim, in
   if (cent_tmp) cudaFree(cent_tmp);
   if (P_tmp) cudaFree(P_tmp);
   if (temp) cudaFree(d_f32);
-  if (s == RQ_OK && !keep_float_raw) s = compress_raw(ix.get());
+  if (s == RQ_OK && raw_on_host) {
+    // the device copy served the build; the re-rank reads the caller's rows
+    cudaFree(ix->raw);
+    ix->raw = host_raw;
+    ix->raw_owned = false;
+  } else if (s == RQ_OK && !keep_float_raw) {
+    s = compress_raw(ix.get());
+  }
   if (s != RQ_OK) {
     if (ix->raw == nullptr) cudaFree(d_raw);
     free_index_arrays(ix.get());
@@ -568,7 +586,7 @@ rq_status rq_build(const void* base, rq_dtype dtype, int64_t n, int32_t dim, int
   if (train < 0) return fail(RQ_ERR_INVALID_ARG, "train_size < 0");
   if (train > 0 && train < nlist) return fail(RQ_ERR_INVALID_ARG, "train_size below nlist");
   return build_common(base, dtype, n, dim, nlist, seed, iters, train, nullptr, nullptr, out,
-                      opts && opts->keep_float_raw);
+                      opts && opts->keep_float_raw, opts && opts->raw_on_host);
 }
 
 rq_status rq_build_with(const void* base, rq_dtype dtype, int64_t n, int32_t dim, int32_t nlist,
@@ -708,7 +726,7 @@ rq_status rq_export(const rq_index* cix, const char* path) {
   for (auto& a : array_specs(ix)) {
     if (!ok) break;
     buf.resize(a.bytes);
-    if (cudaMemcpy(buf.data(), *a.dev, a.bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    if (cudaMemcpy(buf.data(), *a.dev, a.bytes, cudaMemcpyDefault) != cudaSuccess) {
       fclose(f);
       return cuda_fail(cudaGetLastError(), "export copy", __FILE__, __LINE__);
     }

@@ -159,6 +159,7 @@ struct rq_index {
   uint32_t* ids = nullptr;    // n
   int32_t* assign = nullptr;  // n (row order)
   void* raw = nullptr;        // n x dim (float or uint8)
+  bool raw_owned = true;      // false: the caller's page-locked host buffer (raw_on_host)
   int32_t* d_err = nullptr;   // device error word
   int2* items = nullptr;      // static scan items (list, first vector)
   int n_items = 0;

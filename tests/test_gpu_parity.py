@@ -8,6 +8,9 @@ precision than the oracle (the float32 rotation against the float64 one, the
 float32 encode against float64) are compared within stated tolerances, and
 every later stage is replayed from the GPU's own output of that stage.
 """
+import os
+import tempfile
+
 import numpy as np
 import pytest
 
@@ -446,3 +449,35 @@ def test_exact_probe_path_wide_codes_many_lists(rq):
     for mode in (1, 2):
         dump = search_dump(ix, q, 12, 10, 100, scan_mode=mode)
         replay_and_compare(h, q, dump)
+
+
+@pytest.mark.parametrize("u8", [False, True])
+def test_raw_on_host_rerank_equals_device_copy(u8):
+    """With raw_on_host the re-rank reads the caller's page-locked base rows
+    in host memory: every result equals the device-copy index's, the index
+    exports and imports like any other, and a pageable base is refused."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    rq = lib()
+    mix = W.mixture("sift1m" if u8 else "tiny")
+    x = mix.base(20000)
+    if u8:
+        x = x.astype(np.uint8)
+    q = mix.queries(64).astype(np.float32)
+    ref = rq.rq_build(x, 64, seed=3, kmeans_iters=3, keep_float_raw=True)
+    pinned = torch.from_numpy(x).pin_memory()
+    ix = rq.rq_build(pinned, 64, seed=3, kmeans_iters=3, raw_on_host=True)
+    for mode in (1, 3):
+        a = ref.search(q, 12, 10, 120, scan_mode=mode)
+        b = ix.search(q, 12, 10, 120, scan_mode=mode)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
+    path = os.path.join(tempfile.mkdtemp(), "host_raw.rqix")
+    ix.export(path)
+    ix2 = rq.rq_import(path)
+    c = ix2.search(q, 12, 10, 120)
+    assert np.array_equal(c[0], ref.search(q, 12, 10, 120)[0])
+    ix.free()
+    assert pinned.numpy().tobytes() == x.tobytes()  # the caller's buffer, untouched
+    with pytest.raises(rq.RQError) as e:
+        rq.rq_build(x, 64, seed=3, kmeans_iters=3, raw_on_host=True)
+    assert e.value.status == rq.RQ_ERR_INVALID_ARG
