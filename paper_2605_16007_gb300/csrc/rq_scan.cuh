@@ -111,6 +111,13 @@ __host__ __device__ constexpr int pair_rec_bytes(int dp) { return dp / 2 + 32; }
 rq_status launch_scan_stream(rq_index* ix, const SearchShape& sh, Workspace& ws, cudaStream_t st,
                              int sms, uint64_t wait_ns, int withhold);
 
+// Tensor-core centroid ranking (rq_probe_tc.cu): g = ||c||^2 - 2 <q', c>
+// (nq x nlist) and cn = ||c||^2, D_p 128; its approximate distances are
+// within kTcProbeEscale (||q'||^2 + ||c||^2) of the exact ones.
+constexpr float kTcProbeEscale = 0.00390625f;  // 2^-8
+rq_status launch_approx_dist_tc(const float* qrot, int64_t nq, const float* cR, int nlist, int dp,
+                                float* g, float* cn, int32_t* err, cudaStream_t st);
+
 // Tensor-core scan (rq_scan_mma.cu).
 bool mma_supported(const rq_index* ix);
 rq_status launch_scan_mma(rq_index* ix, const SearchShape& sh, Workspace& ws, cudaStream_t st,

@@ -693,109 +693,6 @@ rotate_kernel8(const float* __restrict__ q, int64_t nq, int dim, const float* __
 }
 
 // ---------------------------------------------------------------------------
-// Approximate centroid ranking, the filter of the certified probe selection:
-// g[i][j] = ||c_j||^2 - 2 <q'_i, c_j> in float32 with fused multiply-adds,
-// 64 x 64 tiles per block (4 x 4 per thread). All of K (D_p <= 128 here)
-// is loaded into shared memory at once, every load in flight together;
-// blocks of the first row also write cn[j] = ||c_j||^2. Its error is
-// bounded where it is used (probe_select_certified).
-// ---------------------------------------------------------------------------
-constexpr int kApproxMaxDp = 128;
-constexpr int kApproxLd = 68;  // row stride (floats) of the k-major tiles
-
-__global__ void __launch_bounds__(256)
-approx_dist_kernel(const float* __restrict__ A, int64_t na, const float* __restrict__ B, int nb,
-                   int dp, float* __restrict__ g, float* __restrict__ cn) {
-  extern __shared__ __align__(16) float sm_f[];
-  float* As = sm_f;                         // [dp][kApproxLd], k-major
-  float* Bs = sm_f + dp * kApproxLd;        // [dp][kApproxLd]
-  __shared__ float s_cn[4][64];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int lane = tid & 31, w = tid >> 5;
-  const int64_t row0 = (int64_t)blockIdx.x * 64;
-  const int col0 = blockIdx.y * 64;
-  // rows lane and lane + 32 of each tile; warp w takes dimensions 4 (w + 8 t)
-  const int nk4 = dp / 32;
-  for (int h = 0; h < 2; ++h) {
-    const int r = lane + 32 * h;
-    float4 va[kApproxMaxDp / 32], vb[kApproxMaxDp / 32];
-#pragma unroll
-    for (int t = 0; t < kApproxMaxDp / 32; ++t) {
-      va[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      vb[t] = va[t];
-      if (t < nk4) {
-        const int k = 4 * (w + 8 * t);
-        if (row0 + r < na) va[t] = __ldg(reinterpret_cast<const float4*>(A + (row0 + r) * dp + k));
-        if (col0 + r < nb)
-          vb[t] = __ldg(reinterpret_cast<const float4*>(B + (int64_t)(col0 + r) * dp + k));
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < kApproxMaxDp / 32; ++t) {
-      if (t < nk4) {
-        const int k = 4 * (w + 8 * t);
-        As[(k + 0) * kApproxLd + r] = va[t].x;
-        As[(k + 1) * kApproxLd + r] = va[t].y;
-        As[(k + 2) * kApproxLd + r] = va[t].z;
-        As[(k + 3) * kApproxLd + r] = va[t].w;
-        Bs[(k + 0) * kApproxLd + r] = vb[t].x;
-        Bs[(k + 1) * kApproxLd + r] = vb[t].y;
-        Bs[(k + 2) * kApproxLd + r] = vb[t].z;
-        Bs[(k + 3) * kApproxLd + r] = vb[t].w;
-      }
-    }
-  }
-  __syncthreads();
-  // ||c||^2 of the block's 64 columns: four threads per column, a quarter of
-  // the dimensions each
-  {
-    const int j = tid & 63, qd = tid >> 6, len = dp / 4;
-    float acc = 0.0f;
-    for (int k = qd * len; k < (qd + 1) * len; ++k)
-      acc = fmaf(Bs[k * kApproxLd + j], Bs[k * kApproxLd + j], acc);
-    s_cn[qd][j] = acc;
-  }
-  float acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
-#pragma unroll 8
-  for (int k = 0; k < dp; ++k) {
-    const float4 av = *reinterpret_cast<const float4*>(&As[k * kApproxLd + 4 * ty]);
-    const float4 bv = *reinterpret_cast<const float4*>(&Bs[k * kApproxLd + 4 * tx]);
-    const float ar[4] = {av.x, av.y, av.z, av.w};
-    const float br[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
-  }
-  __syncthreads();
-  float cnv[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int c = 4 * tx + j;
-    cnv[j] = (s_cn[0][c] + s_cn[1][c]) + (s_cn[2][c] + s_cn[3][c]);
-  }
-  if (blockIdx.x == 0 && ty == 0) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (col0 + 4 * tx + j < nb) cn[col0 + 4 * tx + j] = cnv[j];
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int64_t r = row0 + 4 * ty + i;
-    if (r >= na) continue;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = col0 + 4 * tx + j;
-      if (c < nb) g[r * nb + c] = fmaf(-2.0f, acc[i][j], cnv[j]);
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Exact squared distances of selected raw rows to the query in the 32-lane
 // order: partial sum l takes d = l, l + 32, ... (d < dim) in order, then
 // partials l and l + s are added for s = 16, 8, 4, 2, 1. A warp takes eight
@@ -872,7 +769,7 @@ __device__ inline void rerank_rows(const RawT* __restrict__ raw, uint64_t* keys,
 //    the buffer (block radix selection), gathers and re-ranks them exactly and
 //    selects the final k.
 // 3. finalize_kernel: only for a query with more survivors than its buffer
-//    holds. It reads the masks again in rounds and keeps the n_sel smallest
+//    holds (one block per SM walks the queries). It reads the masks again in rounds and keeps the n_sel smallest
 //    keys in shared memory by a streaming threshold: a key below the
 //    threshold goes to the staging area; when that could overflow in the next
 //    step, the n_sel smallest staged keys are kept and the threshold becomes
@@ -882,7 +779,6 @@ __device__ inline void rerank_rows(const RawT* __restrict__ raw, uint64_t* keys,
 constexpr int kFinThreads = 256;
 constexpr int kFinWordsPerThread = 16;                            // four 16-byte mask loads
 constexpr int kFinRoundWords = kFinThreads * kFinWordsPerThread;  // mask words per round
-constexpr int kFinStepMax = kFinThreads * 4;                      // survivors per step, at most
 constexpr int64_t kKeyCap = 65536;                                // key buffer per query
 
 // Shared memory of the streaming finalize, in order: selection (P keys),
@@ -936,6 +832,7 @@ struct FinalizeArgs {
   FinalizeLayout lay;
   int64_t* out_ids;
   float* out_d;
+  int64_t nq;
   uint64_t* keys;            // nq x kcap survivor keys (collect -> select)
   int32_t* kcount;           // nq: survivors of each query (cleared before collect)
   int64_t kcap;
@@ -1184,8 +1081,11 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(FinalizeArgs a) {
   __shared__ int s_warp[NWARP];
   __shared__ int s_nbuf;
   __shared__ uint64_t s_thr;
-  const int64_t row = blockIdx.x;
-  if (a.kcount[row] <= a.kcap) return;  // block-uniform: the selection kernel took it
+  // a grid of a few blocks per SM walks the queries; only those whose keys
+  // overflowed their buffers are worked on
+  for (int64_t row = blockIdx.x; row < a.nq; row += gridDim.x) {
+  if (a.kcount[row] <= a.kcap) continue;  // block-uniform: the selection kernel took it
+  __syncthreads();  // the previous query's shared memory is free
   const FinalizeLayout& lay = a.lay;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint64_t* s_sel = reinterpret_cast<uint64_t*>(smem);
@@ -1264,6 +1164,7 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(FinalizeArgs a) {
   const bool rerank = a.rerank_on[row] != 0;
   const int got = block_select_smallest(s_stage, staged, n_sel, s_sel, hist, small, s_ctl, !rerank);
   fin_rerank<RawT>(a, row, s_sel, got, s_top, hist, small, s_ctl, s_q);
+  }
 }
 
 
@@ -1316,17 +1217,15 @@ __device__ __forceinline__ float seq_sqdist(const float* qs, const float* __rest
   return acc;
 }
 
-// Certified form, for nlist <= kProbeStageKeys. From the approximate
-// ranking g = ||c||^2 - 2 <q', c> (approx_dist_kernel) and ||q'||^2, each
-// centroid's approximate distance a = ||q'||^2 + g has |a - exact| <= e with
-// e = 16 D_p 2^-24 (||q'||^2 + ||c||^2): both the float32 sums of D_p terms
-// behind a and the fixed-order exact distance are within (D_p 2^-24 +
-// O(2^-48)) relative of their terms' magnitudes, which sum to at most
-// ||q'||^2 + ||c||^2 -- a factor of more than 3 to spare. U = the np-th
-// smallest a + e bounds the np-th smallest exact distance from above, so a
-// centroid with a - e > U is not among the np nearest (not even on a tie);
-// the others (np and a few more) get the exact distance and the exact
-// selection.
+// Certified form, for nlist <= kProbeStageKeys and D_p 128. From the
+// approximate ranking g = ||c||^2 - 2 <q', c> (approx_dist_tc_kernel, on the
+// tensor cores in TF32) and ||q'||^2, each centroid's approximate distance
+// a = ||q'||^2 + g has |a - exact| <= e with e = kTcProbeEscale (||q'||^2 +
+// ||c||^2), exact being the fixed-order float32 distance (the bound is
+// derived where g is computed and pinned on the CPU). U = the np-th smallest
+// a + e bounds the np-th smallest exact distance from above, so a centroid
+// with a - e > U is not among the np nearest (not even on a tie); the others
+// (np and a few more) get the exact distance and the exact selection.
 // If more than kProbeCandCap remain, every centroid gets the exact distance.
 // Shared memory: `region` holds max(nlist keys, kProbeRowStage rows of D_p
 // floats) + kProbeCandCap ints + D_p floats.
@@ -1356,7 +1255,7 @@ __device__ inline int probe_select_certified(const float* __restrict__ g,
   __syncthreads();
   float qn = 0.0f;
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) qn += s_red[w];
-  const float escale = 16.0f * (float)dp * 5.9604645e-8f;
+  const float escale = kTcProbeEscale;
   const float* grow = g + row * nlist;
 #pragma unroll 8
   for (int c = tid; c < nlist; c += blockDim.x) {
@@ -1830,10 +1729,10 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
 }
 
 // The certified probe selection (approximate ranking + exact refinement)
-// serves lists up to kProbeStageKeys and D_p up to kApproxMaxDp; otherwise
+// serves lists up to kProbeStageKeys and D_p 128; otherwise
 // every centroid distance is computed exactly.
 bool certified_probe(const rq_index* ix) {
-  return ix->nlist <= kProbeStageKeys && ix->dp <= kApproxMaxDp;
+  return ix->nlist <= kProbeStageKeys && ix->dp == 128;
 }
 
 template <int NW4>
@@ -1974,6 +1873,7 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
                          sh.nsel_max > 512 ? 8192 : 4096, np, ix->dim};
   f.out_ids = ws.out_ids;
   f.out_d = ws.out_d;
+  f.nq = nq;
   f.keys = ws.keys;
   f.kcount = ws.kcount;
   f.kcap = ws.kcap;
@@ -1992,7 +1892,9 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
   sel<<<(unsigned)nq, kFinThreads, f.lay.select_bytes(), st>>>(f);
   auto fin = u8 ? finalize_kernel<uint8_t, NW4> : finalize_kernel<float, NW4>;
   RQ_TRY(allow_dynamic_smem((const void*)fin, 220 * 1024));
-  fin<<<(unsigned)nq, kFinThreads, f.lay.bytes(), st>>>(f);
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
+  fin<<<(unsigned)std::min<int64_t>(nq, sms), kFinThreads, f.lay.bytes(), st>>>(f);
   return RQ_OK;
 }
 
@@ -2010,11 +1912,8 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
   // where certified_probe holds, else exact
   tm.mark(RQ_STAGE_PROBE, st);
   if (certified_probe(ix)) {
-    const size_t smem = (size_t)2 * dp * kApproxLd * sizeof(float);
-    RQ_TRY(allow_dynamic_smem((const void*)approx_dist_kernel,
-                              (int)(2 * kApproxMaxDp * kApproxLd * sizeof(float))));
-    approx_dist_kernel<<<dim3(blocks_for(nq, 64), blocks_for(ix->nlist, 64)), 256, smem, st>>>(
-        ws.qrot, nq, ix->cR, ix->nlist, dp, reinterpret_cast<float*>(ws.pkeys), ws.cn);
+    RQ_TRY(launch_approx_dist_tc(ws.qrot, nq, ix->cR, ix->nlist, dp,
+                                 reinterpret_cast<float*>(ws.pkeys), ws.cn, ix->d_err, st));
   } else {
     pair_dist_kernel<1, 2><<<dim3(blocks_for(nq, 32), blocks_for(ix->nlist, 64)), 256, 0, st>>>(
         ws.qrot, nq, ix->cR, ix->nlist, dp, nullptr, nullptr, ws.pkeys);

@@ -713,6 +713,69 @@ def test_certified_probe_filter_bound():
             assert np.all(gap <= e), (gap / e).max()
 
 
+def _tf32(x):
+    """float32 values with the low 13 mantissa bits dropped (what the tensor
+    core's TF32 operands keep)."""
+    return (np.asarray(x, np.float32).view(np.uint32) & np.uint32(0xFFFFE000)).view(np.float32)
+
+
+def _add32(a, b, mode):
+    """float32 addition, rounded to nearest (numpy) or toward zero."""
+    if mode == "rn":
+        return (a + b).astype(np.float32)
+    s = a.astype(np.float64) + b.astype(np.float64)
+    r = s.astype(np.float32)
+    over = np.abs(r.astype(np.float64)) > np.abs(s)
+    return np.where(over, np.nextafter(r, np.float32(0.0)), r).astype(np.float32)
+
+
+def test_tensor_core_probe_filter_bound():
+    """The certified centroid filter with the tensor-core ranking: inner
+    products of TF32-truncated inputs (products exact in float32), summed in
+    float32 in groups of 8 then across groups, in either direction, rounded
+    to nearest or toward zero; g = fma(-2, dot, ||c||^2) and
+    a = ||q||^2 + g in float32. |a - exact| must stay within
+    2^-8 (||q||^2 + ||c||^2), exact being the fixed-order float32 distance."""
+    rng = np.random.default_rng(23)
+    dp = 128
+    esc = np.float32(2.0 ** -8)
+    q = rng.normal(0, 1, (8, dp)).astype(np.float32)
+    cases = [(q, rng.normal(0, 1, (64, dp)).astype(np.float32)),
+             (q, (q[:1] + rng.normal(0, 1e-3, (64, dp))).astype(np.float32))]
+    big = (rng.normal(0, 1, (8, dp)) * 1e6).astype(np.float32)
+    cases.append((big, (big[:1] * rng.uniform(0.999, 1.001, (64, dp))).astype(np.float32)))
+    cases.append((q * 300, rng.normal(0, 300, (64, dp)).astype(np.float32)))
+    unit = rng.normal(0, 1, (8, dp)).astype(np.float32)
+    unit /= np.linalg.norm(unit, axis=1, keepdims=True)
+    cases.append((unit, (unit[:1] + rng.normal(0, 0.05, (64, dp))).astype(np.float32)))
+    worst = 0.0
+    for qq, cc in cases:
+        exact = R.seq_sqdist(qq, cc)
+        qt, ct = _tf32(qq), _tf32(cc)
+        prod = (qt[:, None, :].astype(np.float64) * ct[None, :, :].astype(np.float64)).astype(np.float32)
+        for mode in ("rn", "rz"):
+            for rev in (False, True):
+                order = list(range(dp))[::-1] if rev else list(range(dp))
+                dot = np.zeros((qq.shape[0], cc.shape[0]), np.float32)
+                for g0 in range(0, dp, 8):
+                    part = np.zeros_like(dot)
+                    for d in order[g0:g0 + 8]:
+                        part = _add32(part, prod[:, :, d], mode)
+                    dot = _add32(dot, part, mode)
+                qn = np.zeros(qq.shape[0], np.float32)
+                cn = np.zeros(cc.shape[0], np.float32)
+                for d in order:
+                    qn = _fma32(qq[:, d], qq[:, d], qn)
+                    cn = _fma32(cc[:, d], cc[:, d], cn)
+                g = _fma32(np.float32(-2.0), dot, cn[None, :])
+                a = (qn[:, None] + g).astype(np.float32)
+                e = esc * (qn[:, None] + cn[None, :])
+                gap = np.abs(a.astype(np.float64) - exact.astype(np.float64))
+                assert np.all(gap <= e), (gap / e).max()
+                worst = max(worst, float((gap / e).max()))
+    assert worst > 0.01  # the truncation does show: the bound is not vacuous
+
+
 def test_fma32_helper_is_correctly_rounded():
     """The helper of the bound pin: against exact rationals on random and
     tie-making inputs."""
