@@ -77,7 +77,12 @@ SKEW_REFERENCE_SETTING = (2, 1000)
 # DRAM traffic of one scan launch from an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by kernel and case; valid only while the
 # hash of the kernel's sources matches the one recorded at capture time.
-TRAFFIC = {}
+TRAFFIC = {
+    # scan_mma_kernel, first 64-query batch of the schedule on the 10M skewed
+    # index (profiles/launch_list_skewed_schedule.md): 240,579,584 B read +
+    # 7,299,584 B written
+    "scan:mma:skewed:64:5bb5bf5ea94c64c7": 247879168,
+}
 
 
 def measured_peaks() -> dict:
@@ -107,7 +112,8 @@ SCAN_SOURCES = {
                 "paper_2605_16007_gb300/csrc/rq_scan.cuh", "paper_2605_16007_gb300/csrc/rq_async.cuh",
                 "paper_2605_16007_gb300/csrc/rq_common.cuh"),
     "mma": ("paper_2605_16007_gb300/csrc/rq_scan_mma.cu", "paper_2605_16007_gb300/csrc/rq_scan.cuh",
-            "paper_2605_16007_gb300/csrc/rq_async.cuh", "paper_2605_16007_gb300/csrc/rq_common.cuh"),
+            "paper_2605_16007_gb300/csrc/rq_async.cuh", "paper_2605_16007_gb300/csrc/rq_common.cuh",
+            "paper_2605_16007_gb300/csrc/rq_tc.cuh"),
 }
 MODE_NAMES = {1: "plain", 2: "grouped", 3: "mma"}
 
