@@ -491,6 +491,14 @@ def run_skewed(rq, args, rank, world, local, pg, dev, flush, stream):
     if not args.no_serving:
         serving = run_skew_serving(rq, ix, q, npb, kk, nrr, offered=0.5 * value / max(world, 1))
         serving["saturated"] = run_skew_saturated(rq, ix, q, npb, kk, nrr)
+        # other loads and batch caps: latency against load
+        serving["variants"] = []
+        for frac, mb in ((0.5, 1024), (0.25, 1024), (0.1, 1024), (0.1, 256)):
+            r = run_skew_serving(rq, ix, q, npb, kk, nrr, offered=frac * value / max(world, 1),
+                                 max_batch=mb)
+            r.pop("request_sizes")
+            r.update(offered_frac=frac, max_batch=mb)
+            serving["variants"].append(r)
     ms_per_step = 1e3 * t_dev / args.steps
     lens = np.diff(ix.offsets())
     res = {
@@ -653,10 +661,10 @@ def run_skew_e2e(rq, ix, q, npb, kk, nr, kmax, args, rank, pg, flush):
             "d2h_bytes_per_step": int(d2h / steps)}
 
 
-def run_skew_serving(rq, ix, q, npb, kk, nrr, offered, seconds=2.0, seed=3):
+def run_skew_serving(rq, ix, q, npb, kk, nrr, offered, seconds=2.0, seed=3, max_batch=4096):
     """Poisson arrivals of requests of 1-64 queries at `offered` queries/s;
     each request takes the nprobe and k of its first pool query."""
-    srv = rq.Server(ix, slots=4, max_batch=4096)
+    srv = rq.Server(ix, slots=4, max_batch=max_batch)
     rng = np.random.default_rng(seed)
     sizes = rng.integers(1, 65, 200000)
     rate = offered / sizes.mean()

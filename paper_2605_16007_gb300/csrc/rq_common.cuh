@@ -267,21 +267,17 @@ __device__ inline void block_narrow(const K* src, int m, int shift, int width, K
   const K dmask = ((K)1 << width) - 1;
   for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
   __syncthreads();
-  // four keys per thread per round, their loads issued together (src may be
-  // global memory)
+  // eight keys per thread per round, their loads issued together (src may
+  // be global memory)
   const int stride = blockDim.x;
-  int i = threadIdx.x;
-  for (; i + 3 * stride < m; i += 4 * stride) {
-    K k[4];
+  for (int i0 = threadIdx.x; i0 < m; i0 += 8 * stride) {
+    K k[8];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) k[j] = src[i + j * stride];
+    for (int j = 0; j < 8; ++j) k[j] = i0 + j * stride < m ? src[i0 + j * stride] : (K)0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if ((k[j] & mask) == prefix) atomicAdd(&hist[(int)((k[j] >> shift) & dmask)], 1);
-  }
-  for (; i < m; i += stride) {
-    const K k = src[i];
-    if ((k & mask) == prefix) atomicAdd(&hist[(int)((k >> shift) & dmask)], 1);
+    for (int j = 0; j < 8; ++j)
+      if (i0 + j * stride < m && (k[j] & mask) == prefix)
+        atomicAdd(&hist[(int)((k[j] >> shift) & dmask)], 1);
   }
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -308,12 +304,13 @@ __device__ inline int block_top_diff_bit(const K* src, int m, K* red) {
   const K k0 = src[0];
   K x = 0;
   const int stride = blockDim.x;
-  int i = threadIdx.x;
-  for (; i + 3 * stride < m; i += 4 * stride) {
-    const K a = src[i], b = src[i + stride], c = src[i + 2 * stride], d = src[i + 3 * stride];
-    x |= (a ^ k0) | (b ^ k0) | (c ^ k0) | (d ^ k0);
+  for (int i0 = threadIdx.x; i0 < m; i0 += 8 * stride) {  // eight loads in flight
+    K k[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) k[j] = i0 + j * stride < m ? src[i0 + j * stride] : k0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x |= k[j] ^ k0;
   }
-  for (; i < m; i += stride) x |= src[i] ^ k0;
 #pragma unroll
   for (int o = 16; o; o >>= 1) x |= __shfl_xor_sync(0xffffffffu, x, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
@@ -375,14 +372,30 @@ __device__ inline int block_select_smallest(const uint64_t* src, int m, int n, u
     ctl[4] = 0;
   }
   __syncthreads();
-  for (int i = tid; i < m; i += blockDim.x) {
-    const uint64_t k = src[i];
-    const uint64_t km = k & mask;
-    if (km < prefix) {
-      dst[atomicAdd(&ctl[3], 1)] = k;
-    } else if (km == prefix) {
-      const int p = atomicAdd(&ctl[4], 1);
-      if (p < 32) small[p] = k;
+  // eight keys per thread in flight; a warp reserves room for its keys
+  // below the bucket with one atomic
+  const int lane = tid & 31;
+  for (int w0 = tid - lane; w0 < m; w0 += 8 * (int)blockDim.x) {  // warp-uniform
+    uint64_t k[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int i = w0 + lane + j * (int)blockDim.x;
+      k[j] = i < m ? src[i] : kU64Max;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const bool in = w0 + lane + j * (int)blockDim.x < m;
+      const uint64_t km = k[j] & mask;
+      const bool lo = in && km < prefix;
+      const uint32_t mb = __ballot_sync(0xffffffffu, lo);
+      int base = 0;
+      if (lane == 0 && mb) base = atomicAdd(&ctl[3], __popc(mb));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (lo) dst[base + __popc(mb & ((1u << lane) - 1u))] = k[j];
+      if (in && km == prefix) {
+        const int p = atomicAdd(&ctl[4], 1);
+        if (p < 32) small[p] = k[j];
+      }
     }
   }
   __syncthreads();
@@ -418,12 +431,16 @@ __device__ inline uint32_t block_kth_u32(const uint32_t* src, int m, int rank, i
   // At most 32 values left in the bucket: sort them in one warp.
   if (threadIdx.x == 0) ctl[4] = 0;
   __syncthreads();
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    const uint32_t k = src[i];
-    if ((k & mask) == prefix) {
-      const int p = atomicAdd(&ctl[4], 1);
-      if (p < 32) small[p] = k;
-    }
+  for (int i0 = threadIdx.x; i0 < m; i0 += 8 * blockDim.x) {  // eight loads in flight
+    uint32_t k[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) k[j] = i0 + j * blockDim.x < m ? src[i0 + j * blockDim.x] : 0u;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (i0 + j * blockDim.x < m && (k[j] & mask) == prefix) {
+        const int p = atomicAdd(&ctl[4], 1);
+        if (p < 32) small[p] = k[j];
+      }
   }
   __syncthreads();
   if (threadIdx.x < 32) {
