@@ -546,10 +546,10 @@ def run_skewed(rq, args, rank, world, local, pg, dev, flush, stream):
                   "min_list": st["min_list"], "max_list": st["max_list"]},
         "clocks": clk,
         # this library's kernels per search: rotate, centroid ranking,
-        # preparation, scan, collection, selection and re-rank, and the
-        # streaming finalize (which returns at once for queries whose keys
-        # fit their buffers)
-        "gpu_launches": 7 * args.steps,
+        # preparation, the first bound's window pass and selection, scan,
+        # collection, selection and re-rank, and the streaming finalize
+        # (which returns at once for queries whose keys fit their buffers)
+        "gpu_launches": 9 * args.steps,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline_threads(ix, q, npb, kk, nr, args.cpu_seconds)

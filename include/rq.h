@@ -134,8 +134,12 @@ typedef enum rq_stage {
   RQ_STAGE_ROTATE = 0,   /* q' = P^T q */
   RQ_STAGE_PROBE = 1,    /* centroid distances */
   RQ_STAGE_QUANTIZE = 2, /* per query, one fused step: nprobe selection,
-                            residuals to 4-bit planes, first pruning bound */
-  RQ_STAGE_BOUND = 3,    /* (runs inside RQ_STAGE_QUANTIZE; reads 0) */
+                            residuals to 4-bit planes; the first pruning
+                            bound too, except in the tensor-core form */
+  RQ_STAGE_BOUND = 3,    /* tensor-core form: the first pruning bound (one
+                            grouped pass over the queries' windows, then
+                            the n_sel-th smallest per query); other forms
+                            read 0 (inside RQ_STAGE_QUANTIZE) */
   RQ_STAGE_WORKLIST = 4, /* (pairs are grouped by list inside
                             RQ_STAGE_QUANTIZE; reads 0) */
   RQ_STAGE_SCAN = 5,     /* the code scan */

@@ -52,14 +52,18 @@ bool alloc_should_fail() {
 }
 
 rq_status allow_dynamic_smem(const void* func, int bytes) {
+  // the limit only grows: a kernel launched with several sizes keeps the
+  // largest asked for (setting a smaller one would fail the larger launches)
   static std::mutex mu;
-  static std::set<std::tuple<const void*, int, int>> done;  // (kernel, device, bytes)
+  static std::map<std::pair<const void*, int>, int> done;  // (kernel, device) -> bytes
   int dev = 0;
   RQ_CUDA(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lk(mu);
-  if (done.count(std::make_tuple(func, dev, bytes))) return RQ_OK;
+  const auto key = std::make_pair(func, dev);
+  const auto it = done.find(key);
+  if (it != done.end() && it->second >= bytes) return RQ_OK;
   RQ_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  done.insert(std::make_tuple(func, dev, bytes));
+  done[key] = bytes;
   return RQ_OK;
 }
 

@@ -124,6 +124,19 @@ struct Workspace {
   float* resid = nullptr;         // FastScan: nq x npmax x D_p residuals
   uint8_t* qrec = nullptr;        // nlist x nq pair records of the streaming scan
                                   // (pair_rec_bytes(D_p) each)
+  // tensor-core scan: the first bound from a grouped pass over each query's
+  // window (the first candidates in probe order). Each window pair gets a
+  // second slot in a per-list window bucket with its digits and parameters;
+  // the pass writes the window's estimates into the query's key buffer
+  // (idle until the collection), as uint32 at [q * 2 kcap + position].
+  int32_t* wcount = nullptr;      // nlist: window pairs of each list, then
+                                  // nlist: the largest window limit of each list
+  uint8_t* wqdig = nullptr;       // nlist x nq x D_p (as qdig)
+  float4* wqpb = nullptr;         // nlist x nq (+2) (as qpb)
+  int64_t* wdest = nullptr;       // nlist x nq (stride of qwrow, +2): first estimate index
+  int32_t* wlim = nullptr;        // nlist x nq (same stride, +4): vectors of the list in the window
+  int32_t* wtake = nullptr;       // nq: window candidates of each query
+  uint32_t* pslot = nullptr;      // nq x npmax: each probe's slot in its list's bucket
   int64_t mwords = 0;             // mask words per query
   int64_t kcap = 0;               // survivor keys each query's buffer holds
 };

@@ -118,10 +118,12 @@ constexpr float kTcProbeEscale = 0.00390625f;  // 2^-8
 rq_status launch_approx_dist_tc(const float* qrot, int64_t nq, const float* cR, int nlist, int dp,
                                 float* g, float* cn, int32_t* err, cudaStream_t st);
 
-// Tensor-core scan (rq_scan_mma.cu).
+// Tensor-core scan (rq_scan_mma.cu). With `window` it is the first bound's
+// grouped pass instead: over the window bucket, writing each window
+// candidate's estimate (orderable uint32) into its query's key buffer.
 bool mma_supported(const rq_index* ix);
 rq_status launch_scan_mma(rq_index* ix, const SearchShape& sh, Workspace& ws, cudaStream_t st,
-                          int sms, int withhold);
+                          int sms, int withhold, bool window);
 int next_pow2_host(int64_t v);
 
 }  // namespace rq

@@ -72,6 +72,26 @@ struct Meta {
   int l, nvec, np, v0, first, pad;
 };
 
+// The estimates of two pairs (columns) for this thread's vector: qa =
+// {vl, vl', delta, delta'}, qb = {nq2, nq2', -Sq, -Sq'}, ra / rb the TMEM
+// words (ip as float), b2 = (2 pc - D_p) twice, r2 / f2 the vector's r^2 and
+// f twice. The popcount form's operations, each rounded once: a = 2 ip - Sq
+// is an exact small integer (one FMA with -Sq gives it exactly); x - 2 y is
+// x + (-2) y (the negation and the doubling are exact, so one fused
+// multiply-add rounds the same); the final + 0 of the popcount form is left
+// out because (nq2 + r^2) - x with nq2, r^2 >= +0 is never -0.
+__device__ __forceinline__ float2 estimate2(float4 qa, float4 qb, uint32_t ra, uint32_t rb,
+                                           float2 b2, float2 r2, float2 f2) {
+  const float2 ip = make_float2(__uint_as_float(ra), __uint_as_float(rb));
+  const float2 a = __ffma2_rn(make_float2(2.0f, 2.0f), ip, make_float2(qb.z, qb.w));
+  // t in scalar operations: a packed multiply feeding a packed add can come
+  // out fused into one rounding.
+  const float2 t = make_float2(__fadd_rn(__fmul_rn(qa.z, a.x), __fmul_rn(qa.x, b2.x)),
+                               __fadd_rn(__fmul_rn(qa.w, a.y), __fmul_rn(qa.y, b2.y)));
+  const float2 base = __fadd2_rn(make_float2(qb.x, qb.y), r2);
+  return __ffma2_rn(make_float2(-2.0f, -2.0f), __fmul2_rn(f2, t), base);
+}
+
 __device__ __forceinline__ void named_bar_consumers() {
   asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory");
 }
@@ -87,7 +107,7 @@ __device__ __forceinline__ void named_bar_consumers() {
 // barrier. No load of the producer depends on another.
 __device__ void producer_loop(uint8_t* sm, uint32_t sbase, const int2* __restrict__ items,
                               int n_items, const int32_t* __restrict__ list_count,
-                              int64_t pair_stride, const int64_t* __restrict__ offsets,
+                              const int32_t* __restrict__ maxlim, int64_t pair_stride, const int64_t* __restrict__ offsets,
                               const uint8_t* __restrict__ codes, const float2* __restrict__ fac,
                               const uint8_t* __restrict__ qdb, const float4* __restrict__ qpb,
                               const int64_t* __restrict__ qwrow, const float* __restrict__ qtau,
@@ -117,6 +137,8 @@ __device__ void producer_loop(uint8_t* sm, uint32_t sbase, const int2* __restric
       l = w.x;
       v0 = w.y;
       cnt = list_count[l];
+      // window pass: past every pair's window end the item has no work
+      if (maxlim && v0 >= maxlim[l]) cnt = 0;
       if (cnt > 0) {
         lo = offsets[l] + v0;
         nvec = (int)min((long long)kItemV, (long long)offsets[l + 1] - lo);
@@ -196,14 +218,23 @@ __device__ void producer_loop(uint8_t* sm, uint32_t sbase, const int2* __restric
   __syncwarp();
 }
 
+// Two forms. The scan (kWindow false): per pair its first mask index
+// (qwrow) and bound (qtau); survivor mask words out. The first bound's
+// window pass (kWindow true): per pair the index of its list's first
+// estimate (qwrow) and the list's vectors in the window (qtau, int bits);
+// the estimates of those vectors out, as orderable uint32, to `est`; items
+// at or past `maxlim` of their list are skipped.
+template <bool kWindow>
 __global__ void __launch_bounds__(kMmaThreads, 3)
 scan_mma_kernel(const int2* __restrict__ items, int n_items,
-                const int32_t* __restrict__ list_count, int64_t pair_stride,
+                const int32_t* __restrict__ list_count, const int32_t* __restrict__ maxlim,
+                int64_t pair_stride,
                 const float4* __restrict__ qpb, const uint8_t* __restrict__ qdb,
                 const int64_t* __restrict__ qwrow, const float* __restrict__ qtau,
                 int64_t qstride, const int64_t* __restrict__ offsets,
                 const uint8_t* __restrict__ codes, const float2* __restrict__ fac,
-                uint32_t* __restrict__ mask, int32_t* err, uint64_t wait_ns, int withhold) {
+                uint32_t* __restrict__ mask, uint32_t* __restrict__ est, int32_t* err,
+                uint64_t wait_ns, int withhold) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ volatile int s_ok[4];  // results of the polled waits
   const uint32_t raw_addr = smem_u32(smem_raw);
@@ -228,8 +259,8 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items,
   const uint32_t taddr = *s_tmem;
 
   if (warp == kConsumers / 32) {
-    producer_loop(sm, sbase, items, n_items, list_count, pair_stride, offsets, codes, fac, qdb,
-                  qpb, qwrow, qtau, qstride, err, wait_ns, withhold);
+    producer_loop(sm, sbase, items, n_items, list_count, maxlim, pair_stride, offsets, codes, fac,
+                  qdb, qpb, qwrow, qtau, qstride, err, wait_ns, withhold);
   } else {
     uint32_t ph_mma = 0;
     bool abort = false, mma_pending = false;
@@ -304,74 +335,77 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items,
       ph_mma ^= 1u;
       tc_fence_after();
       // Epilogue: thread t = vector t = TMEM lane 32 (w % 4) + lane of
-      // tile w / 4; 8 pairs per TMEM load, two at a time, partly in packed
-      // float2 operations (each component rounded as the scalar _rn
-      // operation; used only where fusing could not change the result). The
-      // estimator's operations are the popcount
-      // form's, each rounded once: a = 2 ip - Sq is an exact small integer
-      // (one FMA with -Sq gives it exactly); x - 2 y is x + (-2) y (the
-      // negation and the doubling are exact, so one fused multiply-add
-      // rounds the same); the final + 0 of the popcount form is left out
-      // because (nq2 + r^2) - x with nq2, r^2 >= +0 is never -0. Pairs past
-      // np are computed on stale parameters and masked off.
+      // tile w / 4; 8 pairs per TMEM load, two at a time in packed float2
+      // operations (estimate2). Pairs past np are computed on stale
+      // parameters and masked off.
       {
         const int quarter = warp & 3, tile = warp >> 2;
         if (tile < ntiles) {
           const bool valid = tid < m.nvec;
           const float bterm = (float)(2 * pc - kMmaK);
+          const float2 b2 = make_float2(bterm, bterm);
           const float2 r2 = make_float2(f.x, f.x);
           const float2 f2 = make_float2(f.y, f.y);
-          const float2 two = make_float2(2.0f, 2.0f), mtwo = make_float2(-2.0f, -2.0f);
-          const float2 mone = make_float2(-1.0f, -1.0f);
           const uint32_t tl = taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tile * kMmaNmax);
-          const int64_t word = m.v0 / 32 + warp;
-          for (int c1 = 0; c1 < np; c1 += 8) {
-            uint32_t r[8];
-            tmem_ld8(tl + (uint32_t)c1, r);
-            uint32_t sgn[8];  // sign words of tau - d: clear exactly when d <= tau
+          if constexpr (kWindow) {
+            // each pair's estimates of this block's vectors inside its
+            // window, at its first estimate index + the vector's position
+            const int64_t* dest_s = wr_s;
+            const int* lim_s = reinterpret_cast<const int*>(sm + kSmTau + st * kMmaNmax * 4);
+            const int v = m.v0 + tid;  // position in the list
+            for (int c1 = 0; c1 < np; c1 += 8) {
+              uint32_t r[8];
+              tmem_ld8(tl + (uint32_t)c1, r);
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-              const int g = c1 + 2 * h;
-              const float4 qa = qp_s[g];      // {vl, vl', delta, delta'}
-              const float4 qb = qp_s[g + 1];  // {nq2, nq2', -Sq, -Sq'}
-              const float2 ip = make_float2(__uint_as_float(r[2 * h]), __uint_as_float(r[2 * h + 1]));
-              const float2 a = __ffma2_rn(two, ip, make_float2(qb.z, qb.w));
-              // t in scalar operations: a packed multiply feeding a packed
-              // add can come out fused into one rounding.
-              const float2 t = make_float2(
-                  __fadd_rn(__fmul_rn(qa.z, a.x), __fmul_rn(qa.x, bterm)),
-                  __fadd_rn(__fmul_rn(qa.w, a.y), __fmul_rn(qa.y, bterm)));
-              const float2 base = __fadd2_rn(make_float2(qb.x, qb.y), r2);
-              const float2 dd = __ffma2_rn(mtwo, __fmul2_rn(f2, t), base);
-              // tau - d rounded once is >= +0 exactly when d <= tau (neither
-              // is -0 or NaN; a nonzero difference of floats never rounds to
-              // zero; +inf - d = +inf)
-              const float2 df = __ffma2_rn(mone, dd, tau2[g >> 1]);
-              sgn[2 * h] = __float_as_uint(df.x);
-              sgn[2 * h + 1] = __float_as_uint(df.y);
-            }
-            // the eight sign bits, packed: top bytes gathered by byte
-            // permutes, then bits 7, 15, 23, 31 moved to 28..31 by one
-            // multiply (its partial products do not overlap)
-            const uint32_t b03 = __byte_perm(__byte_perm(sgn[0], sgn[1], 0x0073),
-                                             __byte_perm(sgn[2], sgn[3], 0x0073), 0x5410);
-            const uint32_t b47 = __byte_perm(__byte_perm(sgn[4], sgn[5], 0x0073),
-                                             __byte_perm(sgn[6], sgn[7], 0x0073), 0x5410);
-            const uint32_t fail = (((b03 & 0x80808080u) * 0x00204081u) >> 28) |
-                                  ((((b47 & 0x80808080u) * 0x00204081u) >> 28) << 4);
-            const int left = np - c1;
-            const uint32_t passbits =
-                ~fail & (valid ? (left >= 8 ? 0xFFu : (1u << left) - 1u) : 0u);
-            uint32_t mine = 0;
-            if (__any_sync(0xffffffffu, passbits != 0)) {  // else every word is 0
-#pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                const uint32_t mj = __ballot_sync(0xffffffffu, (passbits >> j) & 1u);
-                if (lane == j) mine = mj;
+              for (int h = 0; h < 4; ++h) {
+                const int g = c1 + 2 * h;
+                const float2 dd = estimate2(qp_s[g], qp_s[g + 1], r[2 * h], r[2 * h + 1], b2, r2, f2);
+                if (valid && g < np && v < lim_s[g]) est[dest_s[g] + v] = orderable(dd.x);
+                if (valid && g + 1 < np && v < lim_s[g + 1])
+                  est[dest_s[g + 1] + v] = orderable(dd.y);
               }
             }
-            // lane j writes pair c1 + j's mask word (none past the block's end)
-            if (warp * 32 < m.nvec && lane < 8 && lane < left) mask[wr_s[c1 + lane] + word] = mine;
+          } else {
+            const float2 mone = make_float2(-1.0f, -1.0f);
+            const int64_t word = m.v0 / 32 + warp;
+            for (int c1 = 0; c1 < np; c1 += 8) {
+              uint32_t r[8];
+              tmem_ld8(tl + (uint32_t)c1, r);
+              uint32_t sgn[8];  // sign words of tau - d: clear exactly when d <= tau
+#pragma unroll
+              for (int h = 0; h < 4; ++h) {
+                const int g = c1 + 2 * h;
+                const float2 dd = estimate2(qp_s[g], qp_s[g + 1], r[2 * h], r[2 * h + 1], b2, r2, f2);
+                // tau - d rounded once is >= +0 exactly when d <= tau (neither
+                // is -0 or NaN; a nonzero difference of floats never rounds to
+                // zero; +inf - d = +inf)
+                const float2 df = __ffma2_rn(mone, dd, tau2[g >> 1]);
+                sgn[2 * h] = __float_as_uint(df.x);
+                sgn[2 * h + 1] = __float_as_uint(df.y);
+              }
+              // the eight sign bits, packed: top bytes gathered by byte
+              // permutes, then bits 7, 15, 23, 31 moved to 28..31 by one
+              // multiply (its partial products do not overlap)
+              const uint32_t b03 = __byte_perm(__byte_perm(sgn[0], sgn[1], 0x0073),
+                                               __byte_perm(sgn[2], sgn[3], 0x0073), 0x5410);
+              const uint32_t b47 = __byte_perm(__byte_perm(sgn[4], sgn[5], 0x0073),
+                                               __byte_perm(sgn[6], sgn[7], 0x0073), 0x5410);
+              const uint32_t fail = (((b03 & 0x80808080u) * 0x00204081u) >> 28) |
+                                    ((((b47 & 0x80808080u) * 0x00204081u) >> 28) << 4);
+              const int left = np - c1;
+              const uint32_t passbits =
+                  ~fail & (valid ? (left >= 8 ? 0xFFu : (1u << left) - 1u) : 0u);
+              uint32_t mine = 0;
+              if (__any_sync(0xffffffffu, passbits != 0)) {  // else every word is 0
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  const uint32_t mj = __ballot_sync(0xffffffffu, (passbits >> j) & 1u);
+                  if (lane == j) mine = mj;
+                }
+              }
+              // lane j writes pair c1 + j's mask word (none past the block's end)
+              if (warp * 32 < m.nvec && lane < 8 && lane < left) mask[wr_s[c1 + lane] + word] = mine;
+            }
           }
         }
       }
@@ -399,16 +433,25 @@ scan_mma_kernel(const int2* __restrict__ items, int n_items,
 bool mma_supported(const rq_index* ix) { return ix->dp == kMmaK; }
 
 rq_status launch_scan_mma(rq_index* ix, const SearchShape& sh, Workspace& ws, cudaStream_t st,
-                          int sms, int withhold) {
+                          int sms, int withhold, bool window) {
   if (ix->dp != kMmaK) return fail(RQ_ERR_NOT_IMPLEMENTED, "tensor-core scan built for D_p = 128");
-  RQ_TRY(allow_dynamic_smem((const void*)scan_mma_kernel, kSmAlloc));
+  const auto kern = window ? scan_mma_kernel<true> : scan_mma_kernel<false>;
+  RQ_TRY(allow_dynamic_smem((const void*)kern, kSmAlloc));
   // Three blocks per SM (registers; ~69 KB of shared memory each); their
   // TMEM (128 columns each) stays within the SM's 512 columns.
   const unsigned grid = (unsigned)std::max(1, std::min(sms * 3, ix->n_items));
-  scan_mma_kernel<<<grid, kMmaThreads, kSmAlloc, st>>>(
-      ix->items, ix->n_items, ws.list_count, sh.nq, ws.qpb, ws.qdig, ws.qwrow, ws.qtau,
-      (sh.nq + 3) & ~int64_t(3), ix->offsets, ix->codes, ix->fac, ws.mask, ix->d_err,
-      withhold ? kTestWaitLimitNs : kWaitLimitNs, withhold);
+  const int64_t qstride = (sh.nq + 3) & ~int64_t(3);
+  if (window) {
+    kern<<<grid, kMmaThreads, kSmAlloc, st>>>(
+        ix->items, ix->n_items, ws.wcount, ws.wcount + ix->nlist, sh.nq, ws.wqpb, ws.wqdig,
+        ws.wdest, reinterpret_cast<const float*>(ws.wlim), qstride, ix->offsets, ix->codes,
+        ix->fac, nullptr, reinterpret_cast<uint32_t*>(ws.keys), ix->d_err, kWaitLimitNs, 0);
+  } else {
+    kern<<<grid, kMmaThreads, kSmAlloc, st>>>(
+        ix->items, ix->n_items, ws.list_count, nullptr, sh.nq, ws.qpb, ws.qdig, ws.qwrow,
+        ws.qtau, qstride, ix->offsets, ix->codes, ix->fac, ws.mask, nullptr, ix->d_err,
+        withhold ? kTestWaitLimitNs : kWaitLimitNs, withhold);
+  }
   RQ_CUDA(cudaGetLastError());
   return RQ_OK;
 }

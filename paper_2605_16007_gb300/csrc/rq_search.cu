@@ -159,7 +159,9 @@ __device__ __forceinline__ void quantize_pair(int64_t pair, int64_t q, int c, in
                                               uint32_t* __restrict__ planes,
                                               uint8_t* __restrict__ qdb,
                                               float4* __restrict__ qpb,
-                                              uint8_t* __restrict__ qrec, uint64_t* slot_out) {
+                                              uint8_t* __restrict__ qrec, uint64_t* slot_out,
+                                              int wslot, uint8_t* __restrict__ wqdb,
+                                              float4* __restrict__ wqpb) {
   constexpr int PER = 4 * NW4;  // values per lane (dp / 32)
   // Streaming scan: the pair's record in its list's bucket (planes, then
   // {vl, delta, nq2, Sq}; query, mask word and bound are added once the
@@ -205,8 +207,11 @@ __device__ __forceinline__ void quantize_pair(int64_t pair, int64_t q, int c, in
       // layout (16-byte chunk d/16 of bucket row `slot` at chunk position
       // (d/16) ^ (slot % 8)), so that one bulk copy lands them in place.
       const int d = lane + 32 * i;
-      qdb[((int64_t)c * nq + slot) * dp + ((((d >> 4) ^ (slot & 7))) << 4) + (d & 15)] =
-          e4m3_of_int(qu);
+      const uint8_t e = e4m3_of_int(qu);
+      qdb[((int64_t)c * nq + slot) * dp + ((((d >> 4) ^ (slot & 7))) << 4) + (d & 15)] = e;
+      // a window pair's copy in the window bucket (same layout)
+      if (wslot >= 0)
+        wqdb[((int64_t)c * nq + wslot) * dp + ((((d >> 4) ^ (wslot & 7))) << 4) + (d & 15)] = e;
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -236,6 +241,13 @@ __device__ __forceinline__ void quantize_pair(int64_t pair, int64_t q, int c, in
       cp[2] = delta;
       cp[4] = nq2;
       cp[6] = -(float)sq;
+      if (wslot >= 0) {
+        float* wp = reinterpret_cast<float*>(wqpb + (int64_t)c * nq + (wslot & ~1)) + (wslot & 1);
+        wp[0] = vl;
+        wp[2] = delta;
+        wp[4] = nq2;
+        wp[6] = -(float)sq;
+      }
     }
   }
 }
@@ -502,6 +514,9 @@ __device__ __forceinline__ void kth_offer(KthState* ks, uint32_t* buf, uint32_t 
 __device__ inline void kth_maybe_compact(KthState* ks, uint32_t* buf, int cap, int room, int n,
                                          int* hist, uint64_t* small, int* ctl) {
   const int nb = ks->nbuf;
+  // every thread reads the count before any thread offers the next round's
+  // keys, so that all take the same branch
+  __syncthreads();
   if (nb <= cap - room) return;
   const uint32_t t2 = block_kth_u32(buf, nb, n, hist, small, ctl);  // nb > n: a key below thr
   if (threadIdx.x == 0) {
@@ -1132,6 +1147,9 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(FinalizeArgs a) {
       }
       __syncthreads();
       const int nb = s_nbuf;
+      // every thread reads the count before any thread offers the next
+      // step's keys, so that all take the same branch
+      __syncthreads();
       if (nb > lay.S - STEP) {
         // keep the n_sel smallest (nb > S - STEP > n_sel)
         block_select_smallest(s_stage, nb, n_sel, s_sel, hist, small, s_ctl, false);
@@ -1467,6 +1485,16 @@ struct PrepArgs {
   int bound_cap;      // keys the shared region holds for the first bound
   int lut_offset;     // byte offset of the table region in dynamic shared memory
   int32_t* err;
+  // grouped first bound (null wcount: the block estimates its own window)
+  int32_t* wcount;    // nlist window pairs per list, then nlist largest limits
+  uint8_t* wqdb;      // window bucket: digits, parameters, first estimate index,
+  float4* wqpb;       // vectors of the list in the window
+  int64_t* wdest;
+  int32_t* wlim;
+  int32_t* wtake;     // nq: window size of each query
+  uint32_t* pslot;    // nq x npmax: bucket slot of each probe
+  int64_t est_stride; // estimates per query in the key buffer
+  int win_offset;     // byte offset of the window table (int2 per probe) in dynamic shared memory
 };
 
 template <int NW4>
@@ -1483,6 +1511,9 @@ __global__ void __launch_bounds__(kPrepThreads, NW4 >= 4 ? 2 : 4) prep_kernel(Pr
   // FastScan tables of the bound (after the region, whose size the host gives)
   float* lut_region = reinterpret_cast<float*>(smem + a.lut_offset);
   const int npq = min(a.nprobe[row], a.npmax);
+  const int n_sel = a.nsel[row];
+  const bool bound_on = !*a.no_prune && n_sel > 0;
+  if (a.wtake && tid == 0) a.wtake[row] = 0;  // until the window is known
   const int got =
       a.g ? probe_select_certified(a.g, a.cn, a.qrot, a.cR, a.nlist, a.npmax, a.dp, row, dst,
                                    region, hist, small, ctl)
@@ -1503,6 +1534,39 @@ __global__ void __launch_bounds__(kPrepThreads, NW4 >= 4 ? 2 : 4) prep_kernel(Pr
     if (tid == 0) flag_error(a.err, kErrBadProbe);
     return;
   }
+  // Grouped first bound: the window is the first bound_window(n_sel)
+  // candidates in probe order, so its probes are a prefix of the probes.
+  // One warp finds them: per probe its first position in the window and its
+  // vectors in the window (s_win), and how many probes reach into it.
+  int2* s_win = reinterpret_cast<int2*>(smem + a.win_offset);
+  __shared__ int s_pw;
+  if (a.wcount && warp == 0) {
+    const int cap1 = bound_on ? bound_window(n_sel) : 0;
+    int carry = 0, pw = 0;
+    for (int b = 0; b < npq && carry < cap1; b += 32) {
+      const int p = b + lane;
+      int len = 0;
+      if (p < npq) {
+        const uint32_t l = (uint32_t)dst[p];
+        len = (int)min(a.offsets[l + 1] - a.offsets[l], (int64_t)cap1);
+      }
+      int incl = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const int first = carry + incl - len;  // < 2^31: carry < cap1, 32 lengths <= cap1
+      const bool in = p < npq && first < cap1;
+      if (in) s_win[p] = make_int2(first, min(len, cap1 - first));
+      pw += __popc(__ballot_sync(0xffffffffu, in));
+      carry = min(carry + __shfl_sync(0xffffffffu, incl, 31), cap1);
+    }
+    if (lane == 0) {
+      s_pw = pw;
+      a.wtake[row] = carry;
+    }
+  }
   // (dst[p] keeps the list id in its low word; the quantisation puts the
   // pair's bucket slot in the high word, which held the distance: every
   // reader of the distances above is done after this barrier)
@@ -1520,12 +1584,22 @@ __global__ void __launch_bounds__(kPrepThreads, NW4 >= 4 ? 2 : 4) prep_kernel(Pr
     float qv[PER], cv[PER];
 #pragma unroll
     for (int i = 0; i < PER; ++i) qv[i] = a.qrot[row * a.dp + lane + 32 * i];
-    int c = 0, slot = 0;
+    int c = 0, slot = 0, wslot = -1;
+    int2 win = make_int2(0, 0);
     auto request = [&](int pp) {
       c = (int)(uint32_t)dst[pp];
 #pragma unroll
       for (int i = 0; i < PER; ++i) cv[i] = a.cR[(int64_t)c * a.dp + lane + 32 * i];
       if (a.list_count && lane == 0) slot = atomicAdd(&a.list_count[c], 1);
+      // a window pair (with vectors in the window) also takes a window slot
+      wslot = -1;
+      if (a.wcount && lane == 0 && pp < s_pw) {
+        win = s_win[pp];
+        if (win.y > 0) {
+          wslot = atomicAdd(&a.wcount[c], 1);
+          atomicMax(&a.wcount[a.nlist + c], win.y);
+        }
+      }
     };
     // (no look-ahead above D_p 1024, where the registers run out)
     constexpr bool kAhead = NW4 <= 8;
@@ -1537,18 +1611,22 @@ __global__ void __launch_bounds__(kPrepThreads, NW4 >= 4 ? 2 : 4) prep_kernel(Pr
       for (int i = 0; i < PER; ++i) cur[i] = cv[i];
       const int cc = c;
       const int sl = __shfl_sync(0xffffffffu, slot, 0);
+      const int wsl = __shfl_sync(0xffffffffu, wslot, 0);
+      if (wsl >= 0 && lane == 0) {
+        a.wdest[cc * a.qstride + wsl] = row * a.est_stride + win.x;
+        a.wlim[cc * a.qstride + wsl] = win.y;
+      }
       if (kAhead && p + kPrepThreads / 32 < npq) request(p + kPrepThreads / 32);
       quantize_pair<NW4>(row * a.npmax + p, row, cc, sl, lane, qv, cur, a.nq, a.dp, a.qparams,
                          a.planes, a.qdb, a.qpb, a.qrec,
-                         &dst[p]);
+                         &dst[p], wsl, a.wqdb, a.wqpb);
     }
   }
   // The block's own writes of planes and parameters are visible to it
   // after the barrier.
   __syncthreads();
-  const int n_sel = a.nsel[row];
   uint32_t tau = kU32Max;
-  if (!*a.no_prune && n_sel > 0) {
+  if (!a.wcount && bound_on) {
     uint32_t* bk = reinterpret_cast<uint32_t*>(region);
     if (a.lut)
       tau = bound_block_lut<NW4>(row, a.npmax, npq, n_sel, dst, a.qparams, a.qrot, a.cR,
@@ -1558,15 +1636,17 @@ __global__ void __launch_bounds__(kPrepThreads, NW4 >= 4 ? 2 : 4) prep_kernel(Pr
       tau = bound_block<NW4>(row, a.npmax, npq, n_sel, dst, a.qparams, a.planes, a.offsets,
                              a.codes, a.fac, a.dp, bk, a.bound_cap, hist, small, ctl);
   }
-  if (tid == 0) a.bound[row] = tau;
+  if (!a.wcount && tid == 0) a.bound[row] = tau;
   if (a.qwrow) {
-    // each pair's first mask index and bound, at its bucket slot
+    // each pair's first mask index and bound, at its bucket slot (with the
+    // grouped bound: the slot, for window_bound_kernel to write the bound)
     const float tf = tau_threshold(tau);
     for (int p = tid; p < npq; p += blockDim.x) {
       const uint64_t e = dst[p];
       const int64_t c = (uint32_t)e, slot = (uint32_t)(e >> 32);
       a.qwrow[c * a.qstride + slot] = row * a.mwords + a.wbase[row * a.npmax + p];
-      a.qtau[c * a.qstride + slot] = tf;
+      if (a.wcount) a.pslot[row * a.npmax + p] = (uint32_t)slot;
+      else a.qtau[c * a.qstride + slot] = tf;
     }
   }
   if (a.qrec) {
@@ -1578,6 +1658,40 @@ __global__ void __launch_bounds__(kPrepThreads, NW4 >= 4 ? 2 : 4) prep_kernel(Pr
       int4* m = reinterpret_cast<int4*>(a.qrec + (c * a.nq + slot) * rb + a.dp / 2 + 16);
       *m = make_int4((int)row, a.wbase[row * a.npmax + p], (int)tau, 0);
     }
+  }
+}
+
+// The grouped first bound's last step (Section 3.3.3), one block per
+// query: the n_sel-th smallest of the window's estimates, which the
+// tensor-core scan's window pass wrote to the query's key buffer (the value
+// the preparation block's streaming selection finds from the same
+// estimates; all ones when the window holds fewer than n_sel), by block
+// radix selection straight from the buffer; then the bound as a float32
+// threshold at each of the query's bucket slots.
+__global__ void __launch_bounds__(256)
+window_bound_kernel(const uint32_t* __restrict__ est, int64_t est_stride,
+                    const int32_t* __restrict__ wtake, const int32_t* __restrict__ nsel,
+                    const int32_t* __restrict__ no_prune, const int32_t* __restrict__ nprobe,
+                    int npmax, const int32_t* __restrict__ probe_ids,
+                    const uint32_t* __restrict__ pslot, int nlist, int64_t nq, int64_t qstride,
+                    uint32_t* __restrict__ bound, float* __restrict__ qtau) {
+  __shared__ int hist[256];
+  __shared__ uint64_t small[32];
+  __shared__ int ctl[8];
+  const int64_t row = blockIdx.x;
+  const int n_sel = nsel[row];
+  const int n = (int)min((int64_t)wtake[row], est_stride);
+  uint32_t tau = kU32Max;
+  if (!*no_prune && n_sel > 0 && n >= n_sel)
+    tau = block_kth_u32(est + row * est_stride, n, n_sel, hist, small, ctl);
+  if (threadIdx.x == 0) bound[row] = tau;
+  const float tf = tau_threshold(tau);
+  const int npq = min(nprobe[row], npmax);
+  for (int p = threadIdx.x; p < npq; p += blockDim.x) {
+    const int c = probe_ids[row * npmax + p];
+    const uint32_t slot = pslot[row * npmax + p];
+    // (a query whose probe selection failed left no slots: skip them)
+    if (c >= 0 && c < nlist && slot < (uint32_t)nq) qtau[(int64_t)c * qstride + slot] = tf;
   }
 }
 
@@ -1603,7 +1717,14 @@ void rebase(T*& p, char* base) {
 }
 
 // Above this many bytes a batch's workspace is split into sub-batches.
-constexpr size_t kWorkspaceBudget = size_t(8) << 30;
+constexpr size_t kWorkspaceBudget = size_t(12) << 30;
+
+// The tensor-core form takes its first bound from a grouped pass over the
+// queries' windows (the window bucket, then window_bound_kernel); the other
+// forms estimate each query's window in its preparation block.
+bool grouped_bound(const rq_index* ix, const SearchShape& sh) {
+  return sh.mode == RQ_SCAN_MMA && !sh.lut && ix->dp == 128;
+}
 
 // Lays out the workspace of a search shape: every field as an offset from
 // the base, the total in ws.bytes.
@@ -1652,6 +1773,16 @@ void layout_workspace(const rq_index* ix, const SearchShape& sh, Workspace& ws) 
     L.take(&ws.qtau, (int64_t)ix->nlist * ((nq + 3) & ~int64_t(3)) + 4);
     L.take(&ws.qdig, (int64_t)ix->nlist * nq * ix->dp);
     L.take(&ws.qpb, (int64_t)ix->nlist * nq + 2);  // + a couple read past the last bucket
+  }
+  if (grouped_bound(ix, sh)) {
+    // the window bucket, with the strides and tails of the main one
+    L.take(&ws.wcount, 2 * (int64_t)ix->nlist);
+    L.take(&ws.wqdig, (int64_t)ix->nlist * nq * ix->dp);
+    L.take(&ws.wqpb, (int64_t)ix->nlist * nq + 2);
+    L.take(&ws.wdest, (int64_t)ix->nlist * ((nq + 3) & ~int64_t(3)) + 2);
+    L.take(&ws.wlim, (int64_t)ix->nlist * ((nq + 3) & ~int64_t(3)) + 4);
+    L.take(&ws.wtake, nq);
+    L.take(&ws.pslot, nq * np);
   }
   ws.bytes = L.off;
 }
@@ -1725,6 +1856,15 @@ rq_status alloc_workspace(rq_index* ix, const SearchShape& sh, cudaStream_t st, 
     rebase(ws.qdig, b);
     rebase(ws.qpb, b);
   }
+  if (grouped_bound(ix, sh)) {
+    rebase(ws.wcount, b);
+    rebase(ws.wqdig, b);
+    rebase(ws.wqpb, b);
+    rebase(ws.wdest, b);
+    rebase(ws.wlim, b);
+    rebase(ws.wtake, b);
+    rebase(ws.pslot, b);
+  }
   return RQ_OK;
 }
 
@@ -1795,17 +1935,40 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
     const size_t bound_keys =
         std::max<size_t>(2 * (size_t)sh.nsel_max + 2048,
                          std::min<size_t>((size_t)bound_window(sh.nsel_max) + 1024, 8192));
-    const size_t bound_bytes = 4 * bound_keys;
+    const bool gb = grouped_bound(ix, sh);
+    const size_t bound_bytes = gb ? 0 : 4 * bound_keys;
     const size_t region = (std::max<size_t>({stage, bound_bytes, 64}) + 15) & ~(size_t)15;
     a.bound_cap = (int)(region / 4);
     size_t smem = (size_t)std::max(2, next_pow2_host(np)) * 8 + region;
     smem = (smem + 15) & ~(size_t)15;
+    // the grouped bound's window table
+    a.win_offset = (int)smem;
+    if (gb) smem += (size_t)np * 8;
+    a.wcount = gb ? ws.wcount : nullptr;
+    a.wqdb = ws.wqdig;
+    a.wqpb = ws.wqpb;
+    a.wdest = ws.wdest;
+    a.wlim = ws.wlim;
+    a.wtake = gb ? ws.wtake : nullptr;
+    a.pslot = ws.pslot;
+    a.est_stride = 2 * ws.kcap;
     a.lut_offset = (int)smem;
     if (sh.lut) smem += (size_t)(32 * dp + dp) * sizeof(float);
     RQ_TRY(allow_dynamic_smem((const void*)prep_kernel<NW4>, 200 * 1024));
     prep_kernel<NW4><<<(unsigned)nq, kPrepThreads, smem, st>>>(a);
   }
   tm.mark(RQ_STAGE_BOUND, st);
+  if (grouped_bound(ix, sh)) {
+    // the first bound from one grouped pass over the windows; the estimates
+    // go to the key buffers, idle until the collection
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
+    RQ_TRY(launch_scan_mma(ix, sh, ws, st, sms, 0, true));
+    window_bound_kernel<<<(unsigned)nq, 256, 0, st>>>(
+        reinterpret_cast<const uint32_t*>(ws.keys), 2 * ws.kcap, ws.wtake, ws.nsel,
+        ws.rerank_on + nq, ws.nprobe, np, ws.probe_ids, ws.pslot, ix->nlist, nq,
+        (nq + 3) & ~int64_t(3), ws.bound, ws.qtau);
+  }
   tm.mark(RQ_STAGE_WORKLIST, st);
   if (sh.lut) {
     tm.mark(RQ_STAGE_SCAN, st);
@@ -1829,7 +1992,7 @@ rq_status enqueue_scan_stages(rq_index* ix, const SearchShape& sh, Workspace& ws
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device);
     tm.mark(RQ_STAGE_SCAN, st);
     if (sh.mode == RQ_SCAN_MMA) {
-      RQ_TRY(launch_scan_mma(ix, sh, ws, st, sms, sh.withhold));
+      RQ_TRY(launch_scan_mma(ix, sh, ws, st, sms, sh.withhold, false));
     } else {
       RQ_TRY(launch_scan_stream(ix, sh, ws, st, sms, sh.withhold ? kTestWaitLimitNs : kWaitLimitNs,
                                 sh.withhold));
@@ -1907,7 +2070,7 @@ rq_status enqueue_search(rq_index* ix, const SearchShape& sh, Workspace& ws, cud
   const bool grouped = sh.mode != RQ_SCAN_PLAIN;
   rotate_kernel8<<<dim3(blocks_for(nq, 8), dp / 64), 256, 0, st>>>(
       ws.q, nq, ix->dim, ix->P32, dp, ws.qrot, grouped ? ws.list_count : nullptr,
-      grouped ? ix->nlist : 0, nullptr, 0);
+      grouped ? ix->nlist : 0, ws.wcount, ws.wcount ? 2 * ix->nlist : 0);
   // 2. centroid ranking: approximate (filter of the certified selection)
   // where certified_probe holds, else exact
   tm.mark(RQ_STAGE_PROBE, st);

@@ -80,11 +80,11 @@ def test_skewed_full_size_modes_agree_and_replay(skewed):
 
 
 def test_skewed_large_batch_split_equals_small_batches(skewed):
-    """A batch whose workspace would pass the 8 GiB budget (8192 queries at
-    nprobe 512 on the skewed index: survivor masks, key buffers and the
-    tensor-core scan's per-list buckets) runs as sub-batches of one
-    workspace; its results equal those of the same queries searched in
-    small batches, in every grouped mode."""
+    """A batch whose workspace would pass the 12 GiB budget (8192 queries at
+    nprobe 512 on the skewed index in the tensor-core form: survivor masks,
+    key buffers and the per-list and window buckets) runs as sub-batches of
+    one workspace; its results equal those of the same queries searched in
+    small batches, in the tensor-core and the streaming form."""
     rq, ix = skewed
     wl = W.WORKLOADS["skewed"]
     nq = 8192
